@@ -1,0 +1,23 @@
+"""Seeded synthetic inputs for the posterior-mean system of the CMB source-separation model.
+
+This module is shared by the CPU oracle (``oracle/``), the tests and ``bench.py``.  It holds
+input synthesis only: pixel graphs and their Laplacian in CSR form (the neighbour structure a
+user of the solver supplies, Sec. 2.2 / App. C), noise-precision maps, spectral parameters and
+simulated observations.  It computes no part of the solve: no mixing matrix used by a solver,
+no right-hand side, no operator application.
+"""
+
+from .grids import (  # noqa: F401
+    GridGraph,
+    periodic_lattice,
+    latlong_sphere,
+    laplacian_csr_from_edges,
+)
+from .problems import (  # noqa: F401
+    PLANCK_NU,
+    Problem,
+    make_problem,
+    config_problem,
+    batch_problems,
+    CONFIG_SEED_BASE,
+)
