@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the posterior-mean solve on one GB300 (or N independent ranks).
+
+One step = one solve of G X = B (eq. mu*) to true FP64 relative residual 1e-8 with the
+mixed-precision path (FP32 preconditioned CG inside FP64 iterative refinement), on the
+1024 x 2048 latitude-longitude sphere workload (n = 2,097,152 pixels, k = 6 sources, m = 9
+Planck channels), with B resident in HBM.  Reported beside it: the same solve in plain FP64
+PCG, the stand-alone operator apply in GB/s, the roofline of the dominant kernel, an
+end-to-end number through the public API with host buffers, and the CPU oracle timed on a
+bounded sample.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solve time to relres 1e-8 (mixed vs FP64 CG, 1 GB300); operator HBM GB/s"
+WORKLOAD = "sphere1024x2048_k6_m9"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--scale", type=int, default=1, help="divide grid sides (small runs)")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic bytes per pixel (kernel table)
+# ---------------------------------------------------------------------------------------------
+def bytes_inner_apply(k, m, E, s=4):
+    # read z, p, q (3k) + D (m) + ELL values (E) + diagonal (1); write p, q (2k); ELL cols int32
+    return (5 * k + m + E + 1) * s + 4 * E
+
+
+def bytes_inner_update(k, m, s=4):
+    # read d, p, r, q (4k) + D (m) + diagonal (1); write d, r, z (3k)
+    return (7 * k + m + 1) * s
+
+
+def bytes_apply(k, m, E, R=1, s=4):
+    # read X (R k) + D (m) + ELL values (E) + diagonal (1); write Y (R k); ELL cols int32
+    return (2 * R * k + m + E + 1) * s + 4 * E
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------------------------
+def oracle_pcg_sample(p, seconds, iters_ref):
+    """Times the oracle's block-Jacobi PCG (FP64, numpy/scipy) on the full workload for a
+    bounded number of iterations; scales ms/iteration to a whole solve of ``iters_ref``
+    iterations.  Returns a cpu_baseline dict."""
+    from oracle import model, solve
+    L = model.laplacian_from_csr(p.graph.rowptr, p.graph.col, p.graph.val, p.n)
+    A = model.powerlaw_mixing(p.nu, p.beta)
+    b = model.rhs(p.D, p.Yobs[0], A)
+    t0 = time.perf_counter()
+    _, it, _, secs = solve.pcg_block_jacobi(L, p.D, p.tau, p.kappa, A, b, eps=1e-8,
+                                            maxit=10 ** 9, max_seconds=seconds)
+    wall = time.perf_counter() - t0
+    per_it = secs / max(it, 1)
+    return {
+        "value": per_it * iters_ref * 1e3, "unit": "ms", "cores": os.cpu_count(),
+        "kind": "oracle",
+        "sample": (f"oracle FP64 block-Jacobi PCG (numpy/scipy, default threading) on the full "
+                   f"{p.name} system: {it} iterations in {secs:.1f} s ({wall:.1f} s with set-up); "
+                   f"ms/iteration x {iters_ref} iterations (the FP64 PCG iteration count to "
+                   f"relres 1e-8)"),
+        "ms_per_iteration": per_it * 1e3, "iterations_timed": it,
+    }
+
+
+def stored_iterations(config):
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_pcg_iterations_c{config}.json")
+    try:
+        with open(path) as f:
+            return int(json.load(f)["iterations"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    import synth
+    if rank != 0:
+        return
+    p = synth.config_problem(args.config, scale=args.scale)
+    iters = stored_iterations(args.config)
+    vals = []
+    sample = None
+    per_step = max(3.0, min(args.cpu_seconds, 150.0 / max(args.steps + args.warmup, 1)))
+    for step in range(args.warmup + args.steps):
+        cb = oracle_pcg_sample(p, per_step, iters or 1)
+        if step >= args.warmup:
+            vals.append(cb["value"])
+            sample = cb
+    v = float(np.mean(vals))
+    if iters is None:
+        sample["sample"] += " [no stored oracle iteration count: value is ms per iteration]"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "nrhs": 1,
+                       "tol": 1e-8},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": sample["cores"],
+                             "kind": "oracle", "sample": sample["sample"]},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import synth
+    from paper_2204_08057_gb300 import build as _build
+    from paper_2204_08057_gb300.operator import Operator
+
+    _build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    # weak scaling: every rank solves its own independent instance (own seed)
+    p = synth.config_problem(args.config, scale=args.scale)
+    if rank > 0:
+        p = synth.make_problem(p.name, p.graph, p.k, p.nu, p.beta, p.kappa, p.tau,
+                               synth.CONFIG_SEED_BASE + 100 * rank + args.config)
+    op = Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
+                  kappa=p.kappa, nu=p.nu, beta=p.beta)
+    E = int(np.max(np.diff(p.graph.rowptr))) - 1
+    Yh = torch.from_numpy(p.Yobs).pin_memory()
+    Y = Yh.to(dev)
+    B = op.rhs(Y)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- mixed-precision solve (the step) ------------------------------------------------------
+    kw = dict(tol=1e-8, precision=1, profile=1)
+    for _ in range(args.warmup):
+        X, info = op.solve(B, **kw)
+    clocks = ClockSampler(local_rank) if not args.no_clocks else None
+    barrier()
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        X, info = op.solve(B, **kw)
+        infos.append(info)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop() if clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    last = infos[-1]
+    assert last["code"] == 0, last
+
+    # ---- plain FP64 PCG on the same system ----------------------------------------------------
+    kw64 = dict(tol=1e-8, precision=0, profile=1)
+    X64, info64 = op.solve(B, **kw64)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    f0.record(stream)
+    for _ in range(args.fp64_steps):
+        X64, info64 = op.solve(B, **kw64)
+    f1.record(stream)
+    barrier()
+    ms64 = f0.elapsed_time(f1) / max(args.fp64_steps, 1)
+    relerr_mixed_vs_fp64 = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
+
+    # ---- stand-alone operator apply (FP32), inputs larger than L2 ----------------------------
+    X32 = X.to(torch.float32)
+    for _ in range(3):
+        Yap = op.apply(X32)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    barrier()
+    a0.record(stream)
+    for _ in range(reps):
+        Yap = op.apply(X32)
+    a1.record(stream)
+    barrier()
+    ms_apply = a0.elapsed_time(a1) / reps
+    apply_bytes = bytes_apply(p.k, p.m, E) * p.n
+    peak, peak_kind = load_peaks()
+    apply_gbs = apply_bytes / (ms_apply * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (from the timed steps' events) ---------------------
+    tot_apply = sum(i["ms_apply"] for i in infos)
+    tot_update = sum(i["ms_update"] for i in infos)
+    n_ap = sum(i["n_apply"] for i in infos)
+    n_up = sum(i["n_update"] for i in infos)
+    if tot_apply >= tot_update:
+        kname, avg_ms, per_px = "k_inner_apply<6,float>", tot_apply / n_ap, \
+            bytes_inner_apply(p.k, p.m, E)
+    else:
+        kname, avg_ms, per_px = "k_inner_update<6,float>", tot_update / n_up, \
+            bytes_inner_update(p.k, p.m)
+    achieved = per_px * p.n / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": kname,
+                "bytes_per_launch": per_px * p.n, "avg_launch_ms": avg_ms,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+
+    # ---- end to end through the public API with host buffers --------------------------------
+    Xh = torch.empty((1, p.k, p.n), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        Yd = Yh.to(dev, non_blocking=True)
+        Xd, _ = op.solve(op.rhs(Yd), tol=1e-8)
+        Xh.copy_(Xd, non_blocking=True)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    g0.record(stream)
+    for _ in range(args.steps):
+        Yd = Yh.to(dev, non_blocking=True)
+        Xd, _ = op.solve(op.rhs(Yd), tol=1e-8)
+        Xh.copy_(Xd, non_blocking=True)
+    g1.record(stream)
+    barrier()
+    ms_e2e = g0.elapsed_time(g1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    # ---- CPU oracle baseline (rank 0, N = 1) -------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters = stored_iterations(args.config) or info64["iterations"]
+        cpu = oracle_pcg_sample(p, args.cpu_seconds, iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded sphere maps shaped like Planck: GMRF-smooth sources, "
+                    "lognormal noise, power-law mixing)",
+            "config": {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "nrhs": 1,
+                       "tol": 1e-8, "precision": "mixed (FP32 inner PCG, FP64 refinement)",
+                       "l2": "inputs larger than L2 (working set ~%d MB)"
+                             % int((p.n * (5 * p.k * 4 + 2 * p.k * 8 + p.m * 12 + 44)) / 1e6),
+                       "per_rank": "independent instance per rank (own seed)"},
+            "iterations": last["iterations"], "outer": last["outer"],
+            "relres": last["relres"],
+            "fp64_pcg": {"ms": ms64, "iterations": info64["iterations"],
+                         "relres": info64["relres"], "speedup_mixed": ms64 / ms,
+                         "relerr_mixed_vs_fp64": relerr_mixed_vs_fp64},
+            "apply": {"ms": ms_apply, "gbs": apply_gbs, "frac": apply_gbs / peak,
+                      "bytes": apply_bytes, "dtype": "f32"},
+            "roofline": roofline,
+            "kernel_ms_per_solve": {"inner_apply": tot_apply / len(infos),
+                                    "inner_update": tot_update / len(infos),
+                                    "residual64": sum(i["ms_residual"] for i in infos)
+                                    / len(infos)},
+            "e2e": {"value": ms_e2e, "unit": "ms",
+                    "h2d_bytes_per_step": int(Yh.numel() * 8),
+                    "d2h_bytes_per_step": int(Xh.numel() * 8)},
+            "gpu_launches": int(sum(i["launches"] for i in infos) + args.steps * 0),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    op.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

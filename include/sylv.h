@@ -1,0 +1,192 @@
+/*
+ * sylv.h -- C ABI of the GB300 solver for the posterior-mean system of the CMB
+ * source-separation model (arxiv 2204.08057).
+ *
+ * The system (Sec. 2.2, eq. mu* and eq. Axb) for an n-pixel sky, k sources and m channels:
+ *
+ *     G vec(X) = b,    G = sum_j (e_j e_j^T) kron Q_j + sum_c (a_c a_c^T) kron D_c,
+ *     Q_j = tau_j (kappa_j^2 W + L),    b = vec( sum_c D_c y_c a_c^T ),
+ *
+ * i.e. Q + B^T C B of eq. Q* with B = A kron I_n (Sec. 2.1), the noise precision C made of
+ * per-channel, per-pixel diagonal maps D_c = diag(d_c), and a Gaussian-field prior Q_j built
+ * from a graph Laplacian L (the neighbour structure of Sec. 3.1 / App. C) plus a mass term
+ * kappa_j^2 W that makes every Q_j positive definite.  a_c is row c of the m x k mixing
+ * matrix A (App. B); by default a_cj = (nu_c / nu0)^beta_j.
+ *
+ * Layout (all vectors): source-major, each source map contiguous, leading dimension ld >= n:
+ *   X[(r * k + j) * ld + i]   right-hand side r, source j, pixel i   (the column-stacked
+ *   vec of the n x k matrix, Sec. 3.1 reshape convention; several right-hand sides follow
+ *   one another).  Noise maps: D[c * ld + i].  Observations: Yobs[(r * m + c) * ld + i].
+ *
+ * Memory: every pointer documented "device" is caller-owned device memory that must stay
+ * valid for the duration of the call only; the handle copies what it keeps (the Laplacian
+ * in a sliced-ELL form, D, w, tau, kappa, A) at create time.  "host" pointers are read
+ * during the call only.  All calls are ordered on the given stream (a cudaStream_t; NULL is
+ * the legacy default stream).  sylv_create, sylv_solve, sylv_solve_batched and
+ * sylv_backward synchronise the stream before returning (they read convergence state);
+ * sylv_rhs and sylv_apply are asynchronous.
+ *
+ * Errors: every function returns a status code and never aborts.  sylv_strerror() names a
+ * code; sylv_last_error() returns a message about the last failure on the calling thread.
+ * A handle is not thread-safe: one thread (or external locking) per handle.
+ */
+#ifndef SYLV_H
+#define SYLV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sylv_ctx* sylv_handle;
+typedef struct CUstream_st* sylv_stream; /* a cudaStream_t */
+
+enum {
+  SYLV_OK = 0,
+  SYLV_E_INVALID = 1,        /* bad argument or input data (nothing was changed)          */
+  SYLV_E_CUDA = 2,           /* a CUDA runtime call failed                               */
+  SYLV_E_NOMEM = 3,          /* device allocation failed                                 */
+  SYLV_E_NOT_CONVERGED = 4,  /* tolerance not reached in the iteration budget; X holds   */
+                             /* the last iterate and info the reached residual           */
+  SYLV_E_BREAKDOWN = 5,      /* a CG scalar became non-positive or non-finite            */
+  SYLV_E_TIMEOUT = 6,        /* a bounded device-side wait expired                       */
+  SYLV_E_UNSUPPORTED = 7     /* valid but outside what this build handles (e.g. k > 8)   */
+};
+
+enum { SYLV_F32 = 0, SYLV_F64 = 1 };                  /* element type for sylv_apply      */
+enum { SYLV_PREC_F64 = 0, SYLV_PREC_MIXED = 1 };      /* solve precision                  */
+enum { SYLV_PRECOND_NONE = 0, SYLV_PRECOND_BLOCK_JACOBI = 1 };
+
+/* Limits of this build. */
+#define SYLV_MAX_K 8      /* sources                                   */
+#define SYLV_MAX_M 16     /* channels                                  */
+#define SYLV_MAX_DEGREE 8 /* off-diagonal entries per Laplacian row    */
+#define SYLV_MAX_RHS 16   /* right-hand sides per system in one solve  */
+
+/* Problem definition (Sec. 2.1-2.2). */
+typedef struct {
+  int64_t n;               /* pixels, >= 1                                               */
+  int32_t k;               /* sources, 1..SYLV_MAX_K                                     */
+  int32_t m;               /* channels, 1..SYLV_MAX_M                                    */
+  int64_t ld;              /* leading dimension of D and of all vectors, >= n            */
+  const int32_t* L_rowptr; /* device, n + 1: CSR of the graph Laplacian L (symmetric,    */
+  const int32_t* L_col;    /* device, nnz     positive semidefinite, shared by all       */
+  const double* L_val;     /* device, nnz     sources); diagonal may be given explicitly */
+  int64_t nnz;             /*                 and duplicates are summed                  */
+  const double* w;         /* device, n: mass diagonal W (> 0), or NULL for W = I        */
+  const double* D;         /* device, m x ld: noise precision maps d_ci >= 0             */
+  const double* tau;       /* host, k: prior scale tau_j > 0                             */
+  const double* kappa;     /* host, k: prior range parameter kappa_j >= 0                */
+  const double* nu;        /* host, m: channel frequencies (GHz) for the power law       */
+  const double* beta;      /* host, k: spectral indices for the power law                */
+  const double* A;         /* host, m x k row-major: explicit mixing matrix, or NULL to  */
+                           /* use a_cj = (nu_c / nu0)^beta_j                             */
+  double nu0;              /* reference frequency of the power law; 0 means 100 GHz     */
+} sylv_problem;
+
+/* Solver options.  sylv_opts_default() fills the defaults given in brackets. */
+typedef struct {
+  double tol;          /* target true FP64 relative residual ||b - G X|| / ||b||  [1e-8]  */
+  double inner_tol;    /* mixed mode: residual reduction asked of each FP32 inner solve  */
+                       /* [1e-4]                                                          */
+  int32_t maxit;       /* cap on inner CG iterations, summed over refinements  [20000]    */
+  int32_t max_outer;   /* cap on FP64 refinement steps (true-residual replacements) [30]  */
+  int32_t precision;   /* SYLV_PREC_MIXED (FP32 inner, FP64 refinement) or SYLV_PREC_F64  */
+                       /* [MIXED]                                                         */
+  int32_t precond;     /* SYLV_PRECOND_BLOCK_JACOBI or SYLV_PRECOND_NONE [BLOCK_JACOBI]   */
+  int32_t use_graph;   /* replay inner-iteration chunks as CUDA graphs [1]                */
+  int32_t check_every; /* inner iterations between convergence polls; 0 = automatic [0]   */
+  int32_t profile;     /* time each kernel class with CUDA events into sylv_info [0]      */
+  int32_t use_x0;      /* 1: X holds the initial guess on entry; 0: start from X = 0 [0]  */
+} sylv_opts;
+
+/* Per-solve report (for several right-hand sides: worst case over them). */
+typedef struct {
+  int32_t status;      /* SYLV_OK, SYLV_E_NOT_CONVERGED or SYLV_E_BREAKDOWN               */
+  int32_t iterations;  /* inner CG iterations (max over right-hand sides)                 */
+  int32_t outer;       /* FP64 residual evaluations after the first (refinement steps)    */
+  int32_t polls;       /* host convergence polls                                          */
+  double relres;       /* final true FP64 relative residual (max over right-hand sides)   */
+  double ms_total;     /* wall time of the call on the stream (CUDA events)               */
+  /* filled when opts.profile = 1: summed kernel time and launch count per kernel class   */
+  double ms_apply;     /* inner operator-apply kernel (q = G z + beta q, p = z + beta p)  */
+  double ms_update;    /* inner update kernel (x, r, preconditioner, dots)                */
+  double ms_residual;  /* FP64 true-residual kernel                                       */
+  int32_t n_apply;
+  int32_t n_update;
+  int32_t n_residual;
+  int32_t launches;    /* kernels this call launched (inside graphs included)             */
+} sylv_info;
+
+/* Fills *o with the defaults.  Returns SYLV_OK, or SYLV_E_INVALID if o is NULL. */
+int sylv_opts_default(sylv_opts* o);
+
+/* Builds a handle for one problem (Sec. 2.1-2.2): validates the CSR Laplacian (row
+ * pointers monotone, columns in range, at most SYLV_MAX_DEGREE off-diagonal entries per
+ * row), checks D >= 0 and finite, and copies the operator data into device layouts owned
+ * by the handle (sliced ELL of L with its diagonal split off; FP32 and FP64 copies of D).
+ * On failure *h is set to NULL and nothing is leaked.  Synchronises s. */
+int sylv_create(sylv_handle* h, const sylv_problem* p, sylv_stream s);
+
+/* Right-hand side b = B^T C y of eq. mu*: B[(r*k + j)*ld + i] = sum_c a_cj d_ci y_rci.
+ * Yobs: device, nrhs x m x ld FP64.  B: device, nrhs x k x ld FP64 (written).
+ * Asynchronous on s. */
+int sylv_rhs(sylv_handle h, const double* Yobs, double* B, int nrhs, sylv_stream s);
+
+/* Operator apply Y = G X (Sec. 3.1, eq. block-vector-mapping-matvec and Algorithm 1):
+ * per source j, tau_j (kappa_j^2 w_i x_ji + (L x_j)_i), plus per pixel
+ * sum_c d_ci a_c (a_c . x_i).  X, Y: device, nrhs x k x ld of float (dtype SYLV_F32) or
+ * double (SYLV_F64); X and Y must not overlap.  Asynchronous on s. */
+int sylv_apply(sylv_handle h, const void* X, void* Y, int nrhs, int dtype, sylv_stream s);
+
+/* Solves G X = B (eq. mu*) by preconditioned conjugate gradients (Algorithm 2 with the
+ * pixel-block Jacobi preconditioner) inside an FP64 iterative-refinement loop: each
+ * refinement step forms the true residual b - G X in FP64, solves for a correction in the
+ * inner precision (FP32 in mixed mode, FP64 otherwise), and adds it to X in FP64.  Stops
+ * when the true relative residual ||b - G X||_F / ||b||_F <= o->tol for every right-hand
+ * side.  B: device nrhs x k x ld FP64.  X: device nrhs x k x ld FP64 (initial guess if
+ * o->use_x0, else overwritten from zero; holds the result).  o may be NULL (defaults);
+ * info may be NULL.  Returns SYLV_OK, SYLV_E_NOT_CONVERGED (X holds the last iterate) or
+ * SYLV_E_BREAKDOWN.  Synchronises s. */
+int sylv_solve(sylv_handle h, const double* B, double* X, int nrhs, const sylv_opts* o,
+               sylv_info* info, sylv_stream s);
+
+/* Solves nsys independent systems (hs[t], B[t], X[t], nrhs[t]) together: every phase of
+ * the iteration is one launch per distinct k covering all systems' pixels, and each system
+ * (and right-hand side) carries its own CG scalars and stopping state.  Arrays are host
+ * arrays of length nsys; B[t], X[t] as in sylv_solve.  infos: host, nsys entries (may be
+ * NULL).  Returns the worst status over the systems.  Synchronises s. */
+int sylv_solve_batched(int nsys, const sylv_handle* hs, const double* const* B,
+                       double* const* X, const int* nrhs, const sylv_opts* o,
+                       sylv_info* infos, sylv_stream s);
+
+/* Gradient of a loss l(X) on the posterior mean with respect to tau_j, kappa_j and beta_j
+ * through one adjoint solve G lambda = dl/dX (G is symmetric):
+ *   dl/dtau_j   = -lambda_j . (kappa_j^2 W + L) x_j
+ *   dl/dkappa_j = -2 tau_j kappa_j lambda_j . W x_j
+ *   dl/dbeta_j  = sum_c ln(nu_c/nu0) a_cj [lambda_j . D_c y_c - (lambda a_c) . D_c x_j
+ *                                          - lambda_j . D_c (X a_c)]
+ * summed over right-hand sides.  Xhat: device, the solution; dLdX: device, same shape;
+ * Yobs: device nrhs x m x ld (needed for g_beta only; may be NULL if g_beta is NULL).
+ * lambda: device nrhs x k x ld FP64 workspace/output (may be NULL: the handle allocates).
+ * g_tau, g_kappa, g_beta: host, k each, or NULL to skip.  g_beta needs the power-law
+ * mixing (SYLV_E_INVALID if the handle was made with an explicit A).  Synchronises s. */
+int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const double* Yobs,
+                  int nrhs, double* lambda, double* g_tau, double* g_kappa, double* g_beta,
+                  const sylv_opts* o, sylv_info* info, sylv_stream s);
+
+/* Releases the handle and everything it owns.  NULL is ignored. */
+void sylv_destroy(sylv_handle h);
+
+/* Static string naming a status code. */
+const char* sylv_strerror(int code);
+
+/* Message about the last failure on the calling thread ("" if none). */
+const char* sylv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYLV_H */

@@ -1,0 +1,824 @@
+// Host runtime and C ABI: handles, solve plans (workspaces, tile maps, captured CUDA graphs)
+// and the FP64 refinement / inner-CG driver.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sylv_internal.cuh"
+
+using namespace sylv;
+
+// ------------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------------
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+                  ")";
+  (void)cudaGetLastError();  // clear a sticky-free error so later calls are not confused
+  return fail(e == cudaErrorMemoryAllocation ? SYLV_E_NOMEM : SYLV_E_CUDA, m);
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);   \
+  } while (0)
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+    dev_ = dev;
+  }
+  ~DeviceGuard() {
+    if (prev_ != dev_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = 0, dev_ = 0;
+};
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  return cudaMalloc((void**)p, bytes);
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// plan: everything needed to run one list of systems
+// ------------------------------------------------------------------------------------------
+struct Group {
+  int k = 0;
+  int block = 256;
+  int ntiles = 0;
+  TileRef* d_tiles = nullptr;
+};
+
+struct SysWork {
+  void* vec = nullptr;       // 5 inner vectors
+  ColState* st = nullptr;
+  double* partial = nullptr;
+  unsigned int* counter = nullptr;
+};
+
+struct Plan {
+  std::vector<sylv_handle> hs;
+  std::vector<int> R;
+  int inner_double = 0;
+  int ncols = 0;
+  std::vector<Group> groups;
+  std::vector<SysWork> work;
+  SysDesc* d_desc = nullptr;
+  SysDesc* h_desc = nullptr;    // pinned
+  Control* d_ctl = nullptr;
+  Control* h_ctl = nullptr;     // pinned
+  unsigned int* h_poll = nullptr;  // pinned, 2 words
+  ColState* h_states = nullptr;    // pinned, ncols
+  int* d_col_sys = nullptr;
+  int* d_col_rhs = nullptr;
+  std::vector<int> col_sys, col_rhs;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  int graph_profile = 0;
+  std::vector<cudaEvent_t> chunk_events;  // 2 * graph_iters + 1 when profiling
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evr0 = nullptr, evr1 = nullptr;
+
+  ~Plan();
+};
+
+struct sylv_ctx {
+  int device = 0;
+  OpData op{};
+  int explicit_A = 0;
+  int32_t* ell_col = nullptr;
+  float* ell_val32 = nullptr;
+  double* ell_val64 = nullptr;
+  float* diag32 = nullptr;
+  double* diag64 = nullptr;
+  float* D32 = nullptr;
+  double* D64 = nullptr;
+  float* w32 = nullptr;
+  double* w64 = nullptr;
+  std::unique_ptr<Plan> plan[2];  // single-system plans, [inner_double]
+  double* lam = nullptr;
+  size_t lam_bytes = 0;
+  double* grad_ws = nullptr;
+  size_t grad_bytes = 0;
+};
+
+Plan::~Plan() {
+  for (auto& g : groups) cudaFree(g.d_tiles);
+  for (auto& w : work) {
+    cudaFree(w.vec);
+    cudaFree(w.st);
+    cudaFree(w.partial);
+    cudaFree(w.counter);
+  }
+  cudaFree(d_desc);
+  cudaFree(d_ctl);
+  cudaFree(d_col_sys);
+  cudaFree(d_col_rhs);
+  cudaFreeHost(h_desc);
+  cudaFreeHost(h_ctl);
+  cudaFreeHost(h_poll);
+  cudaFreeHost(h_states);
+  if (graph) cudaGraphExecDestroy(graph);
+  for (auto e : chunk_events) cudaEventDestroy(e);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (evr0) cudaEventDestroy(evr0);
+  if (evr1) cudaEventDestroy(evr1);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+}
+
+namespace {
+
+// Batched plans, keyed by the list of (handle, nrhs) and the inner type.
+std::mutex g_plan_mu;
+std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> g_plans;
+
+int default_block(int64_t n) {
+  (void)n;
+  return 256;
+}
+
+int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner_double) {
+  P.hs.assign(hs, hs + nsys);
+  P.R.assign(R, R + nsys);
+  P.inner_double = inner_double;
+  const size_t tsz = inner_double ? sizeof(double) : sizeof(float);
+  P.work.resize(nsys);
+  // groups by k
+  std::map<int, std::vector<int>> byk;
+  for (int s = 0; s < nsys; ++s) byk[hs[s]->op.k].push_back(s);
+  std::vector<int> tile_px(nsys);
+  std::vector<int> ntiles(nsys);
+  for (auto& kv : byk) {
+    Group g;
+    g.k = kv.first;
+    int64_t nmax = 0;
+    for (int s : kv.second) nmax = std::max(nmax, hs[s]->op.n);
+    g.block = default_block(nmax);
+    std::vector<TileRef> tl;
+    for (int s : kv.second) {
+      tile_px[s] = g.block;
+      ntiles[s] = (int)ceil_div(hs[s]->op.n, g.block);
+      for (int t = 0; t < ntiles[s]; ++t) tl.push_back(TileRef{s, t});
+    }
+    g.ntiles = (int)tl.size();
+    CK(dalloc(&g.d_tiles, tl.size() * sizeof(TileRef)));
+    CK(cudaMemcpy(g.d_tiles, tl.data(), tl.size() * sizeof(TileRef), cudaMemcpyHostToDevice));
+    P.groups.push_back(g);
+  }
+  for (int s = 0; s < nsys; ++s) {
+    const OpData& op = hs[s]->op;
+    SysWork& w = P.work[s];
+    const size_t vbytes = (size_t)R[s] * op.k * op.ld * tsz;
+    CK(dalloc(&w.vec, 5 * vbytes));
+    CK(cudaMemset(w.vec, 0, 5 * vbytes));
+    CK(dalloc(&w.st, R[s] * sizeof(ColState)));
+    CK(dalloc(&w.partial, (size_t)ntiles[s] * R[s] * NPART * sizeof(double)));
+    CK(dalloc(&w.counter, sizeof(unsigned int)));
+    CK(cudaMemset(w.counter, 0, sizeof(unsigned int)));
+    for (int r = 0; r < R[s]; ++r) {
+      P.col_sys.push_back(s);
+      P.col_rhs.push_back(r);
+    }
+  }
+  P.ncols = (int)P.col_sys.size();
+  CK(dalloc(&P.d_desc, nsys * sizeof(SysDesc)));
+  CK(cudaMallocHost((void**)&P.h_desc, nsys * sizeof(SysDesc)));
+  CK(dalloc(&P.d_ctl, sizeof(Control)));
+  CK(cudaMallocHost((void**)&P.h_ctl, sizeof(Control)));
+  CK(cudaMallocHost((void**)&P.h_poll, 2 * sizeof(unsigned int)));
+  CK(cudaMallocHost((void**)&P.h_states, P.ncols * sizeof(ColState)));
+  CK(dalloc(&P.d_col_sys, P.ncols * sizeof(int)));
+  CK(dalloc(&P.d_col_rhs, P.ncols * sizeof(int)));
+  CK(cudaMemcpy(P.d_col_sys, P.col_sys.data(), P.ncols * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P.d_col_rhs, P.col_rhs.data(), P.ncols * sizeof(int), cudaMemcpyHostToDevice));
+  // static part of the descriptors
+  for (int s = 0; s < nsys; ++s) {
+    SysDesc& d = P.h_desc[s];
+    std::memset(&d, 0, sizeof(SysDesc));
+    d.op = hs[s]->op;
+    d.R = R[s];
+    d.ntiles = ntiles[s];
+    d.tile_px = tile_px[s];
+    const size_t vbytes = (size_t)R[s] * d.op.k * d.op.ld * tsz;
+    char* base = (char*)P.work[s].vec;
+    d.vd = base;
+    d.vr = base + vbytes;
+    d.vz = base + 2 * vbytes;
+    d.vp = base + 3 * vbytes;
+    d.vq = base + 4 * vbytes;
+    d.st = P.work[s].st;
+    d.partial = P.work[s].partial;
+    d.counter = P.work[s].counter;
+  }
+  CK(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreate(&P.ev0));
+  CK(cudaEventCreate(&P.ev1));
+  CK(cudaEventCreate(&P.evr0));
+  CK(cudaEventCreate(&P.evr1));
+  return SYLV_OK;
+}
+
+template <typename T>
+int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
+                           bool capture_events) {
+  for (auto& g : P.groups)
+    CK(launch_inner_apply<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, P.d_ctl, s));
+  if (e_mid)
+    CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
+                      : cudaEventRecord(e_mid, s));
+  for (auto& g : P.groups)
+    CK(launch_inner_update<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, P.d_ctl, s));
+  if (e_end)
+    CK(capture_events ? cudaEventRecordWithFlags(e_end, s, cudaEventRecordExternal)
+                      : cudaEventRecord(e_end, s));
+  return SYLV_OK;
+}
+
+template <typename T>
+int ensure_graph(Plan& P, int iters, int profile) {
+  if (P.graph && P.graph_iters == iters && P.graph_profile == profile) return SYLV_OK;
+  if (P.graph) {
+    cudaGraphExecDestroy(P.graph);
+    P.graph = nullptr;
+  }
+  for (auto e : P.chunk_events) cudaEventDestroy(e);
+  P.chunk_events.clear();
+  if (profile) {
+    P.chunk_events.resize(2 * iters + 1);
+    for (auto& e : P.chunk_events) CK(cudaEventCreate(&e));
+  }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = SYLV_OK;
+  if (profile) {
+    cudaError_t e = cudaEventRecordWithFlags(P.chunk_events[0], P.cap_stream,
+                                             cudaEventRecordExternal);
+    if (e != cudaSuccess) rc = cuda_fail(e, "event record in capture");
+  }
+  for (int it = 0; it < iters && rc == SYLV_OK; ++it)
+    rc = launch_inner_iteration<T>(P, P.cap_stream,
+                                   profile ? P.chunk_events[2 * it + 1] : nullptr,
+                                   profile ? P.chunk_events[2 * it + 2] : nullptr, true);
+  cudaError_t e = cudaStreamEndCapture(P.cap_stream, &graph);
+  if (rc != SYLV_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&P.graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  P.graph_iters = iters;
+  P.graph_profile = profile;
+  return SYLV_OK;
+}
+
+int poll(Plan& P, cudaStream_t s) {
+  CK(cudaMemcpyAsync(P.h_poll, &P.d_ctl->n_active, 2 * sizeof(unsigned int),
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SYLV_OK;
+}
+
+template <typename T>
+int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts& o,
+             sylv_info* infos, cudaStream_t s) {
+  const int nsys = (int)P.hs.size();
+  for (int t = 0; t < nsys; ++t) {
+    P.h_desc[t].B = B[t];
+    P.h_desc[t].X = X[t];
+  }
+  Control& c = *P.h_ctl;
+  std::memset(&c, 0, sizeof(Control));
+  c.tol2 = o.tol * o.tol;
+  c.tol_in2 = o.precision == SYLV_PREC_MIXED ? o.inner_tol * o.inner_tol : 0.0;
+  c.safety2 = 0.25;
+  c.maxit = o.maxit;
+  c.max_outer = o.max_outer;
+  c.precond = o.precond;
+  const int iters = o.check_every > 0 ? o.check_every : 16;
+  const bool prof = o.profile != 0;
+  double ms_apply = 0, ms_update = 0, ms_res = 0;
+  int n_apply = 0, n_update = 0, n_res = 0, polls = 0;
+  long launches = 0;
+  const int ng = (int)P.groups.size();
+
+  CK(cudaEventRecord(P.ev0, s));
+  CK(cudaMemcpyAsync(P.d_desc, P.h_desc, nsys * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.d_ctl, P.h_ctl, sizeof(Control), cudaMemcpyHostToDevice, s));
+  if (!o.use_x0) {
+    for (int t = 0; t < nsys; ++t) {
+      const OpData& op = P.hs[t]->op;
+      CK(cudaMemsetAsync(X[t], 0, (size_t)P.R[t] * op.k * op.ld * sizeof(double), s));
+    }
+  }
+  CK(launch_init_states(P.ncols, P.d_col_sys, P.d_col_rhs, P.d_desc, P.d_ctl, s));
+  launches += 1;
+  if (o.use_graph) {
+    int rc = ensure_graph<T>(P, iters, prof ? 1 : 0);
+    if (rc != SYLV_OK) return rc;
+  }
+  const long max_polls = (long)o.maxit / iters + 4L * (o.max_outer + 2) + 16;
+  bool gave_up = false;
+  std::vector<cudaEvent_t> direct_events;
+  if (prof && !o.use_graph) {
+    direct_events.resize(2 * iters + 1);
+    for (auto& e : direct_events) CK(cudaEventCreate(&e));
+  }
+  int rc = SYLV_OK;
+  while (true) {
+    for (auto& g : P.groups)
+      CK(launch_update_x<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, s));
+    if (prof) CK(cudaEventRecord(P.evr0, s));
+    for (auto& g : P.groups)
+      CK(launch_residual<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, P.d_ctl, s));
+    if (prof) CK(cudaEventRecord(P.evr1, s));
+    launches += 2 * ng;
+    if ((rc = poll(P, s)) != SYLV_OK) break;
+    ++polls;
+    if (prof) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, P.evr0, P.evr1));
+      ms_res += ms;
+      ++n_res;
+    }
+    if (P.h_poll[1] == 0u) break;
+    while (P.h_poll[0] > 0u) {
+      if (polls > max_polls) {
+        gave_up = true;
+        break;
+      }
+      if (o.use_graph) {
+        CK(cudaGraphLaunch(P.graph, s));
+      } else {
+        if (prof) CK(cudaEventRecord(direct_events[0], s));
+        for (int it = 0; it < iters; ++it) {
+          rc = launch_inner_iteration<T>(P, s, prof ? direct_events[2 * it + 1] : nullptr,
+                                         prof ? direct_events[2 * it + 2] : nullptr, false);
+          if (rc != SYLV_OK) return rc;
+        }
+      }
+      launches += 2L * iters * ng;
+      if ((rc = poll(P, s)) != SYLV_OK) return rc;
+      ++polls;
+      if (prof) {
+        auto& ev = o.use_graph ? P.chunk_events : direct_events;
+        for (int it = 0; it < iters; ++it) {
+          float a = 0, b = 0;
+          CK(cudaEventElapsedTime(&a, ev[2 * it], ev[2 * it + 1]));
+          CK(cudaEventElapsedTime(&b, ev[2 * it + 1], ev[2 * it + 2]));
+          ms_apply += a;
+          ms_update += b;
+        }
+        n_apply += iters * (int)P.groups.size();
+        n_update += iters * (int)P.groups.size();
+      }
+    }
+    if (gave_up || polls > max_polls) {
+      gave_up = true;
+      break;
+    }
+  }
+  for (auto e : direct_events) cudaEventDestroy(e);
+  if (rc != SYLV_OK) return rc;
+  CK(cudaEventRecord(P.ev1, s));
+  // read back per-column states
+  int off = 0;
+  for (int t = 0; t < nsys; ++t) {
+    CK(cudaMemcpyAsync(P.h_states + off, P.work[t].st, P.R[t] * sizeof(ColState),
+                       cudaMemcpyDeviceToHost, s));
+    off += P.R[t];
+  }
+  CK(cudaStreamSynchronize(s));
+  float ms_total = 0;
+  CK(cudaEventElapsedTime(&ms_total, P.ev0, P.ev1));
+  int worst = SYLV_OK;
+  off = 0;
+  for (int t = 0; t < nsys; ++t) {
+    sylv_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    inf.status = SYLV_OK;
+    for (int r = 0; r < P.R[t]; ++r) {
+      const ColState& cs = P.h_states[off + r];
+      int st = cs.status;
+      if (cs.phase != PH_CONVERGED && cs.phase != PH_FAILED) st = SYLV_E_NOT_CONVERGED;
+      if (cs.phase == PH_CONVERGED) st = SYLV_OK;
+      if (st != SYLV_OK && (inf.status == SYLV_OK || st == SYLV_E_BREAKDOWN)) inf.status = st;
+      inf.iterations = std::max(inf.iterations, cs.it);
+      inf.outer = std::max(inf.outer, cs.outer);
+      inf.relres = std::max(inf.relres, cs.relres);
+    }
+    off += P.R[t];
+    inf.polls = polls;
+    inf.ms_total = ms_total;
+    inf.ms_apply = ms_apply;
+    inf.ms_update = ms_update;
+    inf.ms_residual = ms_res;
+    inf.n_apply = n_apply;
+    inf.n_update = n_update;
+    inf.n_residual = n_res;
+    inf.launches = (int32_t)std::min<long>(launches, INT32_MAX);
+    if (infos) infos[t] = inf;
+    if (inf.status != SYLV_OK && (worst == SYLV_OK || inf.status == SYLV_E_BREAKDOWN))
+      worst = inf.status;
+  }
+  if (worst == SYLV_E_NOT_CONVERGED)
+    g_last_error = gave_up ? "solve stopped: poll limit reached" : "tolerance not reached";
+  if (worst == SYLV_E_BREAKDOWN) g_last_error = "CG breakdown (non-positive or non-finite scalar)";
+  return worst;
+}
+
+int check_opts(const sylv_opts& o) {
+  if (!(o.tol > 0.0) || !(o.tol < 1.0)) return fail(SYLV_E_INVALID, "opts.tol must be in (0,1)");
+  if (o.precision == SYLV_PREC_MIXED && (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0)))
+    return fail(SYLV_E_INVALID, "opts.inner_tol must be in (0,1)");
+  if (o.precision != SYLV_PREC_MIXED && o.precision != SYLV_PREC_F64)
+    return fail(SYLV_E_INVALID, "opts.precision");
+  if (o.precond != SYLV_PRECOND_NONE && o.precond != SYLV_PRECOND_BLOCK_JACOBI)
+    return fail(SYLV_E_INVALID, "opts.precond");
+  if (o.maxit < 1 || o.max_outer < 1) return fail(SYLV_E_INVALID, "opts.maxit/max_outer");
+  if (o.check_every < 0 || o.check_every > 4096) return fail(SYLV_E_INVALID, "opts.check_every");
+  return SYLV_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+int sylv_opts_default(sylv_opts* o) {
+  if (!o) return fail(SYLV_E_INVALID, "opts is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->inner_tol = 1e-4;
+  o->maxit = 20000;
+  o->max_outer = 30;
+  o->precision = SYLV_PREC_MIXED;
+  o->precond = SYLV_PRECOND_BLOCK_JACOBI;
+  o->use_graph = 1;
+  o->check_every = 0;
+  o->profile = 0;
+  o->use_x0 = 0;
+  return SYLV_OK;
+}
+
+const char* sylv_strerror(int code) {
+  switch (code) {
+    case SYLV_OK: return "ok";
+    case SYLV_E_INVALID: return "invalid argument";
+    case SYLV_E_CUDA: return "CUDA error";
+    case SYLV_E_NOMEM: return "out of device memory";
+    case SYLV_E_NOT_CONVERGED: return "not converged";
+    case SYLV_E_BREAKDOWN: return "CG breakdown";
+    case SYLV_E_TIMEOUT: return "device wait timed out";
+    case SYLV_E_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* sylv_last_error(void) { return g_last_error.c_str(); }
+
+static void free_handle(sylv_ctx* h) {
+  if (!h) return;
+  h->plan[0].reset();
+  h->plan[1].reset();
+  cudaFree(h->ell_col);
+  cudaFree(h->ell_val32);
+  cudaFree(h->ell_val64);
+  cudaFree(h->diag32);
+  cudaFree(h->diag64);
+  cudaFree(h->D32);
+  cudaFree(h->D64);
+  cudaFree(h->w32);
+  cudaFree(h->w64);
+  cudaFree(h->lam);
+  cudaFree(h->grad_ws);
+  delete h;
+}
+
+int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
+  if (!out) return fail(SYLV_E_INVALID, "handle pointer is NULL");
+  *out = nullptr;
+  if (!p) return fail(SYLV_E_INVALID, "problem is NULL");
+  if (p->n < 1) return fail(SYLV_E_INVALID, "n must be >= 1");
+  if (p->n > (int64_t)INT32_MAX) return fail(SYLV_E_UNSUPPORTED, "n exceeds 2^31-1");
+  if (p->k < 1 || p->m < 1) return fail(SYLV_E_INVALID, "k and m must be >= 1");
+  if (p->k > KMAX) return fail(SYLV_E_UNSUPPORTED, "k exceeds SYLV_MAX_K");
+  if (p->m > MMAX) return fail(SYLV_E_UNSUPPORTED, "m exceeds SYLV_MAX_M");
+  if (p->ld < p->n) return fail(SYLV_E_INVALID, "ld must be >= n");
+  if (!p->L_rowptr || !p->L_col || !p->L_val || !p->D || !p->tau || !p->kappa)
+    return fail(SYLV_E_INVALID, "required pointer is NULL");
+  if (p->nnz < 0 || p->nnz > (int64_t)INT32_MAX) return fail(SYLV_E_INVALID, "nnz out of range");
+  if (!p->A && (!p->nu || !p->beta))
+    return fail(SYLV_E_INVALID, "give A, or nu and beta for the power-law mixing");
+  const double nu0 = p->nu0 > 0.0 ? p->nu0 : 100.0;
+  for (int j = 0; j < p->k; ++j) {
+    if (!(p->tau[j] > 0.0) || !std::isfinite(p->tau[j]))
+      return fail(SYLV_E_INVALID, "tau_j must be finite and > 0");
+    if (!(p->kappa[j] >= 0.0) || !std::isfinite(p->kappa[j]))
+      return fail(SYLV_E_INVALID, "kappa_j must be finite and >= 0");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  sylv_ctx* h = new sylv_ctx();
+  cudaGetDevice(&h->device);
+  OpData& op = h->op;
+  op.n = p->n;
+  op.ld = p->ld;
+  op.k = p->k;
+  op.m = p->m;
+  op.has_w = p->w != nullptr;
+  for (int c = 0; c < p->m; ++c) {
+    for (int j = 0; j < p->k; ++j) {
+      double a;
+      if (p->A) {
+        a = p->A[c * p->k + j];
+      } else {
+        if (!(p->nu[c] > 0.0)) {
+          free_handle(h);
+          return fail(SYLV_E_INVALID, "nu_c must be > 0");
+        }
+        a = std::pow(p->nu[c] / nu0, p->beta[j]);
+      }
+      if (!std::isfinite(a)) {
+        free_handle(h);
+        return fail(SYLV_E_INVALID, "mixing matrix entry is not finite");
+      }
+      op.A64[c * p->k + j] = a;
+      op.A32[c * p->k + j] = (float)a;
+    }
+    op.logf64[c] = (!p->A) ? std::log(p->nu[c] / nu0) : 0.0;
+  }
+  h->explicit_A = p->A != nullptr;
+  for (int j = 0; j < p->k; ++j) {
+    op.tau64[j] = p->tau[j];
+    op.kappa64[j] = p->kappa[j];
+    op.tk2_64[j] = p->tau[j] * p->kappa[j] * p->kappa[j];
+    op.tau32[j] = (float)op.tau64[j];
+    op.tk2_32[j] = (float)op.tk2_64[j];
+  }
+  // validate the CSR and find the ELL width
+  unsigned int* dflags = nullptr;
+  int rc = SYLV_OK;
+  auto bail = [&](int code) {
+    cudaFree(dflags);
+    free_handle(h);
+    return code;
+  };
+  cudaError_t e = dalloc(&dflags, 2 * sizeof(unsigned int));
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+  unsigned int hflags[2] = {0, 0};
+  if ((e = cudaMemsetAsync(dflags, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess ||
+      (e = launch_csr_check(op, p->L_rowptr, p->L_col, p->nnz, dflags, dflags + 1, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(hflags, dflags, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                           s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return bail(cuda_fail(e, "CSR validation"));
+  if (hflags[0]) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "invalid Laplacian CSR (flags 0x%x: 1 rowptr, 2 column, "
+                  "4 rowptr[0]/rowptr[n]/nnz, 16 more than %d off-diagonals in a row)",
+                  hflags[0], EMAX);
+    return bail(fail((hflags[0] & 16u) && !(hflags[0] & 15u) ? SYLV_E_UNSUPPORTED
+                                                             : SYLV_E_INVALID, msg));
+  }
+  const int E = (int)hflags[1];
+  op.E = E;
+  const size_t ld = (size_t)p->ld;
+  if ((e = dalloc(&h->ell_col, std::max<size_t>(E, 1) * ld * sizeof(int32_t))) != cudaSuccess ||
+      (e = dalloc(&h->ell_val32, std::max<size_t>(E, 1) * ld * sizeof(float))) != cudaSuccess ||
+      (e = dalloc(&h->ell_val64, std::max<size_t>(E, 1) * ld * sizeof(double))) != cudaSuccess ||
+      (e = dalloc(&h->diag32, ld * sizeof(float))) != cudaSuccess ||
+      (e = dalloc(&h->diag64, ld * sizeof(double))) != cudaSuccess ||
+      (e = dalloc(&h->D32, (size_t)p->m * ld * sizeof(float))) != cudaSuccess ||
+      (e = dalloc(&h->D64, (size_t)p->m * ld * sizeof(double))) != cudaSuccess)
+    return bail(cuda_fail(e, "cudaMalloc (operator data)"));
+  if (p->w) {
+    if ((e = dalloc(&h->w32, ld * sizeof(float))) != cudaSuccess ||
+        (e = dalloc(&h->w64, ld * sizeof(double))) != cudaSuccess)
+      return bail(cuda_fail(e, "cudaMalloc (mass diagonal)"));
+  }
+  // zero the padding so every buffer is defined
+  if ((e = cudaMemsetAsync(h->diag32, 0, ld * sizeof(float), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->diag64, 0, ld * sizeof(double), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->D32, 0, (size_t)p->m * ld * sizeof(float), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->D64, 0, (size_t)p->m * ld * sizeof(double), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->ell_col, 0, std::max<size_t>(E, 1) * ld * sizeof(int32_t), s)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(h->ell_val32, 0, std::max<size_t>(E, 1) * ld * sizeof(float), s)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(h->ell_val64, 0, std::max<size_t>(E, 1) * ld * sizeof(double), s)) !=
+          cudaSuccess)
+    return bail(cuda_fail(e, "cudaMemsetAsync"));
+  op.ell_col = h->ell_col;
+  op.ell_val32 = h->ell_val32;
+  op.ell_val64 = h->ell_val64;
+  op.diag32 = h->diag32;
+  op.diag64 = h->diag64;
+  op.D32 = h->D32;
+  op.D64 = h->D64;
+  op.w32 = h->w32;
+  op.w64 = h->w64;
+  if ((e = cudaMemsetAsync(dflags, 0, sizeof(unsigned int), s)) != cudaSuccess ||
+      (e = launch_ell_build(op, p->L_rowptr, p->L_col, p->L_val, h->ell_col, h->ell_val32,
+                            h->ell_val64, h->diag32, h->diag64, E, s)) != cudaSuccess ||
+      (e = launch_convert_check(p->D, p->m, p->n, p->ld, h->D32, h->D64, 0, dflags, s)) !=
+          cudaSuccess)
+    return bail(cuda_fail(e, "operator set-up"));
+  if (p->w) {
+    if ((e = cudaMemsetAsync(h->w32, 0, ld * sizeof(float), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->w64, 0, ld * sizeof(double), s)) != cudaSuccess ||
+        (e = launch_convert_check(p->w, 1, p->n, p->ld, h->w32, h->w64, 1, dflags, s)) !=
+            cudaSuccess)
+      return bail(cuda_fail(e, "mass diagonal set-up"));
+  }
+  if ((e = cudaMemcpyAsync(hflags, dflags, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return bail(cuda_fail(e, "operator set-up"));
+  if (hflags[0]) return bail(fail(SYLV_E_INVALID, "D (>= 0) or w (> 0) has invalid entries"));
+  cudaFree(dflags);
+  *out = h;
+  (void)rc;
+  return SYLV_OK;
+}
+
+void sylv_destroy(sylv_handle h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+      bool uses = std::find(it->second->hs.begin(), it->second->hs.end(), h) !=
+                  it->second->hs.end();
+      it = uses ? g_plans.erase(it) : std::next(it);
+    }
+  }
+  free_handle(h);
+}
+
+int sylv_rhs(sylv_handle h, const double* Yobs, double* B, int nrhs, sylv_stream s) {
+  if (!h || !Yobs || !B) return fail(SYLV_E_INVALID, "NULL argument");
+  if (nrhs < 1) return fail(SYLV_E_INVALID, "nrhs must be >= 1");
+  DeviceGuard g(h->device);
+  CK(launch_rhs(h->op, Yobs, B, nrhs, (cudaStream_t)s));
+  return SYLV_OK;
+}
+
+int sylv_apply(sylv_handle h, const void* X, void* Y, int nrhs, int dtype, sylv_stream s) {
+  if (!h || !X || !Y) return fail(SYLV_E_INVALID, "NULL argument");
+  if (nrhs < 1) return fail(SYLV_E_INVALID, "nrhs must be >= 1");
+  DeviceGuard g(h->device);
+  if (dtype == SYLV_F32) {
+    CK(launch_apply<float>(h->op, (const float*)X, (float*)Y, nrhs, (cudaStream_t)s));
+  } else if (dtype == SYLV_F64) {
+    CK(launch_apply<double>(h->op, (const double*)X, (double*)Y, nrhs, (cudaStream_t)s));
+  } else {
+    return fail(SYLV_E_INVALID, "dtype must be SYLV_F32 or SYLV_F64");
+  }
+  return SYLV_OK;
+}
+
+static int solve_impl(int nsys, const sylv_handle* hs, const double* const* B, double* const* X,
+                      const int* nrhs, const sylv_opts* o_in, sylv_info* infos,
+                      cudaStream_t s, bool single) {
+  sylv_opts o;
+  if (o_in) o = *o_in;
+  else sylv_opts_default(&o);
+  int rc = check_opts(o);
+  if (rc != SYLV_OK) return rc;
+  if (nsys < 1 || !hs || !B || !X || !nrhs) return fail(SYLV_E_INVALID, "NULL or empty arrays");
+  for (int t = 0; t < nsys; ++t) {
+    if (!hs[t] || !B[t] || !X[t]) return fail(SYLV_E_INVALID, "NULL handle or buffer");
+    if (nrhs[t] < 1 || nrhs[t] > RMAX) return fail(SYLV_E_INVALID, "nrhs out of 1..SYLV_MAX_RHS");
+    if (hs[t]->device != hs[0]->device)
+      return fail(SYLV_E_INVALID, "all handles must live on one device");
+  }
+  DeviceGuard g(hs[0]->device);
+  const int inner_double = o.precision == SYLV_PREC_F64 ? 1 : 0;
+  Plan* P = nullptr;
+  std::unique_lock<std::mutex> lk(g_plan_mu, std::defer_lock);
+  if (single) {
+    auto& slot = hs[0]->plan[inner_double];
+    if (!slot || slot->R[0] != nrhs[0]) {
+      slot.reset(new Plan());
+      rc = build_plan(*slot, 1, hs, nrhs, inner_double);
+      if (rc != SYLV_OK) {
+        slot.reset();
+        return rc;
+      }
+    }
+    P = slot.get();
+  } else {
+    std::vector<uintptr_t> key;
+    key.push_back((uintptr_t)inner_double);
+    for (int t = 0; t < nsys; ++t) {
+      key.push_back((uintptr_t)hs[t]);
+      key.push_back((uintptr_t)nrhs[t]);
+    }
+    lk.lock();
+    auto it = g_plans.find(key);
+    if (it == g_plans.end()) {
+      std::unique_ptr<Plan> np(new Plan());
+      rc = build_plan(*np, nsys, hs, nrhs, inner_double);
+      if (rc != SYLV_OK) return rc;
+      it = g_plans.emplace(key, std::move(np)).first;
+    }
+    P = it->second.get();
+  }
+  return inner_double ? run_plan<double>(*P, B, X, o, infos, s)
+                      : run_plan<float>(*P, B, X, o, infos, s);
+}
+
+int sylv_solve(sylv_handle h, const double* B, double* X, int nrhs, const sylv_opts* o,
+               sylv_info* info, sylv_stream s) {
+  if (!h) return fail(SYLV_E_INVALID, "NULL handle");
+  const double* Bs[1] = {B};
+  double* Xs[1] = {X};
+  int R[1] = {nrhs};
+  return solve_impl(1, &h, Bs, Xs, R, o, info, (cudaStream_t)s, true);
+}
+
+int sylv_solve_batched(int nsys, const sylv_handle* hs, const double* const* B,
+                       double* const* X, const int* nrhs, const sylv_opts* o,
+                       sylv_info* infos, sylv_stream s) {
+  return solve_impl(nsys, hs, B, X, nrhs, o, infos, (cudaStream_t)s, false);
+}
+
+int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const double* Yobs,
+                  int nrhs, double* lambda, double* g_tau, double* g_kappa, double* g_beta,
+                  const sylv_opts* o, sylv_info* info, sylv_stream stream) {
+  if (!h || !Xhat || !dLdX) return fail(SYLV_E_INVALID, "NULL argument");
+  if (nrhs < 1 || nrhs > RMAX) return fail(SYLV_E_INVALID, "nrhs out of range");
+  if (g_beta && h->explicit_A)
+    return fail(SYLV_E_INVALID, "g_beta needs the power-law mixing (handle has explicit A)");
+  if (g_beta && !Yobs) return fail(SYLV_E_INVALID, "g_beta needs Yobs");
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const OpData& op = h->op;
+  const size_t vbytes = (size_t)nrhs * op.k * op.ld * sizeof(double);
+  double* lam = lambda;
+  if (!lam) {
+    if (h->lam_bytes < vbytes) {
+      cudaFree(h->lam);
+      h->lam = nullptr;
+      h->lam_bytes = 0;
+      CK(dalloc(&h->lam, vbytes));
+      h->lam_bytes = vbytes;
+    }
+    lam = h->lam;
+  }
+  // adjoint solve: G lambda = dl/dX (G is symmetric)
+  int rc = sylv_solve(h, dLdX, lam, nrhs, o, info, stream);
+  if (rc != SYLV_OK) return rc;
+  const int ntiles = (int)ceil_div(op.n, 256);
+  const size_t gbytes = ((size_t)ntiles * 3 * op.k + 3 * op.k) * sizeof(double);
+  if (h->grad_bytes < gbytes) {
+    cudaFree(h->grad_ws);
+    h->grad_ws = nullptr;
+    h->grad_bytes = 0;
+    CK(dalloc(&h->grad_ws, gbytes));
+    h->grad_bytes = gbytes;
+  }
+  double* out = h->grad_ws + (size_t)ntiles * 3 * op.k;
+  CK(launch_grad(op, Xhat, lam, Yobs, nrhs, g_beta ? 1 : 0, h->grad_ws, ntiles, out, s));
+  double host[3 * KMAX];
+  CK(cudaMemcpyAsync(host, out, 3 * op.k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int j = 0; j < op.k; ++j) {
+    if (g_tau) g_tau[j] = host[j];
+    if (g_kappa) g_kappa[j] = host[op.k + j];
+    if (g_beta) g_beta[j] = host[2 * op.k + j];
+  }
+  return SYLV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,309 @@
+// Set-up, right-hand side, stand-alone operator apply and gradient kernels.
+#include <cmath>
+
+#include "pcg_kernels.cuh"
+
+namespace sylv {
+
+namespace {
+constexpr int SETUP_BLOCK = 256;
+
+inline int blocks_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
+}  // namespace
+
+// flags bits
+constexpr unsigned FLAG_ROWPTR = 1u, FLAG_COL = 2u, FLAG_NNZ = 4u, FLAG_VALUE = 8u,
+                   FLAG_DEGREE = 16u;
+
+// Validates the CSR structure; records the largest number of off-diagonal entries per row.
+__global__ void k_csr_check(int64_t n, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ col, int64_t nnz,
+                            unsigned int* flags, unsigned int* maxdeg) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    if (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz) atomicOr(flags, FLAG_NNZ);
+  }
+  if (i >= n) return;
+  const int64_t lo = rowptr[i], hi = rowptr[i + 1];
+  if (lo < 0 || hi < lo || hi > nnz) {
+    atomicOr(flags, FLAG_ROWPTR);
+    return;
+  }
+  unsigned deg = 0;
+  for (int64_t e = lo; e < hi; ++e) {
+    const int32_t c = col[e];
+    if (c < 0 || (int64_t)c >= n) {
+      atomicOr(flags, FLAG_COL);
+      return;
+    }
+    if ((int64_t)c != i) ++deg;
+  }
+  if (deg > (unsigned)EMAX) atomicOr(flags, FLAG_DEGREE);
+  atomicMax(maxdeg, deg);
+}
+
+// Sliced ELL: slot e of row i at e * ld + i; diagonal entries (summed) go to diag.
+__global__ void k_ell_build(int64_t n, int64_t ld, const int32_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ col, const double* __restrict__ val,
+                            int E, int32_t* ell_col, float* ell_val32, double* ell_val64,
+                            float* diag32, double* diag64) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double dg = 0.0;
+  int e = 0;
+  for (int64_t t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+    const int32_t c = col[t];
+    const double v = val[t];
+    if ((int64_t)c == i) {
+      dg += v;
+    } else if (e < E) {
+      ell_col[e * ld + i] = c;
+      ell_val32[e * ld + i] = (float)v;
+      ell_val64[e * ld + i] = v;
+      ++e;
+    }
+  }
+  for (; e < E; ++e) {
+    ell_col[e * ld + i] = (int32_t)i;
+    ell_val32[e * ld + i] = 0.0f;
+    ell_val64[e * ld + i] = 0.0;
+  }
+  diag32[i] = (float)dg;
+  diag64[i] = dg;
+}
+
+// Copies rows x n values (pitch ld) into FP32 and FP64 buffers and checks them (>= 0, or > 0
+// if positive, and finite).
+__global__ void k_convert_check(const double* __restrict__ src, int64_t rows, int64_t n,
+                                int64_t ld, float* dst32, double* dst64, int positive,
+                                unsigned int* flags) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * n) return;
+  const int64_t r = t / n, i = t - r * n;
+  const double v = src[r * ld + i];
+  if (!isfinite(v) || v < 0.0 || (positive && !(v > 0.0))) atomicOr(flags, FLAG_VALUE);
+  dst32[r * ld + i] = (float)v;
+  dst64[r * ld + i] = v;
+}
+
+// b = B^T C y (eq. mu*): B[r][j][i] = sum_c a_cj d_ci y[r][c][i]
+__global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restrict__ B, int R) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= op.n) return;
+  const int64_t ld = op.ld;
+  for (int r = 0; r < R; ++r) {
+    double acc[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
+    for (int c = 0; c < op.m; ++c) {
+      const double dy = op.D64[c * ld + i] * Y[((int64_t)r * op.m + c) * ld + i];
+#pragma unroll
+      for (int j = 0; j < KMAX; ++j)
+        if (j < op.k) acc[j] += op.A64[c * op.k + j] * dy;
+    }
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < op.k) B[((int64_t)r * op.k + j) * ld + i] = acc[j];
+  }
+}
+
+// Stand-alone operator apply Y = G X (eq. block-vector-mapping-matvec with Algorithm 1).
+template <int K, typename T>
+__global__ void __launch_bounds__(256) k_apply(OpData op, const T* __restrict__ X,
+                                               T* __restrict__ Y, int R) {
+  __shared__ T sA[MMAX * K];
+  __shared__ T stau[K], stk2[K];
+  for (int t = threadIdx.x; t < op.m * K; t += blockDim.x) sA[t] = OpT<T>::A(op, t);
+  if (threadIdx.x < K) {
+    stau[threadIdx.x] = OpT<T>::tau(op, threadIdx.x);
+    stk2[threadIdx.x] = OpT<T>::tk2(op, threadIdx.x);
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= op.n) return;
+  const int64_t ld = op.ld;
+  PixelOp<T> po;
+  load_pixel_op<T>(op, i, true, true, po);
+  for (int r = 0; r < R; ++r) {
+    const T* x = X + (size_t)r * K * ld;
+    T* y = Y + (size_t)r * K * ld;
+    T xi[K], acc[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) xi[j] = x[j * ld + i];
+    apply_pixel<K, T, T>(op, po, sA, stau, stk2, x, i, xi, acc);
+#pragma unroll
+    for (int j = 0; j < K; ++j) y[j * ld + i] = acc[j];
+  }
+}
+
+// Per-tile partial gradients (see sylv_backward); out layout [tau(k), kappa(k), beta(k)].
+template <int K>
+__global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restrict__ X,
+                                              const double* __restrict__ lam,
+                                              const double* __restrict__ Y, int R,
+                                              int want_beta, double* partial) {
+  __shared__ double red[32 * 3 * K];
+  const int64_t ld = op.ld;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < op.n;
+  double g[3 * K];
+#pragma unroll
+  for (int t = 0; t < 3 * K; ++t) g[t] = 0.0;
+  if (valid) {
+    PixelOp<double> po;
+    load_pixel_op<double>(op, i, true, true, po);
+    for (int r = 0; r < R; ++r) {
+      const double* x = X + (size_t)r * K * ld;
+      const double* l = lam + (size_t)r * K * ld;
+      double xi[K], li[K], Lx[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        xi[j] = x[j * ld + i];
+        li[j] = l[j * ld + i];
+        Lx[j] = po.dg * xi[j];
+      }
+#pragma unroll
+      for (int e = 0; e < EMAX; ++e) {
+        if (e < op.E) {
+          const int64_t c = po.col[e];
+#pragma unroll
+          for (int j = 0; j < K; ++j) Lx[j] += po.val[e] * x[j * ld + c];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const double kap2 = op.kappa64[j] * op.kappa64[j];
+        g[j] -= li[j] * (kap2 * po.wi * xi[j] + Lx[j]);
+        g[K + j] -= 2.0 * op.tau64[j] * op.kappa64[j] * li[j] * po.wi * xi[j];
+      }
+      if (want_beta) {
+        const double* y = Y + (size_t)r * op.m * ld;
+        for (int c = 0; c < op.m; ++c) {
+          double t = 0.0, u = 0.0;
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            t += op.A64[c * K + j] * xi[j];
+            u += op.A64[c * K + j] * li[j];
+          }
+          const double dc = po.dv[c];
+          const double yc = y[c * ld + i];
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            g[2 * K + j] += op.logf64[c] * op.A64[c * K + j] * dc *
+                            (li[j] * yc - u * xi[j] - li[j] * t);
+        }
+      }
+    }
+  }
+  block_sum<3 * K>(g, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int t = 0; t < 3 * K; ++t) partial[(size_t)blockIdx.x * 3 * K + t] = g[t];
+  }
+}
+
+__global__ void k_grad_final(const double* __restrict__ partial, int ntiles, int nv,
+                             double* out) {
+  // one block; fixed-order sums
+  __shared__ double red[32];
+  for (int t = 0; t < nv; ++t) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < ntiles; b += blockDim.x) v[0] += partial[(size_t)b * nv + t];
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) out[t] = v[0];
+  }
+}
+
+__global__ void k_init_states(int ncols, const int* __restrict__ col_sys,
+                              const int* __restrict__ col_rhs, const SysDesc* __restrict__ d,
+                              Control* ctl) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    ctl->n_active = 0u;
+    ctl->n_unfinished = (unsigned)ncols;
+  }
+  if (t >= ncols) return;
+  ColState& cs = d[col_sys[t]].st[col_rhs[t]];
+  cs.bnorm2 = 0.0;
+  cs.rr64 = 0.0;
+  cs.gamma = 0.0;
+  cs.alpha = 0.0;
+  cs.beta = 0.0;
+  cs.rr_in0 = 0.0;
+  cs.rr_in = 0.0;
+  cs.thr_in = 0.0;
+  cs.relres = 0.0;
+  cs.phase = PH_START;
+  cs.it = 0;
+  cs.outer = 0;
+  cs.status = SYLV_OK;
+  cs.first = 1;
+  cs.stop_after = 0;
+  if (col_rhs[t] == 0) *d[col_sys[t]].counter = 0u;
+}
+
+// ------------------------------------------------------------------------------------------
+cudaError_t launch_csr_check(const OpData& op, const int32_t* rowptr, const int32_t* col,
+                             int64_t nnz, unsigned int* flags, unsigned int* maxdeg,
+                             cudaStream_t s) {
+  k_csr_check<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(op.n, rowptr, col, nnz,
+                                                                    flags, maxdeg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ell_build(const OpData& op, const int32_t* rowptr, const int32_t* col,
+                             const double* val, int32_t* ell_col, float* ell_val32,
+                             double* ell_val64, float* diag32, double* diag64, int E,
+                             cudaStream_t s) {
+  k_ell_build<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(
+      op.n, op.ld, rowptr, col, val, E, ell_col, ell_val32, ell_val64, diag32, diag64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int64_t ld,
+                                 float* dst32, double* dst64, int positive,
+                                 unsigned int* flags, cudaStream_t s) {
+  const int64_t tot = rows * n;
+  if (tot == 0) return cudaSuccess;
+  k_convert_check<<<blocks_for(tot, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(src, rows, n, ld, dst32,
+                                                                       dst64, positive, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s) {
+  k_rhs<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(op, Y, B, R);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s) {
+  const int nb = blocks_for(op.n, 256);
+#define CALL(K) k_apply<K, T><<<nb, 256, 0, s>>>(op, X, Y, R)
+  SYLV_DISPATCH_K(op.k, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+template cudaError_t launch_apply<float>(const OpData&, const float*, float*, int,
+                                         cudaStream_t);
+template cudaError_t launch_apply<double>(const OpData&, const double*, double*, int,
+                                          cudaStream_t);
+
+cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, const double* Y,
+                        int R, int want_beta, double* partial, int ntiles, double* out,
+                        cudaStream_t s) {
+#define CALL(K) k_grad<K><<<ntiles, 256, 0, s>>>(op, X, lam, Y, R, want_beta, partial)
+  SYLV_DISPATCH_K(op.k, CALL)
+#undef CALL
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_grad_final<<<1, 256, 0, s>>>(partial, ntiles, 3 * op.k, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,
+                               const SysDesc* d, Control* c, cudaStream_t s) {
+  k_init_states<<<blocks_for(ncols, 128), 128, 0, s>>>(ncols, col_sys, col_rhs, d, c);
+  return cudaGetLastError();
+}
+
+}  // namespace sylv

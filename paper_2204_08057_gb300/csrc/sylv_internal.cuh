@@ -1,0 +1,149 @@
+// Internal device/host data structures of the solver library.
+//
+// One "system" is one handle (operator) together with nrhs right-hand sides.  A solve runs a
+// list of systems at once (sylv_solve is the one-system case).  Systems are cut into tiles of
+// blockDim.x consecutive pixels; every kernel of the iteration launches one CTA per tile over
+// the tiles of all systems that share a number of sources k, and each right-hand side of
+// each system ("column") carries its own CG scalars and state in a ColState.
+//
+// Scalar reductions (dot products) are deterministic: each CTA writes its partial sums for
+// its tile, and the last CTA of a system to finish (detected with an atomic counter, no
+// waiting) adds the partials in a fixed order and updates the system's scalars.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sylv.h"
+
+namespace sylv {
+
+constexpr int KMAX = SYLV_MAX_K;
+constexpr int MMAX = SYLV_MAX_M;
+constexpr int EMAX = SYLV_MAX_DEGREE;
+constexpr int RMAX = SYLV_MAX_RHS;
+constexpr int NPART = 4;          // partial sums per (tile, column)
+constexpr int MAX_BLOCK = 512;
+
+enum Phase : int {
+  PH_START = 0,       // before the first FP64 residual
+  PH_INNER = 1,       // inner CG running
+  PH_INNER_DONE = 2,  // inner CG finished: X += d and a new FP64 residual are due
+  PH_CONVERGED = 3,   // final: tolerance reached
+  PH_FAILED = 4       // final: see status
+};
+
+struct ColState {
+  double bnorm2;   // ||b||^2
+  double rr64;     // ||b - G X||^2 at the last FP64 residual
+  double gamma;    // r . z of the inner iteration
+  double alpha;
+  double beta;
+  double rr_in0;   // ||r||^2 at the start of the inner solve
+  double rr_in;    // current inner ||r||^2 (recursive)
+  double thr_in;   // inner stop threshold on ||r||^2
+  double relres;   // last true relative residual
+  int phase;
+  int it;          // inner iterations so far
+  int outer;       // FP64 residual evaluations so far
+  int status;      // SYLV_* status once final
+  int first;       // next inner apply is the first of this inner solve
+  int stop_after;  // inner solve stopped on the iteration cap
+  int pad0, pad1;
+};
+
+// Operator data of one handle, in the device layouts the kernels read.
+struct OpData {
+  int64_t n;
+  int64_t ld;
+  int k, m, E, has_w;
+  const int32_t* ell_col;    // E x ld: off-diagonal columns of L (padding: own row, value 0)
+  const float* ell_val32;    // E x ld
+  const double* ell_val64;   // E x ld
+  const float* diag32;       // ld: diagonal of L
+  const double* diag64;
+  const float* D32;          // m x ld
+  const double* D64;
+  const float* w32;          // ld or null
+  const double* w64;
+  float A32[MMAX * KMAX];    // A[c * k + j]
+  double A64[MMAX * KMAX];
+  float tau32[KMAX];
+  float tk2_32[KMAX];        // tau_j kappa_j^2
+  double tau64[KMAX];
+  double tk2_64[KMAX];
+  double kappa64[KMAX];
+  double logf64[MMAX];       // ln(nu_c / nu0), power-law mixing only
+};
+
+struct SysDesc {
+  OpData op;
+  int R;                 // right-hand sides
+  int ntiles;            // tiles of this system
+  int tile_px;           // pixels per tile (= blockDim.x of every launch over it)
+  int pad;
+  const double* B;       // R x k x ld
+  double* X;             // R x k x ld
+  void* vd;              // inner vectors, R x k x ld of the inner type
+  void* vr;
+  void* vz;
+  void* vp;
+  void* vq;
+  ColState* st;          // R
+  double* partial;       // ntiles x R x NPART
+  unsigned int* counter; // one per system, zero between kernels
+};
+
+struct Control {
+  unsigned int n_active;      // columns in PH_INNER
+  unsigned int n_unfinished;  // columns not final
+  double tol2;                // tol^2
+  double tol_in2;             // inner_tol^2 (0 in FP64 mode)
+  double safety2;             // squared safety factor on the inner target
+  int maxit;
+  int max_outer;
+  int precond;
+  int pad;
+};
+
+struct TileRef {
+  int sys;
+  int tile;
+};
+
+// ------------------------------------------------------------------------------------------
+// launchers (defined in the kernel translation units)
+// ------------------------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_inner_apply(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+                               Control* c, cudaStream_t s);
+template <typename T>
+cudaError_t launch_inner_update(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+                                Control* c, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+                            Control* c, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_x(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+                            cudaStream_t s);
+cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,
+                               const SysDesc* d, Control* c, cudaStream_t s);
+
+cudaError_t launch_csr_check(const OpData& op, const int32_t* rowptr, const int32_t* col,
+                             int64_t nnz, unsigned int* flags, unsigned int* maxdeg,
+                             cudaStream_t s);
+cudaError_t launch_ell_build(const OpData& op, const int32_t* rowptr, const int32_t* col,
+                             const double* val, int32_t* ell_col, float* ell_val32,
+                             double* ell_val64, float* diag32, double* diag64, int E,
+                             cudaStream_t s);
+cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int64_t ld,
+                                 float* dst32, double* dst64, int positive,
+                                 unsigned int* flags, cudaStream_t s);
+cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s);
+cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, const double* Y,
+                        int R, int want_beta, double* partial, int ntiles, double* out,
+                        cudaStream_t s);
+
+}  // namespace sylv

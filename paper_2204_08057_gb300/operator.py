@@ -1,0 +1,141 @@
+"""Tensor-level wrapper around one solver handle (``sylv_create`` ... ``sylv_destroy``).
+
+The wrapper only moves inputs to the device in the layouts ``include/sylv.h`` documents and
+calls the C ABI; all arithmetic runs in the library's kernels.
+"""
+
+import numpy as np
+
+from . import binding as B
+
+
+def _to_device(x, dtype, device):
+    import torch
+    if isinstance(x, torch.Tensor):
+        return x.to(device=device, dtype=dtype).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device=device)
+
+
+class Operator:
+    """G = sum_j (e_j e_j^T) kron tau_j (kappa_j^2 W + L) + sum_c (a_c a_c^T) kron D_c.
+
+    Vectors are torch tensors of shape (R, k, ld) or (k, ld) (float64 unless noted)."""
+
+    def __init__(self, *, rowptr, col, val, D, tau, kappa, nu=None, beta=None, A=None, w=None,
+                 ld=None, nu0=0.0, device="cuda", stream=None):
+        import torch
+        self.device = torch.device(device)
+        D = _to_device(D, torch.float64, self.device)
+        self.m = int(D.shape[0])
+        n = int(np.asarray(rowptr).shape[0] - 1) if not isinstance(rowptr, torch.Tensor) \
+            else int(rowptr.numel() - 1)
+        self.n = n
+        self.ld = int(ld) if ld is not None else n
+        if D.dim() != 2 or D.shape[1] < self.n:
+            raise ValueError("D must be (m, >= n)")
+        if D.shape[1] != self.ld:
+            Dp = torch.zeros((self.m, self.ld), dtype=torch.float64, device=self.device)
+            Dp[:, :self.n] = D[:, :self.n]
+            D = Dp
+        self.k = int(np.asarray(tau).reshape(-1).shape[0])
+        self._rowptr = _to_device(rowptr, torch.int32, self.device)
+        self._col = _to_device(col, torch.int32, self.device)
+        self._val = _to_device(val, torch.float64, self.device)
+        self._w = _to_device(w, torch.float64, self.device) if w is not None else None
+        self._D = D
+        self.tau = np.asarray(tau, dtype=np.float64).reshape(-1)
+        self.kappa = np.asarray(kappa, dtype=np.float64).reshape(-1)
+        self.nu = None if nu is None else np.asarray(nu, dtype=np.float64).reshape(-1)
+        self.beta = None if beta is None else np.asarray(beta, dtype=np.float64).reshape(-1)
+        self.A = None if A is None else np.asarray(A, dtype=np.float64).reshape(self.m, self.k)
+        self.handle = B.sylv_create(n=self.n, k=self.k, m=self.m, ld=self.ld,
+                                    L_rowptr=self._rowptr, L_col=self._col, L_val=self._val,
+                                    D=self._D, tau=self.tau, kappa=self.kappa, nu=self.nu,
+                                    beta=self.beta, A=self.A, w=self._w, nu0=nu0,
+                                    stream=stream)
+
+    # -- helpers ---------------------------------------------------------------------------
+    def zeros(self, nrhs=1, dtype=None):
+        import torch
+        return torch.zeros((nrhs, self.k, self.ld), dtype=dtype or torch.float64,
+                           device=self.device)
+
+    def _batch(self, X, rows):
+        X = X if X.dim() == 3 else X.unsqueeze(0)
+        if X.shape[1] != rows or X.shape[2] != self.ld:
+            raise ValueError(f"expected (R, {rows}, {self.ld}), got {tuple(X.shape)}")
+        return X.contiguous()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.sylv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points --------------------------------------------------------------------------
+    def rhs(self, Yobs, stream=None):
+        """b = B^T C y for Yobs (R, m, ld) -> (R, k, ld)."""
+        import torch
+        Y = self._batch(Yobs.to(torch.float64), self.m)
+        out = torch.empty((Y.shape[0], self.k, self.ld), dtype=torch.float64, device=self.device)
+        B.sylv_rhs(self.handle, Y, out, Y.shape[0], k=self.k, m=self.m, ld=self.ld, n=self.n,
+                   stream=stream)
+        return out
+
+    def apply(self, X, stream=None):
+        """Y = G X in the dtype of X (float32 or float64)."""
+        import torch
+        Xb = self._batch(X, self.k)
+        Y = torch.empty_like(Xb)
+        B.sylv_apply(self.handle, Xb, Y, Xb.shape[0], k=self.k, ld=self.ld, n=self.n,
+                     stream=stream)
+        return Y
+
+    def solve(self, Bv, X0=None, *, opts=None, stream=None, allow_not_converged=False,
+              allow=(), **kw):
+        """X = G^{-1} B; returns (X, info dict)."""
+        Bb = self._batch(Bv, self.k)
+        if opts is None:
+            opts = B.make_opts(**kw)
+        X = Bb.new_zeros(Bb.shape) if X0 is None else self._batch(X0, self.k).clone()
+        if X0 is not None:
+            opts.use_x0 = 1
+        allow = tuple(allow) + ((B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ())
+        code, info = B.sylv_solve(self.handle, Bb, X, Bb.shape[0], opts, k=self.k, ld=self.ld,
+                                  n=self.n, stream=stream, allow=allow)
+        d = info.as_dict()
+        d["code"] = code
+        return X, d
+
+    def backward(self, Xhat, dLdX, Yobs=None, *, opts=None, want=("tau", "kappa", "beta"),
+                 stream=None, **kw):
+        """Gradients (g_tau, g_kappa, g_beta) of a loss with dl/dX = dLdX at X = Xhat."""
+        Xb = self._batch(Xhat, self.k)
+        Gb = self._batch(dLdX, self.k)
+        Yb = self._batch(Yobs, self.m) if Yobs is not None else None
+        if opts is None:
+            opts = B.make_opts(**kw)
+        lam = Xb.new_zeros(Xb.shape)
+        gt, gk, gb, info = B.sylv_backward(self.handle, Xb, Gb, Yb, Xb.shape[0], lam, opts,
+                                           k=self.k, m=self.m, ld=self.ld, n=self.n,
+                                           want=want, stream=stream)
+        return gt, gk, gb, lam, info.as_dict()
+
+
+def solve_batched(ops, Bs, *, opts=None, stream=None, allow_not_converged=False, **kw):
+    """Solves several Operators' systems in one batched call.  Returns (Xs, infos)."""
+    if opts is None:
+        opts = B.make_opts(**kw)
+    Bb = [op._batch(b, op.k) for op, b in zip(ops, Bs)]
+    Xs = [b.new_zeros(b.shape) for b in Bb]
+    allow = (B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ()
+    code, infos = B.sylv_solve_batched([op.handle for op in ops], Bb, Xs,
+                                       [b.shape[0] for b in Bb], opts,
+                                       shapes=[(op.k, op.ld, op.n) for op in ops],
+                                       stream=stream, allow=allow)
+    return Xs, [i.as_dict() for i in infos]

@@ -1,0 +1,309 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded inputs.
+
+Tolerances:
+* FP64 operator apply: |Y - Y_oracle| <= 64 u64 (|G| |X|) element-wise, the forward error
+  bound of a sum of at most ~40 products per output (u64 = 2^-53).
+* FP32 operator apply: |Y - Y_oracle| <= 64 u32 (|G| |X|) element-wise (u32 = 2^-24).
+* Solves: relative solution error ||X - X_oracle||_F / ||X_oracle||_F <= 1e-8 in FP64 mode and
+  <= 1e-6 in mixed mode (FP32 inner, FP64 refinement).
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import (device_batch, operator_for, oracle_L, oracle_solution, relerr,
+                        small_problem)
+from oracle import model
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_08057_gb300 import build
+    build.build()
+
+
+def abs_apply(p, X, A):
+    """|G| |X| with the same terms as the apply (for rounding-error bounds)."""
+    L = oracle_L(p)
+    absL = abs(L)
+    out = np.empty_like(X)
+    for j in range(p.k):
+        out[j] = p.tau[j] * (p.kappa[j] ** 2 * np.abs(X[j]) + absL @ np.abs(X[j]))
+    out += np.abs(A).T @ (p.D * (np.abs(A) @ np.abs(X)))
+    return out
+
+
+CASES = [
+    ("lattice", 37, 41, 3, 5, 0),     # 1517 px: 6 tiles of 256, ragged tail
+    ("sphere", 20, 33, 6, 9, 5),      # ld > n
+    ("lattice", 9, 11, 1, 1, 3),      # scalar case
+    ("sphere", 16, 17, 8, 16, 0),     # largest k and m of this build
+    ("lattice", 12, 30, 4, 7, 64),
+    ("sphere", 3, 4, 2, 3, 1),        # smaller than one tile
+]
+
+
+@pytest.mark.parametrize("kind,H,W,k,m,pad", CASES)
+def test_apply_parity(kind, H, W, k, m, pad):
+    import torch
+    p = small_problem(kind, H, W, k, m, seed=100 + k + m)
+    ld = p.n + pad
+    op = operator_for(p, ld=ld)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((2, k, p.n))
+    A = model.powerlaw_mixing(p.nu, p.beta)
+    L = oracle_L(p)
+    ref = np.stack([model.apply(L, p.D, p.tau, p.kappa, A, x) for x in X])
+    bound = np.stack([abs_apply(p, x, A) for x in X])
+    Xd = device_batch(X, ld)
+    Y64 = op.apply(Xd).cpu().numpy()[:, :, :p.n]
+    assert np.all(np.abs(Y64 - ref) <= 64 * U64 * bound + 1e-300)
+    Y32 = op.apply(Xd.to(torch.float32)).cpu().numpy()[:, :, :p.n].astype(np.float64)
+    X32 = Xd.to(torch.float32).cpu().numpy()[:, :, :p.n].astype(np.float64)
+    ref32 = np.stack([model.apply(L, p.D, p.tau, p.kappa, A, x) for x in X32])
+    # inputs rounded to FP32 first; then the FP32 arithmetic bound
+    assert np.all(np.abs(Y32 - ref32) <= 64 * U32 * bound * 1.01 + 1e-30)
+    op.close()
+
+
+def test_rhs_parity():
+    p = small_problem("sphere", 19, 23, 5, 7, seed=9, nrhs=3)
+    ld = p.n + 7
+    op = operator_for(p, ld=ld)
+    A = model.powerlaw_mixing(p.nu, p.beta)
+    ref = np.stack([model.rhs(p.D, y, A) for y in p.Yobs])
+    got = op.rhs(device_batch(p.Yobs, ld)).cpu().numpy()[:, :, :p.n]
+    assert np.allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    op.close()
+
+
+def test_explicit_mixing_matrix_override():
+    from oracle import physical_mixing
+    p = small_problem("lattice", 14, 15, 4, 9, seed=4)
+    A = physical_mixing.physical_mixing(synth.PLANCK_NU)
+    op = operator_for(p, A=A)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((1, 4, p.n))
+    ref = model.apply(oracle_L(p), p.D, p.tau, p.kappa, A, X[0])
+    got = op.apply(device_batch(X, p.n)).cpu().numpy()[0]
+    assert np.abs(got - ref).max() <= 64 * U64 * abs_apply(p, X[0], A).max()
+    Xo, b = oracle_solution(p, A=A)
+    Xs, info = op.solve(device_batch(b, p.n), tol=1e-12, precision=0)
+    assert info["code"] == 0
+    assert relerr(Xs.cpu().numpy(), Xo) <= 1e-8
+    op.close()
+
+
+SOLVE_CASES = [
+    ("lattice", 24, 24, 3, 5, 1),
+    ("sphere", 18, 36, 6, 9, 1),
+    ("lattice", 21, 19, 4, 7, 3),     # several right-hand sides, ragged
+    ("sphere", 10, 12, 8, 12, 2),
+    ("lattice", 7, 9, 1, 2, 1),
+]
+
+
+@pytest.mark.parametrize("kind,H,W,k,m,nrhs", SOLVE_CASES)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_parity(kind, H, W, k, m, nrhs, precision):
+    p = small_problem(kind, H, W, k, m, seed=7 + k, nrhs=nrhs)
+    ld = p.n + 3
+    op = operator_for(p, ld=ld)
+    Xo, b = oracle_solution(p)
+    tol = 1e-12 if precision == 0 else 1e-11
+    X, info = op.solve(device_batch(b, ld), tol=tol, precision=precision)
+    assert info["code"] == 0, info
+    assert info["relres"] <= tol
+    X = X.cpu().numpy()[:, :, :p.n]
+    assert relerr(X, Xo) <= (1e-8 if precision == 0 else 1e-6)
+    op.close()
+
+
+def test_solve_options_paths():
+    """No preconditioner, no graph, profiling, warm start: same solution."""
+    p = small_problem("sphere", 16, 20, 4, 6, seed=21)
+    op = operator_for(p)
+    Xo, b = oracle_solution(p)
+    Bd = device_batch(b, p.n)
+    for kw in (dict(precond=0, precision=0), dict(use_graph=0), dict(profile=1),
+               dict(profile=1, use_graph=0), dict(check_every=1), dict(check_every=100),
+               dict(inner_tol=1e-2)):
+        X, info = op.solve(Bd, tol=1e-11, **kw)
+        assert info["code"] == 0, (kw, info)
+        assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6, kw
+        if kw.get("profile"):
+            assert info["n_apply"] > 0 and info["ms_apply"] > 0 and info["n_residual"] > 0
+    X0 = device_batch(Xo + 1e-3, p.n)
+    X, info = op.solve(Bd, X0=X0, tol=1e-11)
+    assert info["code"] == 0
+    assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+    op.close()
+
+
+def test_config1_plain_fp64_cg():
+    """64 x 64 periodic lattice, k=3, m=5, plain FP64 CG (no preconditioner) to 1e-10."""
+    p = synth.config_problem(1)
+    op = operator_for(p)
+    Xo, b = oracle_solution(p)
+    X, info = op.solve(device_batch(b, p.n), tol=1e-10, precision=0, precond=0)
+    assert info["code"] == 0 and info["relres"] <= 1e-10
+    # relres 1e-10 bounds the error by cond(G) * 1e-10; check against the oracle at 1e-6 and
+    # at the FP64 parity bar after tightening the tolerance
+    assert relerr(X.cpu().numpy()[0], Xo[0]) <= 1e-6
+    X2, info2 = op.solve(device_batch(b, p.n), tol=1e-13, precision=0, precond=0)
+    assert relerr(X2.cpu().numpy()[0], Xo[0]) <= 1e-8
+    op.close()
+
+
+def test_batched_parity():
+    from paper_2204_08057_gb300.operator import solve_batched
+    specs = [("lattice", 17, 19, 3, 5, 1), ("sphere", 12, 20, 6, 8, 2),
+             ("lattice", 30, 31, 4, 6, 1), ("lattice", 9, 10, 5, 7, 1),
+             ("sphere", 22, 25, 3, 5, 1), ("lattice", 5, 6, 6, 8, 3)]
+    probs = [small_problem(*s[:5], seed=40 + i, nrhs=s[5]) for i, s in enumerate(specs)]
+    ops = [operator_for(p, ld=p.n + i) for i, p in enumerate(probs)]
+    refs = [oracle_solution(p) for p in probs]
+    Bs = [device_batch(b, op.ld) for (_, b), op in zip(refs, ops)]
+    for precision, bar in ((1, 1e-6), (0, 1e-8)):
+        Xs, infos = solve_batched(ops, Bs, tol=1e-12 if precision == 0 else 1e-11,
+                                  precision=precision)
+        for X, (Xo, _), p, info in zip(Xs, refs, probs, infos):
+            assert info["status"] == 0
+            assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= bar
+    # the same systems one by one give the same answers (independent scalars per system)
+    X1, _ = ops[2].solve(Bs[2], tol=1e-11)
+    assert relerr(X1.cpu().numpy()[:, :, :probs[2].n], refs[2][0]) <= 1e-6
+    for op in ops:
+        op.close()
+
+
+def test_backward_matches_oracle_gradient():
+    from oracle import gradient
+    p = small_problem("sphere", 8, 10, 3, 5, seed=77, nrhs=2)
+    op = operator_for(p)
+    L = oracle_L(p)
+    Xo, _ = oracle_solution(p)
+    g = 2 * (Xo - p.X_true[None])
+    ga = gradient.adjoint_gradient(L, p.D, p.tau, p.kappa, p.nu, p.beta, p.Yobs, Xo, g)
+    gt, gk, gb, lam, info = op.backward(device_batch(Xo, p.n), device_batch(g, p.n),
+                                        device_batch(p.Yobs, p.n), tol=1e-12, precision=0)
+    assert info["status"] == 0
+    for got, ref in zip((gt, gk, gb), ga[:3]):
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    assert relerr(lam.cpu().numpy(), ga[3]) <= 1e-8
+    op.close()
+
+
+def test_autograd_function_fd():
+    import torch
+    from paper_2204_08057_gb300.autograd import SylvProblem, sylv_solve_differentiable
+    from oracle import gradient
+    p = small_problem("lattice", 8, 9, 3, 5, seed=5)
+    prob = SylvProblem(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, nu=p.nu)
+    tau = torch.tensor(p.tau, dtype=torch.float64, requires_grad=True)
+    kappa = torch.tensor(p.kappa, dtype=torch.float64, requires_grad=True)
+    beta = torch.tensor(p.beta, dtype=torch.float64, requires_grad=True)
+    Y = device_batch(p.Yobs, p.n)[0]
+    Xt = torch.as_tensor(p.X_true, device="cuda")
+    X = sylv_solve_differentiable(Y, tau, kappa, beta, prob, tol=1e-13, precision=0)
+    loss = ((X - Xt) ** 2).sum()
+    loss.backward()
+    L = oracle_L(p)
+    fd = gradient.fd_gradient(lambda Z: float(np.sum((Z - p.X_true) ** 2)), L, p.D, p.tau,
+                              p.kappa, p.nu, p.beta, p.Yobs[0], h=1e-6)
+    for got, ref in zip((tau.grad, kappa.grad, beta.grad), fd):
+        assert np.allclose(got.numpy(), ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+def test_single_pixel_and_isolated_pixels():
+    """n = 1 (no neighbours, ELL width 0): G is the k x k block itself."""
+    import torch
+    from paper_2204_08057_gb300.operator import Operator
+    k, m = 3, 4
+    nu = np.array([30.0, 100.0, 217.0, 545.0])
+    beta = np.array([0.5, -2.0, 1.2])
+    tau = np.array([1.0, 2.0, 0.5])
+    kappa = np.array([0.3, 0.1, 1.0])
+    d = np.array([[1.5], [0.7], [2.0], [1.1]])
+    op = Operator(rowptr=np.array([0, 1]), col=np.array([0]), val=np.array([0.0]), D=d,
+                  tau=tau, kappa=kappa, nu=nu, beta=beta)
+    A = model.powerlaw_mixing(nu, beta)
+    Gk = np.diag(tau * kappa ** 2) + (A.T * d[:, 0]) @ A
+    b = np.array([[1.0], [-2.0], [0.5]])
+    X, info = op.solve(torch.as_tensor(b[None], device="cuda"), tol=1e-13, precision=0)
+    assert info["code"] == 0
+    assert np.allclose(X.cpu().numpy()[0, :, 0], np.linalg.solve(Gk, b[:, 0]), rtol=1e-10)
+    op.close()
+
+
+def test_zero_rhs_gives_zero():
+    p = small_problem("lattice", 6, 7, 3, 5, seed=3)
+    op = operator_for(p)
+    X, info = op.solve(op.zeros(1), tol=1e-10)
+    assert info["code"] == 0 and float(X.abs().max()) == 0.0
+    op.close()
+
+
+def test_error_statuses():
+    import torch
+    from paper_2204_08057_gb300 import binding as Bn
+    from paper_2204_08057_gb300.operator import Operator
+    p = small_problem("lattice", 6, 7, 3, 5, seed=3)
+    bad_col = p.graph.col.copy()
+    bad_col[5] = p.n + 3                               # out of range
+    with pytest.raises(Bn.SylvError) as e:
+        Operator(rowptr=p.graph.rowptr, col=bad_col, val=p.graph.val, D=p.D, tau=p.tau,
+                 kappa=p.kappa, nu=p.nu, beta=p.beta)
+    assert e.value.code == Bn.SYLV_E_INVALID
+    bad_ptr = p.graph.rowptr.copy()
+    bad_ptr[3], bad_ptr[4] = bad_ptr[4], bad_ptr[3]    # non-monotone
+    with pytest.raises(Bn.SylvError) as e:
+        Operator(rowptr=bad_ptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
+                 kappa=p.kappa, nu=p.nu, beta=p.beta)
+    assert e.value.code == Bn.SYLV_E_INVALID
+    D = p.D.copy()
+    D[1, 4] = -1.0
+    with pytest.raises(Bn.SylvError) as e:
+        Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=D, tau=p.tau,
+                 kappa=p.kappa, nu=p.nu, beta=p.beta)
+    assert e.value.code == Bn.SYLV_E_INVALID
+    D[1, 4] = np.nan
+    with pytest.raises(Bn.SylvError):
+        Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=D, tau=p.tau,
+                 kappa=p.kappa, nu=p.nu, beta=p.beta)
+    # a row with 9 off-diagonal entries exceeds this build's ELL width
+    n = 10
+    rowptr = np.array([0, 10] + list(range(12, 12 + 2 * 9, 2)), dtype=np.int32)
+    col = np.concatenate([np.arange(10), np.ravel([[i, 0] for i in range(1, 10)])])
+    val = np.concatenate([[9.0], -np.ones(9), np.ravel([[1.0, -1.0]] * 9)])
+    with pytest.raises(Bn.SylvError) as e:
+        Operator(rowptr=rowptr, col=col, val=val, D=np.ones((2, n)), tau=[1.0], kappa=[1.0],
+                 nu=[30.0, 70.0], beta=[1.0])
+    assert e.value.code == Bn.SYLV_E_UNSUPPORTED
+    # iteration cap: NOT_CONVERGED with a finite last iterate and the reached residual
+    op = operator_for(p)
+    _, b = oracle_solution(p)
+    X, info = op.solve(device_batch(b, p.n), tol=1e-12, maxit=2, precision=0,
+                       allow_not_converged=True)
+    assert info["code"] == Bn.SYLV_E_NOT_CONVERGED
+    assert np.isfinite(X.cpu().numpy()).all() and 0 < info["relres"] < 1
+    with pytest.raises(Bn.SylvError) as e:
+        op.solve(device_batch(b, p.n), tol=0.0)
+    assert e.value.code == Bn.SYLV_E_INVALID
+    # non-finite right-hand side: reported, not hung
+    bn = b.copy()
+    bn[0, 1, 3] = np.inf
+    X, info = op.solve(device_batch(bn, p.n), tol=1e-8, allow_not_converged=True,
+                       allow=(Bn.SYLV_E_BREAKDOWN,))
+    assert info["code"] in (Bn.SYLV_E_BREAKDOWN, Bn.SYLV_E_NOT_CONVERGED)
+    assert torch.cuda.is_available()
+    op.close()
