@@ -214,7 +214,7 @@ def test_autograd_function_fd():
     beta = torch.tensor(p.beta, dtype=torch.float64, requires_grad=True)
     Y = device_batch(p.Yobs, p.n)[0]
     Xt = torch.as_tensor(p.X_true, device="cuda")
-    X = sylv_solve_differentiable(Y, tau, kappa, beta, prob, tol=1e-13, precision=0)
+    X = sylv_solve_differentiable(Y, tau, kappa, beta, prob, tol=1e-12, precision=0)
     loss = ((X - Xt) ** 2).sum()
     loss.backward()
     L = oracle_L(p)
