@@ -1,6 +1,6 @@
 // Kernels of the preconditioned CG iteration and of the FP64 refinement loop.
 //
-// Per inner iteration two kernels run over every tile of every active system:
+// Per inner iteration two kernels run over every active system:
 //
 //   inner_apply:  p = z + beta p,  q = G z + beta q   (= G p, since G p = G z + beta G p_old),
 //                 partial sums of p . q; the last CTA of a system sets alpha = gamma / (p . q).
@@ -18,6 +18,11 @@
 // The FP64 refinement loop adds two kernels: update_x (X += d) and residual (r = B - G X in
 // FP64, r_in = r rounded to the inner type, d = 0, z = P^{-1} r_in), whose last CTA decides
 // convergence of each column on the true FP64 residual.
+//
+// Work split: each system owns `nslots` CTAs (all resident at once); CTA `slot` handles tiles
+// slot, slot + nslots, ... of blockDim.x consecutive pixels, keeps per-warp partial sums in
+// shared memory, writes one partial per column at the end, and the last of the system's CTAs
+// to finish (atomic counter, no waiting) reduces the nslots partials in a fixed order.
 #pragma once
 
 #include <cmath>
@@ -75,98 +80,99 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
   __syncthreads();
 }
 
-// Called by all threads after thread 0 wrote this CTA's partials.  True in the last CTA of
-// the system to arrive; that CTA then owns the partials and resets the counter.
-__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total,
-                                            int* s_flag) {
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned int prev = atomicAdd(counter, 1u);
-    *s_flag = (prev == total - 1u) ? 1 : 0;
-  }
-  __syncthreads();
-  const bool last = *s_flag != 0;
-  if (last) __threadfence();
-  return last;
-}
-
-// Fixed-order sum of partial value v of column r over the system's tiles (valid in thread 0).
-template <int NV>
-__device__ __forceinline__ void reduce_partials(const SysDesc& sd, int r, const int (&vidx)[NV],
-                                                double (&out)[NV], double* smem) {
-  double acc[NV];
-#pragma unroll
-  for (int t = 0; t < NV; ++t) acc[t] = 0.0;
-  for (int tl = threadIdx.x; tl < sd.ntiles; tl += blockDim.x) {
-    const double* p = sd.partial + ((size_t)tl * sd.R + r) * NPART;
-#pragma unroll
-    for (int t = 0; t < NV; ++t) acc[t] += __ldcg(p + vidx[t]);
-  }
-  block_sum<NV>(acc, smem);
-#pragma unroll
-  for (int t = 0; t < NV; ++t) out[t] = acc[t];
-}
-
-// Per-pixel operator data held in registers for the duration of a CTA.
-template <typename T>
-struct PixelOp {
-  int col[EMAX];
-  T val[EMAX];
-  T dg;    // L_ii
-  T wi;    // mass diagonal
-  T dv[MMAX];
+// Mixing rows, prior scalars and per-column state of one system, staged in shared memory.
+// Rows of A are padded to 8 entries so a row is read with one or two 16-byte loads.
+template <typename T, int NV>
+struct CtaShared {
+  alignas(16) T A[MMAX][8];
+  alignas(16) T tau[8];
+  alignas(16) T tk2[8];
+  T sc[RMAX];        // per-column scalar (beta or alpha)
+  int act[RMAX];     // column takes part in this kernel
+  int aux[RMAX];     // per-column flag (first iteration)
+  double wacc[RMAX][MAX_BLOCK / 32][NV];  // per-warp partial sums
+  double red[32 * NV];
+  int flag;
 };
 
-template <typename T>
-__device__ __forceinline__ void load_pixel_op(const OpData& op, int64_t i, bool valid,
-                                              bool need_lap, PixelOp<T>& po) {
-  const int64_t ld = op.ld;
-  if (need_lap) {
-#pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-      if (e < op.E) {
-        po.col[e] = valid ? __ldg(op.ell_col + e * ld + i) : 0;
-        po.val[e] = valid ? __ldg(OpT<T>::val(op) + e * ld + i) : T(0);
-      }
-    }
+template <typename T, int NV>
+__device__ __forceinline__ void stage_operator(const OpData& op, int K, CtaShared<T, NV>& sh) {
+  for (int t = threadIdx.x; t < MMAX * 8; t += blockDim.x) {
+    const int c = t >> 3, j = t & 7;
+    sh.A[c][j] = (c < op.m && j < K) ? OpT<T>::A(op, c * K + j) : T(0);
   }
-  po.dg = valid ? __ldg(OpT<T>::diag(op) + i) : T(0);
-  po.wi = (op.has_w && valid) ? __ldg(OpT<T>::w(op) + i) : T(1);
-#pragma unroll
-  for (int c = 0; c < MMAX; ++c)
-    if (c < op.m) po.dv[c] = valid ? __ldg(OpT<T>::D(op) + c * ld + i) : T(0);
+  if (threadIdx.x < 8) {
+    const int j = threadIdx.x;
+    sh.tau[j] = j < K ? OpT<T>::tau(op, j) : T(0);
+    sh.tk2[j] = j < K ? OpT<T>::tk2(op, j) : T(0);
+  }
 }
 
-// acc = G x at pixel i for one column: x points at the column's k x ld block.
-template <int K, typename T, typename TX>
-__device__ __forceinline__ void apply_pixel(const OpData& op, const PixelOp<T>& po,
-                                            const T* s_A, const T* s_tau, const T* s_tk2,
+template <typename T, int NV>
+__device__ __forceinline__ void zero_wacc(CtaShared<T, NV>& sh, int R) {
+  const int nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < R * nw * NV; t += blockDim.x) {
+    const int r = t / (nw * NV), rem = t - r * nw * NV;
+    sh.wacc[r][rem / NV][rem % NV] = 0.0;
+  }
+}
+
+// Reads K entries of a padded row with 16-byte shared-memory loads.
+template <int K, typename T>
+__device__ __forceinline__ void load_row(const T* row, T (&a)[K]) {
+  constexpr int V = 16 / sizeof(T);
+#pragma unroll
+  for (int q = 0; q < (K + V - 1) / V; ++q) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(row + 4 * q);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (4 * q + t < K) a[4 * q + t] = vv[t];
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(row + 2 * q);
+      const double vv[2] = {v.x, v.y};
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        if (2 * q + t < K) a[2 * q + t] = vv[t];
+    }
+  }
+}
+
+// acc = (G x)_i for one column: x points at the column's k x ld block, xi holds x at pixel i.
+template <int K, typename T, typename TX, int NV>
+__device__ __forceinline__ void apply_pixel(const OpData& op, const CtaShared<T, NV>& sh,
                                             const TX* __restrict__ x, int64_t i,
                                             const T (&xi)[K], T (&acc)[K]) {
   const int64_t ld = op.ld;
+  const T dg = __ldg(OpT<T>::diag(op) + i);
+  const T wi = op.has_w ? __ldg(OpT<T>::w(op) + i) : T(1);
   T lap[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) lap[j] = po.dg * xi[j];
+  for (int j = 0; j < K; ++j) lap[j] = dg * xi[j];
 #pragma unroll
   for (int e = 0; e < EMAX; ++e) {
     if (e < op.E) {
-      const int64_t cidx = po.col[e];
-      const T v = po.val[e];
+      const int64_t c = __ldg(op.ell_col + e * ld + i);
+      const T v = __ldg(OpT<T>::val(op) + e * ld + i);
 #pragma unroll
-      for (int j = 0; j < K; ++j) lap[j] += v * T(x[j * ld + cidx]);
+      for (int j = 0; j < K; ++j) lap[j] += v * T(x[j * ld + c]);
     }
   }
 #pragma unroll
-  for (int j = 0; j < K; ++j) acc[j] = s_tk2[j] * po.wi * xi[j] + s_tau[j] * lap[j];
+  for (int j = 0; j < K; ++j) acc[j] = sh.tk2[j] * wi * xi[j] + sh.tau[j] * lap[j];
 #pragma unroll
   for (int c = 0; c < MMAX; ++c) {
     if (c < op.m) {
+      const T d = __ldg(OpT<T>::D(op) + c * ld + i);
+      T a[K];
+      load_row<K, T>(sh.A[c], a);
       T t = T(0);
 #pragma unroll
-      for (int j = 0; j < K; ++j) t += s_A[c * K + j] * xi[j];
-      t *= po.dv[c];
+      for (int j = 0; j < K; ++j) t += a[j] * xi[j];
+      t *= d;
 #pragma unroll
-      for (int j = 0; j < K; ++j) acc[j] += s_A[c * K + j] * t;
+      for (int j = 0; j < K; ++j) acc[j] += a[j] * t;
     }
   }
 }
@@ -178,54 +184,57 @@ __device__ __forceinline__ void apply_pixel(const OpData& op, const PixelOp<T>& 
 // SPD even where rounding makes the scaled block look singular.
 template <int K, typename T>
 struct BlockChol {
-  T s[K];               // scaling
-  T l[K * (K + 1) / 2]; // packed lower factor, row-major; diagonal entries stored inverted
+  T s[K];                // scaling
+  T l[K * (K + 1) / 2];  // packed lower factor, row-major; diagonal entries stored inverted
 };
 
-template <int K, typename T>
-__device__ __forceinline__ void block_chol(const OpData& op, const PixelOp<T>& po, const T* s_A,
-                                           const T* s_tau, const T* s_tk2, BlockChol<K, T>& f) {
+template <int K, typename T, int NV>
+__device__ __forceinline__ void block_chol(const OpData& op, const CtaShared<T, NV>& sh,
+                                           int64_t i, BlockChol<K, T>& f) {
+  const int64_t ld = op.ld;
   T P[K * (K + 1) / 2];
 #pragma unroll
-  for (int a = 0; a < K; ++a)
-#pragma unroll
-    for (int b = 0; b <= a; ++b) P[a * (a + 1) / 2 + b] = T(0);
+  for (int a = 0; a < K * (K + 1) / 2; ++a) P[a] = T(0);
 #pragma unroll
   for (int c = 0; c < MMAX; ++c) {
     if (c < op.m) {
-      const T d = po.dv[c];
+      const T d = __ldg(OpT<T>::D(op) + c * ld + i);
+      T a[K];
+      load_row<K, T>(sh.A[c], a);
 #pragma unroll
-      for (int a = 0; a < K; ++a) {
-        const T da = d * s_A[c * K + a];
+      for (int u = 0; u < K; ++u) {
+        const T du = d * a[u];
 #pragma unroll
-        for (int b = 0; b <= a; ++b) P[a * (a + 1) / 2 + b] += da * s_A[c * K + b];
+        for (int v = 0; v <= u; ++v) P[u * (u + 1) / 2 + v] += du * a[v];
       }
     }
   }
+  const T dg = __ldg(OpT<T>::diag(op) + i);
+  const T wi = op.has_w ? __ldg(OpT<T>::w(op) + i) : T(1);
 #pragma unroll
-  for (int a = 0; a < K; ++a) P[a * (a + 1) / 2 + a] += s_tk2[a] * po.wi + s_tau[a] * po.dg;
+  for (int u = 0; u < K; ++u) P[u * (u + 1) / 2 + u] += sh.tk2[u] * wi + sh.tau[u] * dg;
 #pragma unroll
-  for (int a = 0; a < K; ++a) {
-    const T pa = P[a * (a + 1) / 2 + a];
-    f.s[a] = pa > T(0) ? T(1) / sqrt(pa) : T(1);
+  for (int u = 0; u < K; ++u) {
+    const T pu = P[u * (u + 1) / 2 + u];
+    f.s[u] = pu > T(0) ? T(1) / sqrt(pu) : T(1);
   }
 #pragma unroll
-  for (int a = 0; a < K; ++a)
+  for (int u = 0; u < K; ++u)
 #pragma unroll
-    for (int b = 0; b <= a; ++b) P[a * (a + 1) / 2 + b] *= f.s[a] * f.s[b];
+    for (int v = 0; v <= u; ++v) P[u * (u + 1) / 2 + v] *= f.s[u] * f.s[v];
   const T floor_piv = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
 #pragma unroll
-  for (int a = 0; a < K; ++a) {
+  for (int u = 0; u < K; ++u) {
 #pragma unroll
-    for (int b = 0; b <= a; ++b) {
-      T v = P[a * (a + 1) / 2 + b];
+    for (int v = 0; v <= u; ++v) {
+      T x = P[u * (u + 1) / 2 + v];
 #pragma unroll
-      for (int c = 0; c < b; ++c) v -= f.l[a * (a + 1) / 2 + c] * f.l[b * (b + 1) / 2 + c];
-      if (a == b) {
-        v = v > floor_piv ? v : floor_piv;
-        f.l[a * (a + 1) / 2 + a] = T(1) / sqrt(v);
+      for (int c = 0; c < v; ++c) x -= f.l[u * (u + 1) / 2 + c] * f.l[v * (v + 1) / 2 + c];
+      if (u == v) {
+        x = x > floor_piv ? x : floor_piv;
+        f.l[u * (u + 1) / 2 + u] = T(1) / sqrt(x);
       } else {
-        f.l[a * (a + 1) / 2 + b] = v * f.l[b * (b + 1) / 2 + b];
+        f.l[u * (u + 1) / 2 + v] = x * f.l[v * (v + 1) / 2 + v];
       }
     }
   }
@@ -253,37 +262,69 @@ __device__ __forceinline__ void block_solve(const BlockChol<K, T>& f, const T (&
   for (int a = 0; a < K; ++a) z[a] *= f.s[a];
 }
 
-// Shared per-CTA prologue: system, tile, per-column flags and scalars, mixing in shared memory.
-template <int K, typename T>
-struct CtaCommon {
-  T A[MMAX * K];
-  T tau[K];
-  T tk2[K];
-  T sc[RMAX];       // per-column scalar (beta or alpha)
-  int act[RMAX];
-  int aux[RMAX];    // per-column flag (first, or phase)
-  double red[32 * 4];
-  int flag;
-};
-
-template <int K, typename T>
-__device__ __forceinline__ void load_mixing(const OpData& op, CtaCommon<K, T>& cc) {
-  for (int t = threadIdx.x; t < op.m * K; t += blockDim.x) cc.A[t] = OpT<T>::A(op, t);
-  if (threadIdx.x < K) {
-    cc.tau[threadIdx.x] = OpT<T>::tau(op, threadIdx.x);
-    cc.tk2[threadIdx.x] = OpT<T>::tk2(op, threadIdx.x);
+// Adds this warp's share of NV sums of column r into the CTA's per-warp accumulators.
+template <typename T, int NV>
+__device__ __forceinline__ void warp_accumulate(CtaShared<T, NV>& sh, int r,
+                                                const double (&v)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const double s = warp_sum(v[t]);
+    if (lane == 0) sh.wacc[r][warp][t] += s;
   }
+}
+
+// Writes this CTA's partials, then returns true in the last CTA of the system to arrive, which
+// then holds the fixed-order totals of every active column in sh.red[r * NV + t] (thread 0).
+template <typename T, int NV>
+__device__ __forceinline__ bool finish_partials(const SysDesc& sd, int slot,
+                                                CtaShared<T, NV>& sh, int R,
+                                                double (&tot)[RMAX][NV]) {
+  const int nw = blockDim.x >> 5;
+  __syncthreads();
+  for (int t = threadIdx.x; t < R * NV; t += blockDim.x) {
+    const int r = t / NV, v = t - r * NV;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh.wacc[r][w][v];
+    sd.partial[((size_t)slot * R + r) * NPART + v] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(sd.counter, 1u);
+    sh.flag = (prev == (unsigned)sd.nslots - 1u) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!sh.flag) return false;
+  __threadfence();
+  for (int r = 0; r < R; ++r) {
+    if (!sh.act[r]) continue;
+    double acc[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] = 0.0;
+    for (int sl = threadIdx.x; sl < sd.nslots; sl += blockDim.x) {
+      const double* p = sd.partial + ((size_t)sl * R + r) * NPART;
+#pragma unroll
+      for (int t = 0; t < NV; ++t) acc[t] += __ldcg(p + t);
+    }
+    block_sum<NV>(acc, sh.red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int t = 0; t < NV; ++t) tot[r][t] = acc[t];
+    }
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------------
 // inner_apply: p = z + beta p, q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
 template <int K, typename T>
-__global__ void __launch_bounds__(MAX_BLOCK)
-k_inner_apply(const SysDesc* __restrict__ descs, const TileRef* __restrict__ tiles, Control* ctl) {
-  __shared__ CtaCommon<K, T> cc;
-  const TileRef tr = tiles[blockIdx.x];
-  const SysDesc& sd = descs[tr.sys];
+__global__ void __launch_bounds__(256, 4)
+k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, Control* ctl) {
+  __shared__ CtaShared<T, 1> sh;
+  const CtaRef cr = ctas[blockIdx.x];
+  const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
   int act = 0;
@@ -292,60 +333,57 @@ k_inner_apply(const SysDesc* __restrict__ descs, const TileRef* __restrict__ til
     if (r < R) {
       const ColState& cs = sd.st[r];
       act = cs.phase == PH_INNER;
-      cc.sc[r] = T(cs.beta);
-      cc.aux[r] = cs.first;
+      sh.sc[r] = T(cs.beta);
+      sh.aux[r] = cs.first;
     }
-    cc.act[r] = act;
+    sh.act[r] = act;
   }
-  load_mixing<K, T>(op, cc);
+  stage_operator<T, 1>(op, K, sh);
+  zero_wacc<T, 1>(sh, R);
   if (!__syncthreads_or(act)) return;
 
-  const int64_t ld = op.ld;
-  const int64_t i = (int64_t)tr.tile * sd.tile_px + threadIdx.x;
-  const bool valid = threadIdx.x < sd.tile_px && i < op.n;
-  PixelOp<T> po;
-  load_pixel_op<T>(op, i, valid, true, po);
-
-  for (int r = 0; r < R; ++r) {
-    if (!cc.act[r]) continue;
-    const size_t off = (size_t)r * K * ld;
-    const T* z = (const T*)sd.vz + off;
-    T* p = (T*)sd.vp + off;
-    T* q = (T*)sd.vq + off;
-    T zi[K], w[K];
+  const int64_t ld = op.ld, n = op.n;
+  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+    const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
+    const bool valid = i0 < n;
+    const int64_t i = valid ? i0 : 0;
+    for (int r = 0; r < R; ++r) {
+      if (!sh.act[r]) continue;
+      const size_t off = (size_t)r * K * ld;
+      const T* z = (const T*)sd.vz + off;
+      T* p = (T*)sd.vp + off;
+      T* q = (T*)sd.vq + off;
+      T zi[K], w[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) zi[j] = valid ? z[j * ld + i] : T(0);
-    apply_pixel<K, T, T>(op, po, cc.A, cc.tau, cc.tk2, z, i, zi, w);
-    T pq = T(0);
-    if (valid) {
-      const T beta = cc.sc[r];
-      const bool first = cc.aux[r] != 0;
+      for (int j = 0; j < K; ++j) zi[j] = z[j * ld + i];
+      apply_pixel<K, T, T, 1>(op, sh, z, i, zi, w);
+      T pq = T(0);
+      if (valid) {
+        const T beta = sh.sc[r];
+        const bool first = sh.aux[r] != 0;
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        T pj = zi[j], qj = w[j];
-        if (!first) {
-          pj += beta * p[j * ld + i];
-          qj += beta * q[j * ld + i];
+        for (int j = 0; j < K; ++j) {
+          T pj = zi[j], qj = w[j];
+          if (!first) {
+            pj += beta * p[j * ld + i];
+            qj += beta * q[j * ld + i];
+          }
+          p[j * ld + i] = pj;
+          q[j * ld + i] = qj;
+          pq += pj * qj;
         }
-        p[j * ld + i] = pj;
-        q[j * ld + i] = qj;
-        pq += pj * qj;
       }
+      const double v[1] = {double(pq)};
+      warp_accumulate<T, 1>(sh, r, v);
     }
-    double v[1] = {double(pq)};
-    block_sum<1>(v, cc.red);
-    if (threadIdx.x == 0) sd.partial[((size_t)tr.tile * R + r) * NPART + 0] = v[0];
   }
-  __syncthreads();
-  if (!arrive_last(sd.counter, (unsigned)sd.ntiles, &cc.flag)) return;
-  for (int r = 0; r < R; ++r) {
-    if (!cc.act[r]) continue;
-    const int idx[1] = {0};
-    double tot[1];
-    reduce_partials<1>(sd, r, idx, tot, cc.red);
-    if (threadIdx.x == 0) {
+  double tot[RMAX][1];
+  if (!finish_partials<T, 1>(sd, cr.slot, sh, R, tot)) return;
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < R; ++r) {
+      if (!sh.act[r]) continue;
       ColState& cs = sd.st[r];
-      const double pq = tot[0];
+      const double pq = tot[r][0];
       if (pq > 0.0 && isfinite(pq)) {
         cs.alpha = cs.gamma / pq;
         cs.first = 0;
@@ -359,20 +397,20 @@ k_inner_apply(const SysDesc* __restrict__ descs, const TileRef* __restrict__ til
         atomicSub(&ctl->n_unfinished, 1u);
       }
     }
+    *sd.counter = 0u;
   }
-  if (threadIdx.x == 0) *sd.counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------------------
 // inner_update: d += alpha p, r -= alpha q, z = P^{-1} r, partial r . z and r . r
 // ---------------------------------------------------------------------------------------------
 template <int K, typename T>
-__global__ void __launch_bounds__(MAX_BLOCK)
-k_inner_update(const SysDesc* __restrict__ descs, const TileRef* __restrict__ tiles,
+__global__ void __launch_bounds__(256, 4)
+k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
                Control* ctl) {
-  __shared__ CtaCommon<K, T> cc;
-  const TileRef tr = tiles[blockIdx.x];
-  const SysDesc& sd = descs[tr.sys];
+  __shared__ CtaShared<T, 2> sh;
+  const CtaRef cr = ctas[blockIdx.x];
+  const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
   int act = 0;
@@ -381,72 +419,64 @@ k_inner_update(const SysDesc* __restrict__ descs, const TileRef* __restrict__ ti
     if (r < R) {
       const ColState& cs = sd.st[r];
       act = cs.phase == PH_INNER;
-      cc.sc[r] = T(cs.alpha);
+      sh.sc[r] = T(cs.alpha);
     }
-    cc.act[r] = act;
+    sh.act[r] = act;
   }
-  load_mixing<K, T>(op, cc);
+  stage_operator<T, 2>(op, K, sh);
+  zero_wacc<T, 2>(sh, R);
   if (!__syncthreads_or(act)) return;
 
-  const int64_t ld = op.ld;
-  const int64_t i = (int64_t)tr.tile * sd.tile_px + threadIdx.x;
-  const bool valid = threadIdx.x < sd.tile_px && i < op.n;
+  const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
-  BlockChol<K, T> f;
-  if (prec) {
-    PixelOp<T> po;
-    load_pixel_op<T>(op, i, valid, false, po);
-    block_chol<K, T>(op, po, cc.A, cc.tau, cc.tk2, f);
-  }
-  for (int r = 0; r < R; ++r) {
-    if (!cc.act[r]) continue;
-    const size_t off = (size_t)r * K * ld;
-    T* d = (T*)sd.vd + off;
-    T* rv = (T*)sd.vr + off;
-    T* z = (T*)sd.vz + off;
-    const T* p = (const T*)sd.vp + off;
-    const T* q = (const T*)sd.vq + off;
-    const T alpha = cc.sc[r];
-    T rz = T(0), rr = T(0);
-    if (valid) {
-      T ri[K], zi[K];
+  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+    const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
+    const bool valid = i0 < n;
+    const int64_t i = valid ? i0 : 0;
+    BlockChol<K, T> f;
+    if (prec) block_chol<K, T, 2>(op, sh, i, f);
+    for (int r = 0; r < R; ++r) {
+      if (!sh.act[r]) continue;
+      const size_t off = (size_t)r * K * ld;
+      T* d = (T*)sd.vd + off;
+      T* rv = (T*)sd.vr + off;
+      T* z = (T*)sd.vz + off;
+      const T* p = (const T*)sd.vp + off;
+      const T* q = (const T*)sd.vq + off;
+      const T alpha = sh.sc[r];
+      T rz = T(0), rr = T(0);
+      if (valid) {
+        T ri[K], zi[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        d[j * ld + i] += alpha * p[j * ld + i];
-        ri[j] = rv[j * ld + i] - alpha * q[j * ld + i];
-        rv[j * ld + i] = ri[j];
-      }
-      if (prec) {
-        block_solve<K, T>(f, ri, zi);
-      } else {
+        for (int j = 0; j < K; ++j) {
+          d[j * ld + i] += alpha * p[j * ld + i];
+          ri[j] = rv[j * ld + i] - alpha * q[j * ld + i];
+          rv[j * ld + i] = ri[j];
+        }
+        if (prec) {
+          block_solve<K, T>(f, ri, zi);
+        } else {
 #pragma unroll
-        for (int j = 0; j < K; ++j) zi[j] = ri[j];
-      }
+          for (int j = 0; j < K; ++j) zi[j] = ri[j];
+        }
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        z[j * ld + i] = zi[j];
-        rz += ri[j] * zi[j];
-        rr += ri[j] * ri[j];
+        for (int j = 0; j < K; ++j) {
+          z[j * ld + i] = zi[j];
+          rz += ri[j] * zi[j];
+          rr += ri[j] * ri[j];
+        }
       }
-    }
-    double v[2] = {double(rz), double(rr)};
-    block_sum<2>(v, cc.red);
-    if (threadIdx.x == 0) {
-      double* pp = sd.partial + ((size_t)tr.tile * R + r) * NPART;
-      pp[0] = v[0];
-      pp[1] = v[1];
+      const double v[2] = {double(rz), double(rr)};
+      warp_accumulate<T, 2>(sh, r, v);
     }
   }
-  __syncthreads();
-  if (!arrive_last(sd.counter, (unsigned)sd.ntiles, &cc.flag)) return;
-  for (int r = 0; r < R; ++r) {
-    if (!cc.act[r]) continue;
-    const int idx[2] = {0, 1};
-    double tot[2];
-    reduce_partials<2>(sd, r, idx, tot, cc.red);
-    if (threadIdx.x == 0) {
+  double tot[RMAX][2];
+  if (!finish_partials<T, 2>(sd, cr.slot, sh, R, tot)) return;
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < R; ++r) {
+      if (!sh.act[r]) continue;
       ColState& cs = sd.st[r];
-      const double rz = tot[0], rr = tot[1];
+      const double rz = tot[r][0], rr = tot[r][1];
       cs.it += 1;
       cs.rr_in = rr;
       if (!isfinite(rz) || !isfinite(rr)) {
@@ -471,28 +501,30 @@ k_inner_update(const SysDesc* __restrict__ descs, const TileRef* __restrict__ ti
         cs.gamma = rz;
       }
     }
+    *sd.counter = 0u;
   }
-  if (threadIdx.x == 0) *sd.counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------------------
 // update_x: X += d for columns whose inner solve finished
 // ---------------------------------------------------------------------------------------------
 template <int K, typename T>
-__global__ void __launch_bounds__(MAX_BLOCK)
-k_update_x(const SysDesc* __restrict__ descs, const TileRef* __restrict__ tiles) {
-  const TileRef tr = tiles[blockIdx.x];
-  const SysDesc& sd = descs[tr.sys];
-  const int64_t ld = sd.op.ld;
-  const int64_t i = (int64_t)tr.tile * sd.tile_px + threadIdx.x;
-  if (threadIdx.x >= sd.tile_px || i >= sd.op.n) return;
+__global__ void __launch_bounds__(256)
+k_update_x(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas) {
+  const CtaRef cr = ctas[blockIdx.x];
+  const SysDesc& sd = descs[cr.sys];
+  const int64_t ld = sd.op.ld, n = sd.op.n;
   for (int r = 0; r < sd.R; ++r) {
     if (sd.st[r].phase != PH_INNER_DONE) continue;
     const size_t off = (size_t)r * K * ld;
     const T* d = (const T*)sd.vd + off;
     double* X = sd.X + off;
+    for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+      const int64_t i = (int64_t)tile * blockDim.x + threadIdx.x;
+      if (i >= n) continue;
 #pragma unroll
-    for (int j = 0; j < K; ++j) X[j * ld + i] += double(d[j * ld + i]);
+      for (int j = 0; j < K; ++j) X[j * ld + i] += double(d[j * ld + i]);
+    }
   }
 }
 
@@ -500,13 +532,12 @@ k_update_x(const SysDesc* __restrict__ descs, const TileRef* __restrict__ tiles)
 // residual: r64 = B - G X (FP64), r_in = r64 rounded, d = 0, z = P^{-1} r_in; decisions
 // ---------------------------------------------------------------------------------------------
 template <int K, typename T>
-__global__ void __launch_bounds__(MAX_BLOCK)
-k_residual(const SysDesc* __restrict__ descs, const TileRef* __restrict__ tiles, Control* ctl) {
-  __shared__ CtaCommon<K, double> cd;   // FP64 operator
-  __shared__ T sA[MMAX * K];            // inner-type preconditioner data
-  __shared__ T stau[K], stk2[K];
-  const TileRef tr = tiles[blockIdx.x];
-  const SysDesc& sd = descs[tr.sys];
+__global__ void __launch_bounds__(256)
+k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, Control* ctl) {
+  __shared__ CtaShared<double, 4> sh;     // FP64 operator
+  __shared__ CtaShared<T, 1> shT;         // inner-type preconditioner data
+  const CtaRef cr = ctas[blockIdx.x];
+  const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
   int act = 0;
@@ -517,88 +548,71 @@ k_residual(const SysDesc* __restrict__ descs, const TileRef* __restrict__ tiles,
       ph = sd.st[r].phase;
       act = (ph == PH_START || ph == PH_INNER_DONE);
     }
-    cd.act[r] = act;
-    cd.aux[r] = ph;
+    sh.act[r] = act;
   }
-  load_mixing<K, double>(op, cd);
-  for (int t = threadIdx.x; t < op.m * K; t += blockDim.x) sA[t] = OpT<T>::A(op, t);
-  if (threadIdx.x < K) {
-    stau[threadIdx.x] = OpT<T>::tau(op, threadIdx.x);
-    stk2[threadIdx.x] = OpT<T>::tk2(op, threadIdx.x);
-  }
+  stage_operator<double, 4>(op, K, sh);
+  stage_operator<T, 1>(op, K, shT);
+  zero_wacc<double, 4>(sh, R);
   if (!__syncthreads_or(act)) return;
 
-  const int64_t ld = op.ld;
-  const int64_t i = (int64_t)tr.tile * sd.tile_px + threadIdx.x;
-  const bool valid = threadIdx.x < sd.tile_px && i < op.n;
-  PixelOp<double> po;
-  load_pixel_op<double>(op, i, valid, true, po);
+  const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
-  BlockChol<K, T> f;
-  if (prec) {
-    PixelOp<T> pt;
-    load_pixel_op<T>(op, i, valid, false, pt);
-    block_chol<K, T>(op, pt, sA, stau, stk2, f);
-  }
-  for (int r = 0; r < R; ++r) {
-    if (!cd.act[r]) continue;
-    const size_t off = (size_t)r * K * ld;
-    const double* X = sd.X + off;
-    const double* B = sd.B + off;
-    T* d = (T*)sd.vd + off;
-    T* rv = (T*)sd.vr + off;
-    T* z = (T*)sd.vz + off;
-    double rr64 = 0.0, bb = 0.0, rz = 0.0, rr = 0.0;
-    if (valid) {
+  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+    const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
+    const bool valid = i0 < n;
+    const int64_t i = valid ? i0 : 0;
+    BlockChol<K, T> f;
+    if (prec) block_chol<K, T, 1>(op, shT, i, f);
+    for (int r = 0; r < R; ++r) {
+      if (!sh.act[r]) continue;
+      const size_t off = (size_t)r * K * ld;
+      const double* X = sd.X + off;
+      const double* B = sd.B + off;
+      T* d = (T*)sd.vd + off;
+      T* rv = (T*)sd.vr + off;
+      T* z = (T*)sd.vz + off;
       double xi[K], gx[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) xi[j] = X[j * ld + i];
-      apply_pixel<K, double, double>(op, po, cd.A, cd.tau, cd.tk2, X, i, xi, gx);
-      T ri[K], zi[K];
+      apply_pixel<K, double, double, 4>(op, sh, X, i, xi, gx);
+      double rr64 = 0.0, bb = 0.0, rz = 0.0, rr = 0.0;
+      if (valid) {
+        T ri[K], zi[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const double bj = B[j * ld + i];
-        const double r64 = bj - gx[j];
-        rr64 += r64 * r64;
-        bb += bj * bj;
-        ri[j] = T(r64);
-        rv[j * ld + i] = ri[j];
-        d[j * ld + i] = T(0);
-      }
-      if (prec) {
-        block_solve<K, T>(f, ri, zi);
-      } else {
+        for (int j = 0; j < K; ++j) {
+          const double bj = B[j * ld + i];
+          const double r64 = bj - gx[j];
+          rr64 += r64 * r64;
+          bb += bj * bj;
+          ri[j] = T(r64);
+          rv[j * ld + i] = ri[j];
+          d[j * ld + i] = T(0);
+        }
+        if (prec) {
+          block_solve<K, T>(f, ri, zi);
+        } else {
 #pragma unroll
-        for (int j = 0; j < K; ++j) zi[j] = ri[j];
-      }
+          for (int j = 0; j < K; ++j) zi[j] = ri[j];
+        }
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        z[j * ld + i] = zi[j];
-        rz += double(ri[j]) * double(zi[j]);
-        rr += double(ri[j]) * double(ri[j]);
+        for (int j = 0; j < K; ++j) {
+          z[j * ld + i] = zi[j];
+          rz += double(ri[j]) * double(zi[j]);
+          rr += double(ri[j]) * double(ri[j]);
+        }
       }
-    }
-    double v[4] = {rr64, bb, rz, rr};
-    block_sum<4>(v, cd.red);
-    if (threadIdx.x == 0) {
-      double* pp = sd.partial + ((size_t)tr.tile * R + r) * NPART;
-      pp[0] = v[0];
-      pp[1] = v[1];
-      pp[2] = v[2];
-      pp[3] = v[3];
+      const double v[4] = {rr64, bb, rz, rr};
+      warp_accumulate<double, 4>(sh, r, v);
     }
   }
-  __syncthreads();
-  if (!arrive_last(sd.counter, (unsigned)sd.ntiles, &cd.flag)) return;
-  for (int r = 0; r < R; ++r) {
-    if (!cd.act[r]) continue;
-    const int idx[4] = {0, 1, 2, 3};
-    double tot[4];
-    reduce_partials<4>(sd, r, idx, tot, cd.red);
-    if (threadIdx.x == 0) {
+  double tot[RMAX][4];
+  if (!finish_partials<double, 4>(sd, cr.slot, sh, R, tot)) return;
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < R; ++r) {
+      if (!sh.act[r]) continue;
       ColState& cs = sd.st[r];
-      const double rr64 = tot[0], rz = tot[2], rr = tot[3];
-      if (cs.phase == PH_START) cs.bnorm2 = tot[1];
+      const double rr64 = tot[r][0], rz = tot[r][2], rr = tot[r][3];
+      if (cs.phase == PH_START) cs.bnorm2 = tot[r][1];
       cs.rr64 = rr64;
       const double den = cs.bnorm2 > 0.0 ? cs.bnorm2 : 1.0;
       const double rel2 = rr64 / den;
@@ -635,64 +649,93 @@ k_residual(const SysDesc* __restrict__ descs, const TileRef* __restrict__ tiles,
         atomicAdd(&ctl->n_active, 1u);
       }
     }
+    *sd.counter = 0u;
   }
-  if (threadIdx.x == 0) *sd.counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
-#define SYLV_DISPATCH_K(k, CALL) \
-  switch (k) {                   \
-    case 1: CALL(1); break;      \
-    case 2: CALL(2); break;      \
-    case 3: CALL(3); break;      \
-    case 4: CALL(4); break;      \
-    case 5: CALL(5); break;      \
-    case 6: CALL(6); break;      \
-    case 7: CALL(7); break;      \
-    case 8: CALL(8); break;      \
+#define SYLV_DISPATCH_K(k, CALL)           \
+  switch (k) {                             \
+    case 1: CALL(1); break;                \
+    case 2: CALL(2); break;                \
+    case 3: CALL(3); break;                \
+    case 4: CALL(4); break;                \
+    case 5: CALL(5); break;                \
+    case 6: CALL(6); break;                \
+    case 7: CALL(7); break;                \
+    case 8: CALL(8); break;                \
     default: return cudaErrorInvalidValue; \
   }
 
 template <typename T>
-cudaError_t launch_inner_apply_impl(int k, int ntiles, int block, const SysDesc* d,
-                                    const TileRef* t, Control* c, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-#define CALL(K) k_inner_apply<K, T><<<ntiles, block, 0, s>>>(d, t, c)
+cudaError_t launch_inner_apply_impl(int k, int ncta, int block, const SysDesc* d,
+                                    const CtaRef* c, Control* ctl, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+#define CALL(K) k_inner_apply<K, T><<<ncta, block, 0, s>>>(d, c, ctl)
   SYLV_DISPATCH_K(k, CALL)
 #undef CALL
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_inner_update_impl(int k, int ntiles, int block, const SysDesc* d,
-                                     const TileRef* t, Control* c, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-#define CALL(K) k_inner_update<K, T><<<ntiles, block, 0, s>>>(d, t, c)
+cudaError_t launch_inner_update_impl(int k, int ncta, int block, const SysDesc* d,
+                                     const CtaRef* c, Control* ctl, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+#define CALL(K) k_inner_update<K, T><<<ncta, block, 0, s>>>(d, c, ctl)
   SYLV_DISPATCH_K(k, CALL)
 #undef CALL
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_residual_impl(int k, int ntiles, int block, const SysDesc* d,
-                                 const TileRef* t, Control* c, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-#define CALL(K) k_residual<K, T><<<ntiles, block, 0, s>>>(d, t, c)
+cudaError_t launch_residual_impl(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
+                                 Control* ctl, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+#define CALL(K) k_residual<K, T><<<ncta, block, 0, s>>>(d, c, ctl)
   SYLV_DISPATCH_K(k, CALL)
 #undef CALL
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_update_x_impl(int k, int ntiles, int block, const SysDesc* d,
-                                 const TileRef* t, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-#define CALL(K) k_update_x<K, T><<<ntiles, block, 0, s>>>(d, t)
+cudaError_t launch_update_x_impl(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
+                                 cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+#define CALL(K) k_update_x<K, T><<<ncta, block, 0, s>>>(d, c)
   SYLV_DISPATCH_K(k, CALL)
 #undef CALL
   return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the less occupant inner-iteration kernel for (k, block).
+template <typename T>
+int occupancy_impl(int k, int block) {
+  int best = 1 << 30;
+  auto take = [&](const void* fn) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) == cudaSuccess)
+      best = nb < best ? nb : best;
+  };
+#define CALL(K)                                        \
+  do {                                                 \
+    take((const void*)k_inner_apply<K, T>);            \
+    take((const void*)k_inner_update<K, T>);           \
+  } while (0)
+  switch (k) {
+    case 1: CALL(1); break;
+    case 2: CALL(2); break;
+    case 3: CALL(3); break;
+    case 4: CALL(4); break;
+    case 5: CALL(5); break;
+    case 6: CALL(6); break;
+    case 7: CALL(7); break;
+    case 8: CALL(8); break;
+    default: return 1;
+  }
+#undef CALL
+  return best == (1 << 30) || best < 1 ? 1 : best;
 }
 
 }  // namespace sylv

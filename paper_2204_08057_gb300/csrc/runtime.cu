@@ -70,8 +70,8 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 struct Group {
   int k = 0;
   int block = 256;
-  int ntiles = 0;
-  TileRef* d_tiles = nullptr;
+  int ncta = 0;             // CTAs of every iteration launch over this group
+  CtaRef* d_ctas = nullptr;
 };
 
 struct SysWork {
@@ -128,7 +128,7 @@ struct sylv_ctx {
 };
 
 Plan::~Plan() {
-  for (auto& g : groups) cudaFree(g.d_tiles);
+  for (auto& g : groups) cudaFree(g.d_ctas);
   for (auto& w : work) {
     cudaFree(w.vec);
     cudaFree(w.st);
@@ -169,26 +169,36 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
   P.inner_double = inner_double;
   const size_t tsz = inner_double ? sizeof(double) : sizeof(float);
   P.work.resize(nsys);
-  // groups by k
+  // groups by k; each system of a group gets CTA slots in proportion to its tiles, and the
+  // launch is sized to what the device keeps resident (nothing relies on residency: no CTA
+  // ever waits for another)
+  int dev = 0, nsm = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   std::map<int, std::vector<int>> byk;
   for (int s = 0; s < nsys; ++s) byk[hs[s]->op.k].push_back(s);
-  std::vector<int> tile_px(nsys);
-  std::vector<int> ntiles(nsys);
+  std::vector<int> nslots(nsys), ntiles(nsys);
   for (auto& kv : byk) {
     Group g;
     g.k = kv.first;
-    int64_t nmax = 0;
-    for (int s : kv.second) nmax = std::max(nmax, hs[s]->op.n);
-    g.block = default_block(nmax);
-    std::vector<TileRef> tl;
+    g.block = default_block(0);
+    const int occ = inner_double ? occupancy<double>(g.k, g.block)
+                                 : occupancy<float>(g.k, g.block);
+    const int64_t budget = (int64_t)nsm * std::max(occ, 1);
+    int64_t total = 0;
     for (int s : kv.second) {
-      tile_px[s] = g.block;
       ntiles[s] = (int)ceil_div(hs[s]->op.n, g.block);
-      for (int t = 0; t < ntiles[s]; ++t) tl.push_back(TileRef{s, t});
+      total += ntiles[s];
     }
-    g.ntiles = (int)tl.size();
-    CK(dalloc(&g.d_tiles, tl.size() * sizeof(TileRef)));
-    CK(cudaMemcpy(g.d_tiles, tl.data(), tl.size() * sizeof(TileRef), cudaMemcpyHostToDevice));
+    std::vector<CtaRef> cl;
+    for (int s : kv.second) {
+      int64_t ns = total <= budget ? ntiles[s] : (budget * ntiles[s]) / total;
+      nslots[s] = (int)std::max<int64_t>(1, std::min<int64_t>(ns, ntiles[s]));
+      for (int t = 0; t < nslots[s]; ++t) cl.push_back(CtaRef{s, t});
+    }
+    g.ncta = (int)cl.size();
+    CK(dalloc(&g.d_ctas, cl.size() * sizeof(CtaRef)));
+    CK(cudaMemcpy(g.d_ctas, cl.data(), cl.size() * sizeof(CtaRef), cudaMemcpyHostToDevice));
     P.groups.push_back(g);
   }
   for (int s = 0; s < nsys; ++s) {
@@ -198,7 +208,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     CK(dalloc(&w.vec, 5 * vbytes));
     CK(cudaMemset(w.vec, 0, 5 * vbytes));
     CK(dalloc(&w.st, R[s] * sizeof(ColState)));
-    CK(dalloc(&w.partial, (size_t)ntiles[s] * R[s] * NPART * sizeof(double)));
+    CK(dalloc(&w.partial, (size_t)nslots[s] * R[s] * NPART * sizeof(double)));
     CK(dalloc(&w.counter, sizeof(unsigned int)));
     CK(cudaMemset(w.counter, 0, sizeof(unsigned int)));
     for (int r = 0; r < R[s]; ++r) {
@@ -224,7 +234,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     d.op = hs[s]->op;
     d.R = R[s];
     d.ntiles = ntiles[s];
-    d.tile_px = tile_px[s];
+    d.nslots = nslots[s];
     const size_t vbytes = (size_t)R[s] * d.op.k * d.op.ld * tsz;
     char* base = (char*)P.work[s].vec;
     d.vd = base;
@@ -248,12 +258,12 @@ template <typename T>
 int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
                            bool capture_events) {
   for (auto& g : P.groups)
-    CK(launch_inner_apply<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, P.d_ctl, s));
+    CK(launch_inner_apply<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_mid)
     CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_mid, s));
   for (auto& g : P.groups)
-    CK(launch_inner_update<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, P.d_ctl, s));
+    CK(launch_inner_update<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_end)
     CK(capture_events ? cudaEventRecordWithFlags(e_end, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_end, s));
@@ -311,6 +321,7 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
              sylv_info* infos, cudaStream_t s) {
   const int nsys = (int)P.hs.size();
   for (int t = 0; t < nsys; ++t) {
+    P.h_desc[t].op = P.hs[t]->op;  // operator scalars may have changed since the plan was built
     P.h_desc[t].B = B[t];
     P.h_desc[t].X = X[t];
   }
@@ -354,10 +365,10 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   int rc = SYLV_OK;
   while (true) {
     for (auto& g : P.groups)
-      CK(launch_update_x<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, s));
+      CK(launch_update_x<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, s));
     if (prof) CK(cudaEventRecord(P.evr0, s));
     for (auto& g : P.groups)
-      CK(launch_residual<T>(g.k, g.ntiles, g.block, P.d_desc, g.d_tiles, P.d_ctl, s));
+      CK(launch_residual<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
     if (prof) CK(cudaEventRecord(P.evr1, s));
     launches += 2 * ng;
     if ((rc = poll(P, s)) != SYLV_OK) break;

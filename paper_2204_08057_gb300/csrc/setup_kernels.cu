@@ -1,4 +1,5 @@
 // Set-up, right-hand side, stand-alone operator apply and gradient kernels.
+#include <algorithm>
 #include <cmath>
 
 #include "pcg_kernels.cuh"
@@ -107,36 +108,31 @@ __global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restric
   }
 }
 
-// Stand-alone operator apply Y = G X (eq. block-vector-mapping-matvec with Algorithm 1).
+// Stand-alone operator apply Y = G X (eq. block-vector-mapping-matvec with Algorithm 1);
+// grid-stride over pixels.
 template <int K, typename T>
-__global__ void __launch_bounds__(256) k_apply(OpData op, const T* __restrict__ X,
+__global__ void __launch_bounds__(256, 4) k_apply(OpData op, const T* __restrict__ X,
                                                T* __restrict__ Y, int R) {
-  __shared__ T sA[MMAX * K];
-  __shared__ T stau[K], stk2[K];
-  for (int t = threadIdx.x; t < op.m * K; t += blockDim.x) sA[t] = OpT<T>::A(op, t);
-  if (threadIdx.x < K) {
-    stau[threadIdx.x] = OpT<T>::tau(op, threadIdx.x);
-    stk2[threadIdx.x] = OpT<T>::tk2(op, threadIdx.x);
-  }
+  __shared__ CtaShared<T, 1> sh;
+  stage_operator<T, 1>(op, K, sh);
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= op.n) return;
   const int64_t ld = op.ld;
-  PixelOp<T> po;
-  load_pixel_op<T>(op, i, true, true, po);
-  for (int r = 0; r < R; ++r) {
-    const T* x = X + (size_t)r * K * ld;
-    T* y = Y + (size_t)r * K * ld;
-    T xi[K], acc[K];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < op.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int r = 0; r < R; ++r) {
+      const T* x = X + (size_t)r * K * ld;
+      T* y = Y + (size_t)r * K * ld;
+      T xi[K], acc[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) xi[j] = x[j * ld + i];
-    apply_pixel<K, T, T>(op, po, sA, stau, stk2, x, i, xi, acc);
+      for (int j = 0; j < K; ++j) xi[j] = x[j * ld + i];
+      apply_pixel<K, T, T, 1>(op, sh, x, i, xi, acc);
 #pragma unroll
-    for (int j = 0; j < K; ++j) y[j * ld + i] = acc[j];
+      for (int j = 0; j < K; ++j) y[j * ld + i] = acc[j];
+    }
   }
 }
 
-// Per-tile partial gradients (see sylv_backward); out layout [tau(k), kappa(k), beta(k)].
+// Per-block partial gradients (see sylv_backward); out layout [tau(k), kappa(k), beta(k)].
 template <int K>
 __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restrict__ X,
                                               const double* __restrict__ lam,
@@ -150,8 +146,8 @@ __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restric
 #pragma unroll
   for (int t = 0; t < 3 * K; ++t) g[t] = 0.0;
   if (valid) {
-    PixelOp<double> po;
-    load_pixel_op<double>(op, i, true, true, po);
+    const double dg = op.diag64[i];
+    const double wi = op.has_w ? op.w64[i] : 1.0;
     for (int r = 0; r < R; ++r) {
       const double* x = X + (size_t)r * K * ld;
       const double* l = lam + (size_t)r * K * ld;
@@ -160,21 +156,19 @@ __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restric
       for (int j = 0; j < K; ++j) {
         xi[j] = x[j * ld + i];
         li[j] = l[j * ld + i];
-        Lx[j] = po.dg * xi[j];
+        Lx[j] = dg * xi[j];
       }
+      for (int e = 0; e < op.E; ++e) {
+        const int64_t c = op.ell_col[e * ld + i];
+        const double v = op.ell_val64[e * ld + i];
 #pragma unroll
-      for (int e = 0; e < EMAX; ++e) {
-        if (e < op.E) {
-          const int64_t c = po.col[e];
-#pragma unroll
-          for (int j = 0; j < K; ++j) Lx[j] += po.val[e] * x[j * ld + c];
-        }
+        for (int j = 0; j < K; ++j) Lx[j] += v * x[j * ld + c];
       }
 #pragma unroll
       for (int j = 0; j < K; ++j) {
         const double kap2 = op.kappa64[j] * op.kappa64[j];
-        g[j] -= li[j] * (kap2 * po.wi * xi[j] + Lx[j]);
-        g[K + j] -= 2.0 * op.tau64[j] * op.kappa64[j] * li[j] * po.wi * xi[j];
+        g[j] -= li[j] * (kap2 * wi * xi[j] + Lx[j]);
+        g[K + j] -= 2.0 * op.tau64[j] * op.kappa64[j] * li[j] * wi * xi[j];
       }
       if (want_beta) {
         const double* y = Y + (size_t)r * op.m * ld;
@@ -185,7 +179,7 @@ __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restric
             t += op.A64[c * K + j] * xi[j];
             u += op.A64[c * K + j] * li[j];
           }
-          const double dc = po.dv[c];
+          const double dc = op.D64[c * ld + i];
           const double yc = y[c * ld + i];
 #pragma unroll
           for (int j = 0; j < K; ++j)
@@ -277,7 +271,14 @@ cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cuda
 
 template <typename T>
 cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s) {
-  const int nb = blocks_for(op.n, 256);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const int nb = (int)std::min<int64_t>(blocks_for(op.n, 256), (int64_t)nsm * 8);
 #define CALL(K) k_apply<K, T><<<nb, 256, 0, s>>>(op, X, Y, R)
   SYLV_DISPATCH_K(op.k, CALL)
 #undef CALL

@@ -2,12 +2,13 @@
 //
 // One "system" is one handle (operator) together with nrhs right-hand sides.  A solve runs a
 // list of systems at once (sylv_solve is the one-system case).  Systems are cut into tiles of
-// blockDim.x consecutive pixels; every kernel of the iteration launches one CTA per tile over
-// the tiles of all systems that share a number of sources k, and each right-hand side of
-// each system ("column") carries its own CG scalars and state in a ColState.
+// blockDim.x consecutive pixels.  Every kernel of the iteration is one launch over all systems
+// that share a number of sources k: each system owns `nslots` CTAs (the launch is sized to be
+// resident at once) and CTA `slot` walks the system's tiles slot, slot + nslots, ...  Each
+// right-hand side of each system ("column") carries its own CG scalars and state (ColState).
 //
-// Scalar reductions (dot products) are deterministic: each CTA writes its partial sums for
-// its tile, and the last CTA of a system to finish (detected with an atomic counter, no
+// Scalar reductions (dot products) are deterministic: each CTA writes one partial sum per
+// column, and the last CTA of a system to finish (detected with an atomic counter, no
 // waiting) adds the partials in a fixed order and updates the system's scalars.
 #pragma once
 
@@ -23,7 +24,7 @@ constexpr int MMAX = SYLV_MAX_M;
 constexpr int EMAX = SYLV_MAX_DEGREE;
 constexpr int RMAX = SYLV_MAX_RHS;
 constexpr int NPART = 4;          // partial sums per (tile, column)
-constexpr int MAX_BLOCK = 512;
+constexpr int MAX_BLOCK = 256;
 
 enum Phase : int {
   PH_START = 0,       // before the first FP64 residual
@@ -79,8 +80,8 @@ struct OpData {
 struct SysDesc {
   OpData op;
   int R;                 // right-hand sides
-  int ntiles;            // tiles of this system
-  int tile_px;           // pixels per tile (= blockDim.x of every launch over it)
+  int ntiles;            // tiles of blockDim.x pixels
+  int nslots;            // CTAs working on this system in every iteration kernel
   int pad;
   const double* B;       // R x k x ld
   double* X;             // R x k x ld
@@ -90,7 +91,7 @@ struct SysDesc {
   void* vp;
   void* vq;
   ColState* st;          // R
-  double* partial;       // ntiles x R x NPART
+  double* partial;       // nslots x R x NPART
   unsigned int* counter; // one per system, zero between kernels
 };
 
@@ -106,26 +107,28 @@ struct Control {
   int pad;
 };
 
-struct TileRef {
-  int sys;
-  int tile;
+struct CtaRef {
+  int sys;   // system of this CTA
+  int slot;  // 0..nslots-1 within the system
 };
 
 // ------------------------------------------------------------------------------------------
 // launchers (defined in the kernel translation units)
 // ------------------------------------------------------------------------------------------
 template <typename T>
-cudaError_t launch_inner_apply(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+cudaError_t launch_inner_apply(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
                                Control* c, cudaStream_t s);
 template <typename T>
-cudaError_t launch_inner_update(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+cudaError_t launch_inner_update(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
                                 Control* c, cudaStream_t s);
 template <typename T>
-cudaError_t launch_residual(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+cudaError_t launch_residual(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
                             Control* c, cudaStream_t s);
 template <typename T>
-cudaError_t launch_update_x(int k, int ntiles, int block, const SysDesc* d, const TileRef* t,
+cudaError_t launch_update_x(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
                             cudaStream_t s);
+template <typename T>
+int occupancy(int k, int block);
 cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,
                                const SysDesc* d, Control* c, cudaStream_t s);
 
