@@ -4,29 +4,29 @@
 namespace sylv {
 
 template <>
-cudaError_t launch_inner_apply<float>(int k, int ntiles, int block, const SysDesc* d,
-                                      const CtaRef* t, Control* c, cudaStream_t s) {
-  return launch_inner_apply_impl<float>(k, ntiles, block, d, t, c, s);
+cudaError_t launch_inner_apply<float>(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                                     const CtaRef* c, Control* ctl, cudaStream_t s) {
+  return launch_inner_apply_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_inner_update<float>(int k, int ntiles, int block, const SysDesc* d,
-                                       const CtaRef* t, Control* c, cudaStream_t s) {
-  return launch_inner_update_impl<float>(k, ntiles, block, d, t, c, s);
+cudaError_t launch_inner_update<float>(int k, int m, int e, int ncta, int block,
+                                      const SysDesc* d, const CtaRef* c, Control* ctl,
+                                      cudaStream_t s) {
+  return launch_inner_update_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_residual<float>(int k, int ntiles, int block, const SysDesc* d,
-                                   const CtaRef* t, Control* c, cudaStream_t s) {
-  return launch_residual_impl<float>(k, ntiles, block, d, t, c, s);
+cudaError_t launch_residual<float>(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                                  const CtaRef* c, Control* ctl, cudaStream_t s) {
+  return launch_residual_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_update_x<float>(int k, int ntiles, int block, const SysDesc* d,
-                                   const CtaRef* t, cudaStream_t s) {
-  return launch_update_x_impl<float>(k, ntiles, block, d, t, s);
+cudaError_t launch_update_x<float>(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
+                                  cudaStream_t s) {
+  return launch_update_x_impl<float>(k, ncta, block, d, c, s);
 }
-
 template <>
-int occupancy<float>(int k, int block) {
-  return occupancy_impl<float>(k, block);
+int occupancy<float>(int k, int m, int e, int block) {
+  return occupancy_impl<float>(k, m, e, block);
 }
 
 }  // namespace sylv

@@ -4,29 +4,29 @@
 namespace sylv {
 
 template <>
-cudaError_t launch_inner_apply<double>(int k, int ntiles, int block, const SysDesc* d,
-                                      const CtaRef* t, Control* c, cudaStream_t s) {
-  return launch_inner_apply_impl<double>(k, ntiles, block, d, t, c, s);
+cudaError_t launch_inner_apply<double>(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                                     const CtaRef* c, Control* ctl, cudaStream_t s) {
+  return launch_inner_apply_impl<double>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_inner_update<double>(int k, int ntiles, int block, const SysDesc* d,
-                                       const CtaRef* t, Control* c, cudaStream_t s) {
-  return launch_inner_update_impl<double>(k, ntiles, block, d, t, c, s);
+cudaError_t launch_inner_update<double>(int k, int m, int e, int ncta, int block,
+                                      const SysDesc* d, const CtaRef* c, Control* ctl,
+                                      cudaStream_t s) {
+  return launch_inner_update_impl<double>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_residual<double>(int k, int ntiles, int block, const SysDesc* d,
-                                   const CtaRef* t, Control* c, cudaStream_t s) {
-  return launch_residual_impl<double>(k, ntiles, block, d, t, c, s);
+cudaError_t launch_residual<double>(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                                  const CtaRef* c, Control* ctl, cudaStream_t s) {
+  return launch_residual_impl<double>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_update_x<double>(int k, int ntiles, int block, const SysDesc* d,
-                                   const CtaRef* t, cudaStream_t s) {
-  return launch_update_x_impl<double>(k, ntiles, block, d, t, s);
+cudaError_t launch_update_x<double>(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
+                                  cudaStream_t s) {
+  return launch_update_x_impl<double>(k, ncta, block, d, c, s);
 }
-
 template <>
-int occupancy<double>(int k, int block) {
-  return occupancy_impl<double>(k, block);
+int occupancy<double>(int k, int m, int e, int block) {
+  return occupancy_impl<double>(k, m, e, block);
 }
 
 }  // namespace sylv

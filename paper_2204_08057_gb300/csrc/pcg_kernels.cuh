@@ -140,39 +140,58 @@ __device__ __forceinline__ void load_row(const T* row, T (&a)[K]) {
 }
 
 // acc = (G x)_i for one column: x points at the column's k x ld block, xi holds x at pixel i.
-template <int K, typename T, typename TX, int NV>
+// M and E are the number of channels and the ELL width when known at compile time (0: read
+// from op, loaded in batches of 4 at clamped, always valid addresses so that a batch of loads
+// is issued together).
+template <int K, int M, int E, typename T, typename TX, int NV>
 __device__ __forceinline__ void apply_pixel(const OpData& op, const CtaShared<T, NV>& sh,
                                             const TX* __restrict__ x, int64_t i,
                                             const T (&xi)[K], T (&acc)[K]) {
   const int64_t ld = op.ld;
+  constexpr int EC = E > 0 ? E : 4;
+  constexpr int MC = M > 0 ? M : 4;
+  const int Er = E > 0 ? E : op.E;
+  const int Mr = M > 0 ? M : op.m;
   const T dg = __ldg(OpT<T>::diag(op) + i);
   const T wi = op.has_w ? __ldg(OpT<T>::w(op) + i) : T(1);
   T lap[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) lap[j] = dg * xi[j];
+  for (int e0 = 0; e0 < Er; e0 += EC) {
+    int64_t col[EC];
+    T val[EC];
 #pragma unroll
-  for (int e = 0; e < EMAX; ++e) {
-    if (e < op.E) {
-      const int64_t c = __ldg(op.ell_col + e * ld + i);
-      const T v = __ldg(OpT<T>::val(op) + e * ld + i);
-#pragma unroll
-      for (int j = 0; j < K; ++j) lap[j] += v * T(x[j * ld + c]);
+    for (int t = 0; t < EC; ++t) {
+      const int e = E > 0 ? t : min(e0 + t, Er - 1);
+      col[t] = __ldg(op.ell_col + e * ld + i);
+      val[t] = __ldg(OpT<T>::val(op) + e * ld + i);
+      if (E == 0 && e0 + t >= Er) val[t] = T(0);
     }
+#pragma unroll
+    for (int t = 0; t < EC; ++t)
+#pragma unroll
+      for (int j = 0; j < K; ++j) lap[j] += val[t] * T(x[j * ld + col[t]]);
   }
 #pragma unroll
   for (int j = 0; j < K; ++j) acc[j] = sh.tk2[j] * wi * xi[j] + sh.tau[j] * lap[j];
+  for (int c0 = 0; c0 < Mr; c0 += MC) {
+    T dv[MC];
 #pragma unroll
-  for (int c = 0; c < MMAX; ++c) {
-    if (c < op.m) {
-      const T d = __ldg(OpT<T>::D(op) + c * ld + i);
+    for (int t = 0; t < MC; ++t) {
+      const int c = M > 0 ? t : min(c0 + t, Mr - 1);
+      dv[t] = __ldg(OpT<T>::D(op) + c * ld + i);
+      if (M == 0 && c0 + t >= Mr) dv[t] = T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < MC; ++t) {
       T a[K];
-      load_row<K, T>(sh.A[c], a);
-      T t = T(0);
+      load_row<K, T>(sh.A[c0 + t], a);   // rows past m are zero
+      T u = T(0);
 #pragma unroll
-      for (int j = 0; j < K; ++j) t += a[j] * xi[j];
-      t *= d;
+      for (int j = 0; j < K; ++j) u += a[j] * xi[j];
+      u *= dv[t];
 #pragma unroll
-      for (int j = 0; j < K; ++j) acc[j] += a[j] * t;
+      for (int j = 0; j < K; ++j) acc[j] += a[j] * u;
     }
   }
 }
@@ -188,22 +207,30 @@ struct BlockChol {
   T l[K * (K + 1) / 2];  // packed lower factor, row-major; diagonal entries stored inverted
 };
 
-template <int K, typename T, int NV>
+template <int K, int M, typename T, int NV>
 __device__ __forceinline__ void block_chol(const OpData& op, const CtaShared<T, NV>& sh,
                                            int64_t i, BlockChol<K, T>& f) {
   const int64_t ld = op.ld;
+  constexpr int MC = M > 0 ? M : 4;
+  const int Mr = M > 0 ? M : op.m;
   T P[K * (K + 1) / 2];
 #pragma unroll
   for (int a = 0; a < K * (K + 1) / 2; ++a) P[a] = T(0);
+  for (int c0 = 0; c0 < Mr; c0 += MC) {
+    T dv[MC];
 #pragma unroll
-  for (int c = 0; c < MMAX; ++c) {
-    if (c < op.m) {
-      const T d = __ldg(OpT<T>::D(op) + c * ld + i);
+    for (int t = 0; t < MC; ++t) {
+      const int c = M > 0 ? t : min(c0 + t, Mr - 1);
+      dv[t] = __ldg(OpT<T>::D(op) + c * ld + i);
+      if (M == 0 && c0 + t >= Mr) dv[t] = T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < MC; ++t) {
       T a[K];
-      load_row<K, T>(sh.A[c], a);
+      load_row<K, T>(sh.A[c0 + t], a);
 #pragma unroll
       for (int u = 0; u < K; ++u) {
-        const T du = d * a[u];
+        const T du = dv[t] * a[u];
 #pragma unroll
         for (int v = 0; v <= u; ++v) P[u * (u + 1) / 2 + v] += du * a[v];
       }
@@ -319,8 +346,10 @@ __device__ __forceinline__ bool finish_partials(const SysDesc& sd, int slot,
 // ---------------------------------------------------------------------------------------------
 // inner_apply: p = z + beta p, q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
-template <int K, typename T>
-__global__ void __launch_bounds__(256, 4)
+// FP32 instances are held to 64 registers (4 CTAs of 256 per SM); FP64 ones, whose
+// preconditioner factor alone needs ~60 registers, to 128.
+template <int K, int M, int E, typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, Control* ctl) {
   __shared__ CtaShared<T, 1> sh;
   const CtaRef cr = ctas[blockIdx.x];
@@ -356,7 +385,7 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
       T zi[K], w[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) zi[j] = z[j * ld + i];
-      apply_pixel<K, T, T, 1>(op, sh, z, i, zi, w);
+      apply_pixel<K, M, E, T, T, 1>(op, sh, z, i, zi, w);
       T pq = T(0);
       if (valid) {
         const T beta = sh.sc[r];
@@ -404,8 +433,8 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
 // ---------------------------------------------------------------------------------------------
 // inner_update: d += alpha p, r -= alpha q, z = P^{-1} r, partial r . z and r . r
 // ---------------------------------------------------------------------------------------------
-template <int K, typename T>
-__global__ void __launch_bounds__(256, 4)
+template <int K, int M, int E, typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
                Control* ctl) {
   __shared__ CtaShared<T, 2> sh;
@@ -434,7 +463,7 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
     BlockChol<K, T> f;
-    if (prec) block_chol<K, T, 2>(op, sh, i, f);
+    if (prec) block_chol<K, M, T, 2>(op, sh, i, f);
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
       const size_t off = (size_t)r * K * ld;
@@ -531,7 +560,7 @@ k_update_x(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas) {
 // ---------------------------------------------------------------------------------------------
 // residual: r64 = B - G X (FP64), r_in = r64 rounded, d = 0, z = P^{-1} r_in; decisions
 // ---------------------------------------------------------------------------------------------
-template <int K, typename T>
+template <int K, int M, int E, typename T>
 __global__ void __launch_bounds__(256)
 k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, Control* ctl) {
   __shared__ CtaShared<double, 4> sh;     // FP64 operator
@@ -562,7 +591,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
     BlockChol<K, T> f;
-    if (prec) block_chol<K, T, 1>(op, shT, i, f);
+    if (prec) block_chol<K, M, T, 1>(op, shT, i, f);
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
       const size_t off = (size_t)r * K * ld;
@@ -574,7 +603,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
       double xi[K], gx[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) xi[j] = X[j * ld + i];
-      apply_pixel<K, double, double, 4>(op, sh, X, i, xi, gx);
+      apply_pixel<K, M, E, double, double, 4>(op, sh, X, i, xi, gx);
       double rr64 = 0.0, bb = 0.0, rz = 0.0, rr = 0.0;
       if (valid) {
         T ri[K], zi[K];
@@ -656,6 +685,34 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
+// Shapes with compile-time (k, m, E) kernels; every other shape uses the (k, 0, 0) kernels.
+#define SYLV_SPECIAL_SHAPES(X) X(3, 5, 4) X(4, 6, 4) X(4, 7, 4) X(5, 7, 4) X(6, 8, 4) X(6, 9, 4)
+
+#define SYLV_IS_SPECIAL_(K_, M_, E_) || (k == K_ && m == M_ && e == E_)
+inline bool special_shape(int k, int m, int e) {
+  return false SYLV_SPECIAL_SHAPES(SYLV_IS_SPECIAL_);
+}
+
+// Calls CALL(K, M, E) for the kernel instance that serves shape (k, m, e).
+#define SYLV_TRY_SPECIAL_(K_, M_, E_) \
+  if (!done && k == K_ && m == M_ && e == E_) { CALL(K_, M_, E_); done = true; }
+#define SYLV_DISPATCH_SHAPE(k, m, e)                     \
+  bool done = false;                                     \
+  SYLV_SPECIAL_SHAPES(SYLV_TRY_SPECIAL_)                 \
+  if (!done) {                                           \
+    switch (k) {                                         \
+      case 1: CALL(1, 0, 0); break;                      \
+      case 2: CALL(2, 0, 0); break;                      \
+      case 3: CALL(3, 0, 0); break;                      \
+      case 4: CALL(4, 0, 0); break;                      \
+      case 5: CALL(5, 0, 0); break;                      \
+      case 6: CALL(6, 0, 0); break;                      \
+      case 7: CALL(7, 0, 0); break;                      \
+      case 8: CALL(8, 0, 0); break;                      \
+      default: return cudaErrorInvalidValue;             \
+    }                                                    \
+  }
+
 #define SYLV_DISPATCH_K(k, CALL)           \
   switch (k) {                             \
     case 1: CALL(1); break;                \
@@ -670,31 +727,33 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
   }
 
 template <typename T>
-cudaError_t launch_inner_apply_impl(int k, int ncta, int block, const SysDesc* d,
-                                    const CtaRef* c, Control* ctl, cudaStream_t s) {
+cudaError_t launch_inner_apply_impl(int k, int m, int e, int ncta, int block,
+                                    const SysDesc* d, const CtaRef* c, Control* ctl,
+                                    cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-#define CALL(K) k_inner_apply<K, T><<<ncta, block, 0, s>>>(d, c, ctl)
-  SYLV_DISPATCH_K(k, CALL)
+#define CALL(K, M, E) k_inner_apply<K, M, E, T><<<ncta, block, 0, s>>>(d, c, ctl)
+  SYLV_DISPATCH_SHAPE(k, m, e)
 #undef CALL
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_inner_update_impl(int k, int ncta, int block, const SysDesc* d,
-                                     const CtaRef* c, Control* ctl, cudaStream_t s) {
+cudaError_t launch_inner_update_impl(int k, int m, int e, int ncta, int block,
+                                     const SysDesc* d, const CtaRef* c, Control* ctl,
+                                     cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-#define CALL(K) k_inner_update<K, T><<<ncta, block, 0, s>>>(d, c, ctl)
-  SYLV_DISPATCH_K(k, CALL)
+#define CALL(K, M, E) k_inner_update<K, M, E, T><<<ncta, block, 0, s>>>(d, c, ctl)
+  SYLV_DISPATCH_SHAPE(k, m, e)
 #undef CALL
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_residual_impl(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
-                                 Control* ctl, cudaStream_t s) {
+cudaError_t launch_residual_impl(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                                 const CtaRef* c, Control* ctl, cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-#define CALL(K) k_residual<K, T><<<ncta, block, 0, s>>>(d, c, ctl)
-  SYLV_DISPATCH_K(k, CALL)
+#define CALL(K, M, E) k_residual<K, M, E, T><<<ncta, block, 0, s>>>(d, c, ctl)
+  SYLV_DISPATCH_SHAPE(k, m, e)
 #undef CALL
   return cudaGetLastError();
 }
@@ -709,32 +768,26 @@ cudaError_t launch_update_x_impl(int k, int ncta, int block, const SysDesc* d, c
   return cudaGetLastError();
 }
 
-// Resident CTAs per SM of the less occupant inner-iteration kernel for (k, block).
+// Resident CTAs per SM of the less occupant inner-iteration kernel for the shape.
 template <typename T>
-int occupancy_impl(int k, int block) {
+int occupancy_impl(int k, int m, int e, int block) {
   int best = 1 << 30;
   auto take = [&](const void* fn) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) == cudaSuccess)
       best = nb < best ? nb : best;
   };
-#define CALL(K)                                        \
-  do {                                                 \
-    take((const void*)k_inner_apply<K, T>);            \
-    take((const void*)k_inner_update<K, T>);           \
+  auto body = [&]() -> cudaError_t {
+#define CALL(K, M, E)                                      \
+  do {                                                     \
+    take((const void*)k_inner_apply<K, M, E, T>);          \
+    take((const void*)k_inner_update<K, M, E, T>);         \
   } while (0)
-  switch (k) {
-    case 1: CALL(1); break;
-    case 2: CALL(2); break;
-    case 3: CALL(3); break;
-    case 4: CALL(4); break;
-    case 5: CALL(5); break;
-    case 6: CALL(6); break;
-    case 7: CALL(7); break;
-    case 8: CALL(8); break;
-    default: return 1;
-  }
+    SYLV_DISPATCH_SHAPE(k, m, e)
 #undef CALL
+    return cudaSuccess;
+  };
+  body();
   return best == (1 << 30) || best < 1 ? 1 : best;
 }
 

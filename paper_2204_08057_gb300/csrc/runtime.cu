@@ -68,7 +68,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // plan: everything needed to run one list of systems
 // ------------------------------------------------------------------------------------------
 struct Group {
-  int k = 0;
+  int k = 0, m = 0, e = 0;  // shape shared by the group's systems
   int block = 256;
   int ncta = 0;             // CTAs of every iteration launch over this group
   CtaRef* d_ctas = nullptr;
@@ -169,21 +169,24 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
   P.inner_double = inner_double;
   const size_t tsz = inner_double ? sizeof(double) : sizeof(float);
   P.work.resize(nsys);
-  // groups by k; each system of a group gets CTA slots in proportion to its tiles, and the
+  // groups by shape (k, m, ELL width); each system of a group gets CTA slots in proportion to its tiles, and the
   // launch is sized to what the device keeps resident (nothing relies on residency: no CTA
   // ever waits for another)
   int dev = 0, nsm = 1;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  std::map<int, std::vector<int>> byk;
-  for (int s = 0; s < nsys; ++s) byk[hs[s]->op.k].push_back(s);
+  std::map<std::vector<int>, std::vector<int>> byshape;
+  for (int s = 0; s < nsys; ++s)
+    byshape[{hs[s]->op.k, hs[s]->op.m, hs[s]->op.E}].push_back(s);
   std::vector<int> nslots(nsys), ntiles(nsys);
-  for (auto& kv : byk) {
+  for (auto& kv : byshape) {
     Group g;
-    g.k = kv.first;
+    g.k = kv.first[0];
+    g.m = kv.first[1];
+    g.e = kv.first[2];
     g.block = default_block(0);
-    const int occ = inner_double ? occupancy<double>(g.k, g.block)
-                                 : occupancy<float>(g.k, g.block);
+    const int occ = inner_double ? occupancy<double>(g.k, g.m, g.e, g.block)
+                                 : occupancy<float>(g.k, g.m, g.e, g.block);
     const int64_t budget = (int64_t)nsm * std::max(occ, 1);
     int64_t total = 0;
     for (int s : kv.second) {
@@ -258,12 +261,12 @@ template <typename T>
 int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
                            bool capture_events) {
   for (auto& g : P.groups)
-    CK(launch_inner_apply<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_mid)
     CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_mid, s));
   for (auto& g : P.groups)
-    CK(launch_inner_update<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_update<T>(g.k, g.m, g.e, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_end)
     CK(capture_events ? cudaEventRecordWithFlags(e_end, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_end, s));
@@ -368,7 +371,7 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
       CK(launch_update_x<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, s));
     if (prof) CK(cudaEventRecord(P.evr0, s));
     for (auto& g : P.groups)
-      CK(launch_residual<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+      CK(launch_residual<T>(g.k, g.m, g.e, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
     if (prof) CK(cudaEventRecord(P.evr1, s));
     launches += 2 * ng;
     if ((rc = poll(P, s)) != SYLV_OK) break;

@@ -110,7 +110,7 @@ __global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restric
 
 // Stand-alone operator apply Y = G X (eq. block-vector-mapping-matvec with Algorithm 1);
 // grid-stride over pixels.
-template <int K, typename T>
+template <int K, int M, int E, typename T>
 __global__ void __launch_bounds__(256, 4) k_apply(OpData op, const T* __restrict__ X,
                                                T* __restrict__ Y, int R) {
   __shared__ CtaShared<T, 1> sh;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256, 4) k_apply(OpData op, const T* __restrict
       T xi[K], acc[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) xi[j] = x[j * ld + i];
-      apply_pixel<K, T, T, 1>(op, sh, x, i, xi, acc);
+      apply_pixel<K, M, E, T, T, 1>(op, sh, x, i, xi, acc);
 #pragma unroll
       for (int j = 0; j < K; ++j) y[j * ld + i] = acc[j];
     }
@@ -279,8 +279,9 @@ cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t
     if (nsm <= 0) nsm = 1;
   }
   const int nb = (int)std::min<int64_t>(blocks_for(op.n, 256), (int64_t)nsm * 8);
-#define CALL(K) k_apply<K, T><<<nb, 256, 0, s>>>(op, X, Y, R)
-  SYLV_DISPATCH_K(op.k, CALL)
+  const int k = op.k, m = op.m, e = op.E;
+#define CALL(K, M, E) k_apply<K, M, E, T><<<nb, 256, 0, s>>>(op, X, Y, R)
+  SYLV_DISPATCH_SHAPE(k, m, e)
 #undef CALL
   return cudaGetLastError();
 }

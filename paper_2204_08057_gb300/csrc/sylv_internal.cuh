@@ -115,20 +115,21 @@ struct CtaRef {
 // ------------------------------------------------------------------------------------------
 // launchers (defined in the kernel translation units)
 // ------------------------------------------------------------------------------------------
+// Iteration kernels for a group of systems of one shape (k sources, m channels, ELL width e).
 template <typename T>
-cudaError_t launch_inner_apply(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
-                               Control* c, cudaStream_t s);
+cudaError_t launch_inner_apply(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                               const CtaRef* c, Control* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_inner_update(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
-                                Control* c, cudaStream_t s);
+cudaError_t launch_inner_update(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                                const CtaRef* c, Control* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_residual(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
-                            Control* c, cudaStream_t s);
+cudaError_t launch_residual(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                            const CtaRef* c, Control* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_update_x(int k, int ntiles, int block, const SysDesc* d, const CtaRef* t,
+cudaError_t launch_update_x(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
                             cudaStream_t s);
 template <typename T>
-int occupancy(int k, int block);
+int occupancy(int k, int m, int e, int block);
 cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,
                                const SysDesc* d, Control* c, cudaStream_t s);
 
