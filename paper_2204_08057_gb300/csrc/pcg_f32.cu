@@ -1,31 +1,109 @@
-// Explicit instantiation of the iteration kernels with inner type float.
-#include "pcg_kernels.cuh"
+// Iteration kernels with inner type float: the generic kernels and the bulk-copy staged ones.
+#include "pcg_tma.cuh"
 
 namespace sylv {
 
+bool tma_available(int k, int m, int e) { return special_shape(k, m, e); }
+
+namespace {
+
+template <int K, int M, int E>
+size_t apply_tma_smem() {
+  return (size_t)tma::NSTAGE * tma::ApplyLayout<K, M, E>::STAGE_BYTES;
+}
+template <int K, int M>
+size_t update_tma_smem() {
+  return (size_t)tma::NSTAGE * tma::UpdateLayout<K, M>::STAGE_BYTES;
+}
+
+template <int K, int M, int E>
+cudaError_t apply_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl, cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = apply_tma_smem<K, M, E>();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tma::k_inner_apply_tma<K, M, E>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  tma::k_inner_apply_tma<K, M, E><<<ncta, TILE_PX, smem, s>>>(d, c, ctl);
+  return cudaGetLastError();
+}
+
+template <int K, int M>
+cudaError_t update_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
+                       cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = update_tma_smem<K, M>();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tma::k_inner_update_tma<K, M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  tma::k_inner_update_tma<K, M><<<ncta, TILE_PX, smem, s>>>(d, c, ctl);
+  return cudaGetLastError();
+}
+
+template <int K, int M, int E>
+int tma_occupancy() {
+  int a = 0, b = 0;
+  cudaFuncSetAttribute(tma::k_inner_apply_tma<K, M, E>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_tma_smem<K, M, E>());
+  cudaFuncSetAttribute(tma::k_inner_update_tma<K, M>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_tma_smem<K, M>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, tma::k_inner_apply_tma<K, M, E>, TILE_PX,
+                                                apply_tma_smem<K, M, E>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tma::k_inner_update_tma<K, M>, TILE_PX,
+                                                update_tma_smem<K, M>());
+  const int o = a < b ? a : b;
+  return o < 1 ? 1 : o;
+}
+
+}  // namespace
+
+#define SYLV_TMA_APPLY_(K_, M_, E_) \
+  if (k == K_ && m == M_ && e == E_) return apply_tma<K_, M_, E_>(ncta, d, c, ctl, s);
+#define SYLV_TMA_UPDATE_(K_, M_, E_) \
+  if (k == K_ && m == M_ && e == E_) return update_tma<K_, M_>(ncta, d, c, ctl, s);
+#define SYLV_TMA_OCC_(K_, M_, E_) \
+  if (k == K_ && m == M_ && e == E_) return tma_occupancy<K_, M_, E_>();
+
 template <>
-cudaError_t launch_inner_apply<float>(int k, int m, int e, int ncta, int block, const SysDesc* d,
-                                     const CtaRef* c, Control* ctl, cudaStream_t s) {
+cudaError_t launch_inner_apply<float>(int k, int m, int e, int variant, int ncta, int block,
+                                      const SysDesc* d, const CtaRef* c, Control* ctl,
+                                      cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+  if (variant == 1) {
+    SYLV_SPECIAL_SHAPES(SYLV_TMA_APPLY_)
+  }
   return launch_inner_apply_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_inner_update<float>(int k, int m, int e, int ncta, int block,
-                                      const SysDesc* d, const CtaRef* c, Control* ctl,
-                                      cudaStream_t s) {
+cudaError_t launch_inner_update<float>(int k, int m, int e, int variant, int ncta, int block,
+                                       const SysDesc* d, const CtaRef* c, Control* ctl,
+                                       cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+  if (variant == 1) {
+    SYLV_SPECIAL_SHAPES(SYLV_TMA_UPDATE_)
+  }
   return launch_inner_update_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
 cudaError_t launch_residual<float>(int k, int m, int e, int ncta, int block, const SysDesc* d,
-                                  const CtaRef* c, Control* ctl, cudaStream_t s) {
+                                   const CtaRef* c, Control* ctl, cudaStream_t s) {
   return launch_residual_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
 cudaError_t launch_update_x<float>(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
-                                  cudaStream_t s) {
+                                   cudaStream_t s) {
   return launch_update_x_impl<float>(k, ncta, block, d, c, s);
 }
 template <>
-int occupancy<float>(int k, int m, int e, int block) {
+int occupancy<float>(int k, int m, int e, int variant, int block) {
+  if (variant == 1) {
+    SYLV_SPECIAL_SHAPES(SYLV_TMA_OCC_)
+  }
   return occupancy_impl<float>(k, m, e, block);
 }
 

@@ -4,14 +4,17 @@
 namespace sylv {
 
 template <>
-cudaError_t launch_inner_apply<double>(int k, int m, int e, int ncta, int block, const SysDesc* d,
-                                     const CtaRef* c, Control* ctl, cudaStream_t s) {
+cudaError_t launch_inner_apply<double>(int k, int m, int e, int variant, int ncta, int block,
+                                       const SysDesc* d, const CtaRef* c, Control* ctl,
+                                       cudaStream_t s) {
+  (void)variant;
   return launch_inner_apply_impl<double>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
-cudaError_t launch_inner_update<double>(int k, int m, int e, int ncta, int block,
-                                      const SysDesc* d, const CtaRef* c, Control* ctl,
-                                      cudaStream_t s) {
+cudaError_t launch_inner_update<double>(int k, int m, int e, int variant, int ncta, int block,
+                                        const SysDesc* d, const CtaRef* c, Control* ctl,
+                                        cudaStream_t s) {
+  (void)variant;
   return launch_inner_update_impl<double>(k, m, e, ncta, block, d, c, ctl, s);
 }
 template <>
@@ -25,7 +28,8 @@ cudaError_t launch_update_x<double>(int k, int ncta, int block, const SysDesc* d
   return launch_update_x_impl<double>(k, ncta, block, d, c, s);
 }
 template <>
-int occupancy<double>(int k, int m, int e, int block) {
+int occupancy<double>(int k, int m, int e, int variant, int block) {
+  (void)variant;
   return occupancy_impl<double>(k, m, e, block);
 }
 

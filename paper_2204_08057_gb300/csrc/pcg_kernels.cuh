@@ -139,13 +139,13 @@ __device__ __forceinline__ void load_row(const T* row, T (&a)[K]) {
   }
 }
 
-// acc = (G x)_i for one column: x points at the column's k x ld block, xi holds x at pixel i.
+// acc = (G x)_i for one column: x points at the column's k x ldx block, xi holds x at pixel i.
 // M and E are the number of channels and the ELL width when known at compile time (0: read
 // from op, loaded in batches of 4 at clamped, always valid addresses so that a batch of loads
 // is issued together).
 template <int K, int M, int E, typename T, typename TX, int NV>
 __device__ __forceinline__ void apply_pixel(const OpData& op, const CtaShared<T, NV>& sh,
-                                            const TX* __restrict__ x, int64_t i,
+                                            const TX* __restrict__ x, int64_t ldx, int64_t i,
                                             const T (&xi)[K], T (&acc)[K]) {
   const int64_t ld = op.ld;
   constexpr int EC = E > 0 ? E : 4;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void apply_pixel(const OpData& op, const CtaShared<T,
 #pragma unroll
     for (int t = 0; t < EC; ++t)
 #pragma unroll
-      for (int j = 0; j < K; ++j) lap[j] += val[t] * T(x[j * ld + col[t]]);
+      for (int j = 0; j < K; ++j) lap[j] += val[t] * T(x[j * ldx + col[t]]);
   }
 #pragma unroll
   for (int j = 0; j < K; ++j) acc[j] = sh.tk2[j] * wi * xi[j] + sh.tau[j] * lap[j];
@@ -207,6 +207,38 @@ struct BlockChol {
   T l[K * (K + 1) / 2];  // packed lower factor, row-major; diagonal entries stored inverted
 };
 
+// Factors a packed SPD block P (row-major lower triangle) into f; P is overwritten.  The
+// reciprocal square roots use the device rsqrt (a preconditioner needs no correctly rounded
+// division or square root; both sides of PCG use the same factor).
+template <int K, typename T>
+__device__ __forceinline__ void block_chol_factor(T (&P)[K * (K + 1) / 2], BlockChol<K, T>& f) {
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const T pu = P[u * (u + 1) / 2 + u];
+    f.s[u] = pu > T(0) ? rsqrt(pu) : T(1);
+  }
+#pragma unroll
+  for (int u = 0; u < K; ++u)
+#pragma unroll
+    for (int v = 0; v <= u; ++v) P[u * (u + 1) / 2 + v] *= f.s[u] * f.s[v];
+  const T floor_piv = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+#pragma unroll
+    for (int v = 0; v <= u; ++v) {
+      T x = P[u * (u + 1) / 2 + v];
+#pragma unroll
+      for (int c = 0; c < v; ++c) x -= f.l[u * (u + 1) / 2 + c] * f.l[v * (v + 1) / 2 + c];
+      if (u == v) {
+        x = x > floor_piv ? x : floor_piv;
+        f.l[u * (u + 1) / 2 + u] = rsqrt(x);
+      } else {
+        f.l[u * (u + 1) / 2 + v] = x * f.l[v * (v + 1) / 2 + v];
+      }
+    }
+  }
+}
+
 template <int K, int M, typename T, int NV>
 __device__ __forceinline__ void block_chol(const OpData& op, const CtaShared<T, NV>& sh,
                                            int64_t i, BlockChol<K, T>& f) {
@@ -240,31 +272,7 @@ __device__ __forceinline__ void block_chol(const OpData& op, const CtaShared<T, 
   const T wi = op.has_w ? __ldg(OpT<T>::w(op) + i) : T(1);
 #pragma unroll
   for (int u = 0; u < K; ++u) P[u * (u + 1) / 2 + u] += sh.tk2[u] * wi + sh.tau[u] * dg;
-#pragma unroll
-  for (int u = 0; u < K; ++u) {
-    const T pu = P[u * (u + 1) / 2 + u];
-    f.s[u] = pu > T(0) ? T(1) / sqrt(pu) : T(1);
-  }
-#pragma unroll
-  for (int u = 0; u < K; ++u)
-#pragma unroll
-    for (int v = 0; v <= u; ++v) P[u * (u + 1) / 2 + v] *= f.s[u] * f.s[v];
-  const T floor_piv = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
-#pragma unroll
-  for (int u = 0; u < K; ++u) {
-#pragma unroll
-    for (int v = 0; v <= u; ++v) {
-      T x = P[u * (u + 1) / 2 + v];
-#pragma unroll
-      for (int c = 0; c < v; ++c) x -= f.l[u * (u + 1) / 2 + c] * f.l[v * (v + 1) / 2 + c];
-      if (u == v) {
-        x = x > floor_piv ? x : floor_piv;
-        f.l[u * (u + 1) / 2 + u] = T(1) / sqrt(x);
-      } else {
-        f.l[u * (u + 1) / 2 + v] = x * f.l[v * (v + 1) / 2 + v];
-      }
-    }
-  }
+  block_chol_factor<K, T>(P, f);
 }
 
 template <int K, typename T>
@@ -385,7 +393,7 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
       T zi[K], w[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) zi[j] = z[j * ld + i];
-      apply_pixel<K, M, E, T, T, 1>(op, sh, z, i, zi, w);
+      apply_pixel<K, M, E, T, T, 1>(op, sh, z, ld, i, zi, w);
       T pq = T(0);
       if (valid) {
         const T beta = sh.sc[r];
@@ -542,17 +550,16 @@ __global__ void __launch_bounds__(256)
 k_update_x(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas) {
   const CtaRef cr = ctas[blockIdx.x];
   const SysDesc& sd = descs[cr.sys];
-  const int64_t ld = sd.op.ld, n = sd.op.n;
+  const int64_t ld = sd.op.ld, ldu = sd.op.ldu, n = sd.op.n;
   for (int r = 0; r < sd.R; ++r) {
     if (sd.st[r].phase != PH_INNER_DONE) continue;
-    const size_t off = (size_t)r * K * ld;
-    const T* d = (const T*)sd.vd + off;
-    double* X = sd.X + off;
+    const T* d = (const T*)sd.vd + (size_t)r * K * ld;
+    double* X = sd.X + (size_t)r * K * ldu;
     for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
       const int64_t i = (int64_t)tile * blockDim.x + threadIdx.x;
       if (i >= n) continue;
 #pragma unroll
-      for (int j = 0; j < K; ++j) X[j * ld + i] += double(d[j * ld + i]);
+      for (int j = 0; j < K; ++j) X[j * ldu + i] += double(d[j * ld + i]);
     }
   }
 }
@@ -595,21 +602,23 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
       const size_t off = (size_t)r * K * ld;
-      const double* X = sd.X + off;
-      const double* B = sd.B + off;
+      const size_t offu = (size_t)r * K * op.ldu;
+      const int64_t ldu = op.ldu;
+      const double* X = sd.X + offu;
+      const double* B = sd.B + offu;
       T* d = (T*)sd.vd + off;
       T* rv = (T*)sd.vr + off;
       T* z = (T*)sd.vz + off;
       double xi[K], gx[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) xi[j] = X[j * ld + i];
-      apply_pixel<K, M, E, double, double, 4>(op, sh, X, i, xi, gx);
+      for (int j = 0; j < K; ++j) xi[j] = X[j * ldu + i];
+      apply_pixel<K, M, E, double, double, 4>(op, sh, X, ldu, i, xi, gx);
       double rr64 = 0.0, bb = 0.0, rz = 0.0, rr = 0.0;
       if (valid) {
         T ri[K], zi[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          const double bj = B[j * ld + i];
+          const double bj = B[j * ldu + i];
           const double r64 = bj - gx[j];
           rr64 += r64 * r64;
           bb += bj * bj;

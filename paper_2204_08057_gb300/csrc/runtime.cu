@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -69,6 +70,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // ------------------------------------------------------------------------------------------
 struct Group {
   int k = 0, m = 0, e = 0;  // shape shared by the group's systems
+  int variant = 0;          // 1: bulk-copy staged FP32 inner kernels
   int block = 256;
   int ncta = 0;             // CTAs of every iteration launch over this group
   CtaRef* d_ctas = nullptr;
@@ -92,7 +94,7 @@ struct Plan {
   SysDesc* h_desc = nullptr;    // pinned
   Control* d_ctl = nullptr;
   Control* h_ctl = nullptr;     // pinned
-  unsigned int* h_poll = nullptr;  // pinned, 2 words
+  unsigned int* h_poll = nullptr;  // pinned: n_active, n_unfinished, error
   ColState* h_states = nullptr;    // pinned, ncols
   int* d_col_sys = nullptr;
   int* d_col_rhs = nullptr;
@@ -154,13 +156,20 @@ Plan::~Plan() {
 
 namespace {
 
+// Staged (bulk-copy) FP32 inner kernels where a shape has them; SYLV_NO_TMA=1 in the
+// environment selects the plain kernels (for comparisons).
+const bool g_use_tma = [] {
+  const char* v = std::getenv("SYLV_NO_TMA");
+  return !(v && v[0] == '1');
+}();
+
 // Batched plans, keyed by the list of (handle, nrhs) and the inner type.
 std::mutex g_plan_mu;
 std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> g_plans;
 
 int default_block(int64_t n) {
   (void)n;
-  return 256;
+  return TILE_PX;
 }
 
 int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner_double) {
@@ -185,8 +194,11 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     g.m = kv.first[1];
     g.e = kv.first[2];
     g.block = default_block(0);
-    const int occ = inner_double ? occupancy<double>(g.k, g.m, g.e, g.block)
-                                 : occupancy<float>(g.k, g.m, g.e, g.block);
+    bool any_w = false;
+    for (int s : kv.second) any_w = any_w || hs[s]->op.has_w;
+    g.variant = (!inner_double && !any_w && g_use_tma && tma_available(g.k, g.m, g.e)) ? 1 : 0;
+    const int occ = inner_double ? occupancy<double>(g.k, g.m, g.e, g.variant, g.block)
+                                 : occupancy<float>(g.k, g.m, g.e, g.variant, g.block);
     const int64_t budget = (int64_t)nsm * std::max(occ, 1);
     int64_t total = 0;
     for (int s : kv.second) {
@@ -224,7 +236,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
   CK(cudaMallocHost((void**)&P.h_desc, nsys * sizeof(SysDesc)));
   CK(dalloc(&P.d_ctl, sizeof(Control)));
   CK(cudaMallocHost((void**)&P.h_ctl, sizeof(Control)));
-  CK(cudaMallocHost((void**)&P.h_poll, 2 * sizeof(unsigned int)));
+  CK(cudaMallocHost((void**)&P.h_poll, 4 * sizeof(unsigned int)));
   CK(cudaMallocHost((void**)&P.h_states, P.ncols * sizeof(ColState)));
   CK(dalloc(&P.d_col_sys, P.ncols * sizeof(int)));
   CK(dalloc(&P.d_col_rhs, P.ncols * sizeof(int)));
@@ -261,12 +273,12 @@ template <typename T>
 int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
                            bool capture_events) {
   for (auto& g : P.groups)
-    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.variant, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_mid)
     CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_mid, s));
   for (auto& g : P.groups)
-    CK(launch_inner_update<T>(g.k, g.m, g.e, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_update<T>(g.k, g.m, g.e, g.variant, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_end)
     CK(capture_events ? cudaEventRecordWithFlags(e_end, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_end, s));
@@ -313,9 +325,10 @@ int ensure_graph(Plan& P, int iters, int profile) {
 }
 
 int poll(Plan& P, cudaStream_t s) {
-  CK(cudaMemcpyAsync(P.h_poll, &P.d_ctl->n_active, 2 * sizeof(unsigned int),
+  CK(cudaMemcpyAsync(P.h_poll, &P.d_ctl->n_active, 3 * sizeof(unsigned int),
                      cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (P.h_poll[2]) return fail(SYLV_E_TIMEOUT, "a bounded device-side wait expired");
   return SYLV_OK;
 }
 
@@ -349,7 +362,7 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   if (!o.use_x0) {
     for (int t = 0; t < nsys; ++t) {
       const OpData& op = P.hs[t]->op;
-      CK(cudaMemsetAsync(X[t], 0, (size_t)P.R[t] * op.k * op.ld * sizeof(double), s));
+      CK(cudaMemsetAsync(X[t], 0, (size_t)P.R[t] * op.k * op.ldu * sizeof(double), s));
     }
   }
   CK(launch_init_states(P.ncols, P.d_col_sys, P.d_col_rhs, P.d_desc, P.d_ctl, s));
@@ -565,7 +578,8 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   cudaGetDevice(&h->device);
   OpData& op = h->op;
   op.n = p->n;
-  op.ld = p->ld;
+  op.ld = ceil_div(p->n, TILE_PX) * TILE_PX;
+  op.ldu = p->ld;
   op.k = p->k;
   op.m = p->m;
   op.has_w = p->w != nullptr;
@@ -626,7 +640,7 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   }
   const int E = (int)hflags[1];
   op.E = E;
-  const size_t ld = (size_t)p->ld;
+  const size_t ld = (size_t)op.ld;
   if ((e = dalloc(&h->ell_col, std::max<size_t>(E, 1) * ld * sizeof(int32_t))) != cudaSuccess ||
       (e = dalloc(&h->ell_val32, std::max<size_t>(E, 1) * ld * sizeof(float))) != cudaSuccess ||
       (e = dalloc(&h->ell_val64, std::max<size_t>(E, 1) * ld * sizeof(double))) != cudaSuccess ||
@@ -664,13 +678,13 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   if ((e = cudaMemsetAsync(dflags, 0, sizeof(unsigned int), s)) != cudaSuccess ||
       (e = launch_ell_build(op, p->L_rowptr, p->L_col, p->L_val, h->ell_col, h->ell_val32,
                             h->ell_val64, h->diag32, h->diag64, E, s)) != cudaSuccess ||
-      (e = launch_convert_check(p->D, p->m, p->n, p->ld, h->D32, h->D64, 0, dflags, s)) !=
+      (e = launch_convert_check(p->D, p->m, p->n, p->ld, op.ld, h->D32, h->D64, 0, dflags, s)) !=
           cudaSuccess)
     return bail(cuda_fail(e, "operator set-up"));
   if (p->w) {
     if ((e = cudaMemsetAsync(h->w32, 0, ld * sizeof(float), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->w64, 0, ld * sizeof(double), s)) != cudaSuccess ||
-        (e = launch_convert_check(p->w, 1, p->n, p->ld, h->w32, h->w64, 1, dflags, s)) !=
+        (e = launch_convert_check(p->w, 1, p->n, p->ld, op.ld, h->w32, h->w64, 1, dflags, s)) !=
             cudaSuccess)
       return bail(cuda_fail(e, "mass diagonal set-up"));
   }
@@ -798,7 +812,7 @@ int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const d
   DeviceGuard g(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   const OpData& op = h->op;
-  const size_t vbytes = (size_t)nrhs * op.k * op.ld * sizeof(double);
+  const size_t vbytes = (size_t)nrhs * op.k * op.ldu * sizeof(double);
   double* lam = lambda;
   if (!lam) {
     if (h->lam_bytes < vbytes) {

@@ -76,35 +76,35 @@ __global__ void k_ell_build(int64_t n, int64_t ld, const int32_t* __restrict__ r
 // Copies rows x n values (pitch ld) into FP32 and FP64 buffers and checks them (>= 0, or > 0
 // if positive, and finite).
 __global__ void k_convert_check(const double* __restrict__ src, int64_t rows, int64_t n,
-                                int64_t ld, float* dst32, double* dst64, int positive,
-                                unsigned int* flags) {
+                                int64_t ld_src, int64_t ld_dst, float* dst32, double* dst64,
+                                int positive, unsigned int* flags) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * n) return;
   const int64_t r = t / n, i = t - r * n;
-  const double v = src[r * ld + i];
+  const double v = src[r * ld_src + i];
   if (!isfinite(v) || v < 0.0 || (positive && !(v > 0.0))) atomicOr(flags, FLAG_VALUE);
-  dst32[r * ld + i] = (float)v;
-  dst64[r * ld + i] = v;
+  dst32[r * ld_dst + i] = (float)v;
+  dst64[r * ld_dst + i] = v;
 }
 
 // b = B^T C y (eq. mu*): B[r][j][i] = sum_c a_cj d_ci y[r][c][i]
 __global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restrict__ B, int R) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= op.n) return;
-  const int64_t ld = op.ld;
+  const int64_t ld = op.ld, ldu = op.ldu;
   for (int r = 0; r < R; ++r) {
     double acc[KMAX];
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) acc[j] = 0.0;
     for (int c = 0; c < op.m; ++c) {
-      const double dy = op.D64[c * ld + i] * Y[((int64_t)r * op.m + c) * ld + i];
+      const double dy = op.D64[c * ld + i] * Y[((int64_t)r * op.m + c) * ldu + i];
 #pragma unroll
       for (int j = 0; j < KMAX; ++j)
         if (j < op.k) acc[j] += op.A64[c * op.k + j] * dy;
     }
 #pragma unroll
     for (int j = 0; j < KMAX; ++j)
-      if (j < op.k) B[((int64_t)r * op.k + j) * ld + i] = acc[j];
+      if (j < op.k) B[((int64_t)r * op.k + j) * ldu + i] = acc[j];
   }
 }
 
@@ -116,18 +116,18 @@ __global__ void __launch_bounds__(256, 4) k_apply(OpData op, const T* __restrict
   __shared__ CtaShared<T, 1> sh;
   stage_operator<T, 1>(op, K, sh);
   __syncthreads();
-  const int64_t ld = op.ld;
+  const int64_t ldu = op.ldu;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < op.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     for (int r = 0; r < R; ++r) {
-      const T* x = X + (size_t)r * K * ld;
-      T* y = Y + (size_t)r * K * ld;
+      const T* x = X + (size_t)r * K * ldu;
+      T* y = Y + (size_t)r * K * ldu;
       T xi[K], acc[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) xi[j] = x[j * ld + i];
-      apply_pixel<K, M, E, T, T, 1>(op, sh, x, i, xi, acc);
+      for (int j = 0; j < K; ++j) xi[j] = x[j * ldu + i];
+      apply_pixel<K, M, E, T, T, 1>(op, sh, x, ldu, i, xi, acc);
 #pragma unroll
-      for (int j = 0; j < K; ++j) y[j * ld + i] = acc[j];
+      for (int j = 0; j < K; ++j) y[j * ldu + i] = acc[j];
     }
   }
 }
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restric
                                               const double* __restrict__ Y, int R,
                                               int want_beta, double* partial) {
   __shared__ double red[32 * 3 * K];
-  const int64_t ld = op.ld;
+  const int64_t ld = op.ld, ldu = op.ldu;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < op.n;
   double g[3 * K];
@@ -149,20 +149,20 @@ __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restric
     const double dg = op.diag64[i];
     const double wi = op.has_w ? op.w64[i] : 1.0;
     for (int r = 0; r < R; ++r) {
-      const double* x = X + (size_t)r * K * ld;
-      const double* l = lam + (size_t)r * K * ld;
+      const double* x = X + (size_t)r * K * ldu;
+      const double* l = lam + (size_t)r * K * ldu;
       double xi[K], li[K], Lx[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        xi[j] = x[j * ld + i];
-        li[j] = l[j * ld + i];
+        xi[j] = x[j * ldu + i];
+        li[j] = l[j * ldu + i];
         Lx[j] = dg * xi[j];
       }
       for (int e = 0; e < op.E; ++e) {
         const int64_t c = op.ell_col[e * ld + i];
         const double v = op.ell_val64[e * ld + i];
 #pragma unroll
-        for (int j = 0; j < K; ++j) Lx[j] += v * x[j * ld + c];
+        for (int j = 0; j < K; ++j) Lx[j] += v * x[j * ldu + c];
       }
 #pragma unroll
       for (int j = 0; j < K; ++j) {
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restric
         g[K + j] -= 2.0 * op.tau64[j] * op.kappa64[j] * li[j] * wi * xi[j];
       }
       if (want_beta) {
-        const double* y = Y + (size_t)r * op.m * ld;
+        const double* y = Y + (size_t)r * op.m * ldu;
         for (int c = 0; c < op.m; ++c) {
           double t = 0.0, u = 0.0;
 #pragma unroll
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_grad(OpData op, const double* __restric
             u += op.A64[c * K + j] * li[j];
           }
           const double dc = op.D64[c * ld + i];
-          const double yc = y[c * ld + i];
+          const double yc = y[c * ldu + i];
 #pragma unroll
           for (int j = 0; j < K; ++j)
             g[2 * K + j] += op.logf64[c] * op.A64[c * K + j] * dc *
@@ -215,6 +215,7 @@ __global__ void k_init_states(int ncols, const int* __restrict__ col_sys,
   if (t == 0) {
     ctl->n_active = 0u;
     ctl->n_unfinished = (unsigned)ncols;
+    ctl->error = 0u;
   }
   if (t >= ncols) return;
   ColState& cs = d[col_sys[t]].st[col_rhs[t]];
@@ -254,13 +255,13 @@ cudaError_t launch_ell_build(const OpData& op, const int32_t* rowptr, const int3
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int64_t ld,
-                                 float* dst32, double* dst64, int positive,
+cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int64_t ld_src,
+                                 int64_t ld_dst, float* dst32, double* dst64, int positive,
                                  unsigned int* flags, cudaStream_t s) {
   const int64_t tot = rows * n;
   if (tot == 0) return cudaSuccess;
-  k_convert_check<<<blocks_for(tot, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(src, rows, n, ld, dst32,
-                                                                       dst64, positive, flags);
+  k_convert_check<<<blocks_for(tot, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(
+      src, rows, n, ld_src, ld_dst, dst32, dst64, positive, flags);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ constexpr int EMAX = SYLV_MAX_DEGREE;
 constexpr int RMAX = SYLV_MAX_RHS;
 constexpr int NPART = 4;          // partial sums per (tile, column)
 constexpr int MAX_BLOCK = 256;
+constexpr int TILE_PX = 256;      // pixels per tile = threads per CTA of the iteration kernels
 
 enum Phase : int {
   PH_START = 0,       // before the first FP64 residual
@@ -56,7 +57,9 @@ struct ColState {
 // Operator data of one handle, in the device layouts the kernels read.
 struct OpData {
   int64_t n;
-  int64_t ld;
+  int64_t ld;                // leading dimension of every library-owned buffer: n rounded up
+                             // to whole tiles (TILE_PX), so tile rows are 16-byte aligned
+  int64_t ldu;               // leading dimension of the caller's vectors (X, B, Y, Yobs)
   int k, m, E, has_w;
   const int32_t* ell_col;    // E x ld: off-diagonal columns of L (padding: own row, value 0)
   const float* ell_val32;    // E x ld
@@ -98,6 +101,8 @@ struct SysDesc {
 struct Control {
   unsigned int n_active;      // columns in PH_INNER
   unsigned int n_unfinished;  // columns not final
+  unsigned int error;         // nonzero: a bounded device wait expired (SYLV_E_TIMEOUT)
+  unsigned int pad0;
   double tol2;                // tol^2
   double tol_in2;             // inner_tol^2 (0 in FP64 mode)
   double safety2;             // squared safety factor on the inner target
@@ -116,12 +121,16 @@ struct CtaRef {
 // launchers (defined in the kernel translation units)
 // ------------------------------------------------------------------------------------------
 // Iteration kernels for a group of systems of one shape (k sources, m channels, ELL width e).
+// variant 1 selects the bulk-copy staged FP32 kernels (shapes with compile-time instances,
+// no mass diagonal); tma_available() says whether a shape has them.
 template <typename T>
-cudaError_t launch_inner_apply(int k, int m, int e, int ncta, int block, const SysDesc* d,
-                               const CtaRef* c, Control* ctl, cudaStream_t s);
+cudaError_t launch_inner_apply(int k, int m, int e, int variant, int ncta, int block,
+                               const SysDesc* d, const CtaRef* c, Control* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_inner_update(int k, int m, int e, int ncta, int block, const SysDesc* d,
-                                const CtaRef* c, Control* ctl, cudaStream_t s);
+cudaError_t launch_inner_update(int k, int m, int e, int variant, int ncta, int block,
+                                const SysDesc* d, const CtaRef* c, Control* ctl,
+                                cudaStream_t s);
+bool tma_available(int k, int m, int e);
 template <typename T>
 cudaError_t launch_residual(int k, int m, int e, int ncta, int block, const SysDesc* d,
                             const CtaRef* c, Control* ctl, cudaStream_t s);
@@ -129,7 +138,7 @@ template <typename T>
 cudaError_t launch_update_x(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
                             cudaStream_t s);
 template <typename T>
-int occupancy(int k, int m, int e, int block);
+int occupancy(int k, int m, int e, int variant, int block);
 cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,
                                const SysDesc* d, Control* c, cudaStream_t s);
 
@@ -140,8 +149,8 @@ cudaError_t launch_ell_build(const OpData& op, const int32_t* rowptr, const int3
                              const double* val, int32_t* ell_col, float* ell_val32,
                              double* ell_val64, float* diag32, double* diag64, int E,
                              cudaStream_t s);
-cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int64_t ld,
-                                 float* dst32, double* dst64, int positive,
+cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int64_t ld_src,
+                                 int64_t ld_dst, float* dst32, double* dst64, int positive,
                                  unsigned int* flags, cudaStream_t s);
 cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s);
 template <typename T>
