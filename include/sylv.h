@@ -176,6 +176,23 @@ int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const d
                   int nrhs, double* lambda, double* g_tau, double* g_kappa, double* g_beta,
                   const sylv_opts* o, sylv_info* info, sylv_stream s);
 
+/* Allocation-free variant of sylv_solve (the paper has no counterpart; this is a service for
+ * callers that cannot allocate).  Some callers cannot call cudaMalloc, or any routine that
+ * allocates, at the point where they solve: a real-time pipeline whose memory is reserved
+ * at start-up, a process held to a fixed device-memory budget, or a loop that must not incur
+ * an allocator's implicit synchronisation.  This entry point runs the same preconditioned CG
+ * inside FP64 refinement as sylv_solve (same arguments and results, without the staged
+ * kernels, CUDA graphs or per-kernel timing; info->ms_total is host wall time) and keeps its
+ * whole workspace in one file-scope device array of 16 MiB that every GPU loading the library
+ * holds until the process exits.  It allocates nothing: no device or pinned memory, events,
+ * graphs or host heap.  The array's device address is looked up on the first call on each
+ * device, so that first call should come before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams or threads) race; serialise them.
+ * Problems whose workspace (about 20 * nrhs * k * n bytes in mixed precision, 40 in FP64)
+ * exceeds the array return SYLV_E_UNSUPPORTED.  Synchronises s. */
+int sylv_solve_noalloc(sylv_handle h, const double* B, double* X, int nrhs,
+                       const sylv_opts* o, sylv_info* info, sylv_stream s);
+
 /* Releases the handle and everything it owns.  NULL is ignored. */
 void sylv_destroy(sylv_handle h);
 

@@ -496,6 +496,17 @@ int check_opts(const sylv_opts& o) {
 
 }  // namespace
 
+namespace sylv {
+// Read-only view of a handle for other translation units of the library.
+int handle_view(sylv_handle h, OpData* op, int* device) {
+  if (!h) return SYLV_E_INVALID;
+  *op = h->op;
+  *device = h->device;
+  return SYLV_OK;
+}
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace sylv
+
 // ------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------

@@ -159,4 +159,8 @@ cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, co
                         int R, int want_beta, double* partial, int ntiles, double* out,
                         cudaStream_t s);
 
+// Handle internals for other translation units (runtime.cu).
+int handle_view(sylv_handle h, OpData* op, int* device);
+void set_last_error(const char* msg);
+
 }  // namespace sylv
