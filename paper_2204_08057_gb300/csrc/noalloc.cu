@@ -86,7 +86,9 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   const int ntiles = (int)((op.n + TILE_PX - 1) / TILE_PX);
   int nsm = 1;
   NA_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-  const int occ = occupancy<T>(op.k, op.m, op.E, 0, TILE_PX);
+  const int oa = occupancy<T>(0, op.k, op.m, op.E, 0, TILE_PX);
+  const int ou = occupancy<T>(1, op.k, op.m, op.E, 0, TILE_PX);
+  const int occ = oa < ou ? oa : ou;
   int nslots = ntiles < nsm * occ ? ntiles : nsm * occ;
   if (nslots > MAX_NOALLOC_CTAS) nslots = MAX_NOALLOC_CTAS;
   if (nslots < 1) nslots = 1;

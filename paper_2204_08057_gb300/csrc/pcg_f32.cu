@@ -46,18 +46,22 @@ cudaError_t update_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl
 }
 
 template <int K, int M, int E>
-int tma_occupancy() {
-  int a = 0, b = 0;
-  cudaFuncSetAttribute(tma::k_inner_apply_tma<K, M, E>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_tma_smem<K, M, E>());
-  cudaFuncSetAttribute(tma::k_inner_update_tma<K, M>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)update_tma_smem<K, M>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, tma::k_inner_apply_tma<K, M, E>, TILE_PX,
-                                                apply_tma_smem<K, M, E>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tma::k_inner_update_tma<K, M>, TILE_PX,
-                                                update_tma_smem<K, M>());
-  const int o = a < b ? a : b;
-  return o < 1 ? 1 : o;
+int tma_occupancy(int kind) {
+  int nb = 0;
+  if (kind == 0) {
+    cudaFuncSetAttribute(tma::k_inner_apply_tma<K, M, E>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)apply_tma_smem<K, M, E>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_apply_tma<K, M, E>, TILE_PX,
+                                                  apply_tma_smem<K, M, E>());
+  } else {
+    cudaFuncSetAttribute(tma::k_inner_update_tma<K, M>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)update_tma_smem<K, M>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_update_tma<K, M>, TILE_PX,
+                                                  update_tma_smem<K, M>());
+  }
+  return nb < 1 ? 1 : nb;
 }
 
 }  // namespace
@@ -67,7 +71,7 @@ int tma_occupancy() {
 #define SYLV_TMA_UPDATE_(K_, M_, E_) \
   if (k == K_ && m == M_ && e == E_) return update_tma<K_, M_>(ncta, d, c, ctl, s);
 #define SYLV_TMA_OCC_(K_, M_, E_) \
-  if (k == K_ && m == M_ && e == E_) return tma_occupancy<K_, M_, E_>();
+  if (k == K_ && m == M_ && e == E_) return tma_occupancy<K_, M_, E_>(kind);
 
 template <>
 cudaError_t launch_inner_apply<float>(int k, int m, int e, int variant, int ncta, int block,
@@ -100,11 +104,11 @@ cudaError_t launch_update_x<float>(int k, int ncta, int block, const SysDesc* d,
   return launch_update_x_impl<float>(k, ncta, block, d, c, s);
 }
 template <>
-int occupancy<float>(int k, int m, int e, int variant, int block) {
+int occupancy<float>(int kind, int k, int m, int e, int variant, int block) {
   if (variant == 1) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_OCC_)
   }
-  return occupancy_impl<float>(k, m, e, block);
+  return occupancy_impl<float>(kind, k, m, e, block);
 }
 
 }  // namespace sylv

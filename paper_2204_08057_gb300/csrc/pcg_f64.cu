@@ -28,9 +28,9 @@ cudaError_t launch_update_x<double>(int k, int ncta, int block, const SysDesc* d
   return launch_update_x_impl<double>(k, ncta, block, d, c, s);
 }
 template <>
-int occupancy<double>(int k, int m, int e, int variant, int block) {
+int occupancy<double>(int kind, int k, int m, int e, int variant, int block) {
   (void)variant;
-  return occupancy_impl<double>(k, m, e, block);
+  return occupancy_impl<double>(kind, k, m, e, block);
 }
 
 }  // namespace sylv

@@ -297,6 +297,62 @@ __device__ __forceinline__ void block_solve(const BlockChol<K, T>& f, const T (&
   for (int a = 0; a < K; ++a) z[a] *= f.s[a];
 }
 
+// FP64 operator from the precomputed pixel blocks: acc = P_i x_i + sum_j tau_j (L_off x_j)_i,
+// i.e. the same G x as apply_pixel with the pixel-local terms gathered into one k x k block
+// (k(k+1) FMAs instead of m(2k+1) + 2k; FP64 is the scarce unit on this GPU).
+template <int K, int E, typename TX, int NV>
+__device__ __forceinline__ void apply_pixel_blk64(const OpData& op,
+                                                  const CtaShared<double, NV>& sh,
+                                                  const TX* __restrict__ x, int64_t ldx,
+                                                  int64_t i, const double (&xi)[K],
+                                                  double (&acc)[K]) {
+  const int64_t ld = op.ld;
+  constexpr int EC = E > 0 ? E : 4;
+  const int Er = E > 0 ? E : op.E;
+#pragma unroll
+  for (int a = 0; a < K; ++a) acc[a] = 0.0;
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      const double pab = __ldg(op.blk64 + (size_t)(a * (a + 1) / 2 + b) * ld + i);
+      acc[a] += pab * xi[b];
+      if (b != a) acc[b] += pab * xi[a];
+    }
+  }
+  double lap[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) lap[j] = 0.0;
+  for (int e0 = 0; e0 < Er; e0 += EC) {
+    int64_t col[EC];
+    double val[EC];
+#pragma unroll
+    for (int t = 0; t < EC; ++t) {
+      const int e = E > 0 ? t : min(e0 + t, Er - 1);
+      col[t] = __ldg(op.ell_col + e * ld + i);
+      val[t] = __ldg(op.ell_val64 + e * ld + i);
+      if (E == 0 && e0 + t >= Er) val[t] = 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < EC; ++t)
+#pragma unroll
+      for (int j = 0; j < K; ++j) lap[j] += val[t] * double(x[j * ldx + col[t]]);
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j] += sh.tau[j] * lap[j];
+}
+
+// Loads the precomputed FP64 factor of the pixel block (see block_chol).
+template <int K>
+__device__ __forceinline__ void load_factor64(const OpData& op, int64_t i,
+                                              BlockChol<K, double>& f) {
+  const int64_t ld = op.ld;
+#pragma unroll
+  for (int a = 0; a < K; ++a) f.s[a] = __ldg(op.fac64 + (size_t)a * ld + i);
+#pragma unroll
+  for (int a = 0; a < K * (K + 1) / 2; ++a) f.l[a] = __ldg(op.fac64 + (size_t)(K + a) * ld + i);
+}
+
 // Adds this warp's share of NV sums of column r into the CTA's per-warp accumulators.
 template <typename T, int NV>
 __device__ __forceinline__ void warp_accumulate(CtaShared<T, NV>& sh, int r,
@@ -393,7 +449,11 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
       T zi[K], w[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) zi[j] = z[j * ld + i];
-      apply_pixel<K, M, E, T, T, 1>(op, sh, z, ld, i, zi, w);
+      if constexpr (sizeof(T) == 8) {
+        apply_pixel_blk64<K, E, T, 1>(op, sh, z, ld, i, zi, w);
+      } else {
+        apply_pixel<K, M, E, T, T, 1>(op, sh, z, ld, i, zi, w);
+      }
       T pq = T(0);
       if (valid) {
         const T beta = sh.sc[r];
@@ -471,7 +531,13 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
     BlockChol<K, T> f;
-    if (prec) block_chol<K, M, T, 2>(op, sh, i, f);
+    if (prec) {
+      if constexpr (sizeof(T) == 8) {
+        load_factor64<K>(op, i, f);
+      } else {
+        block_chol<K, M, T, 2>(op, sh, i, f);
+      }
+    }
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
       const size_t off = (size_t)r * K * ld;
@@ -598,7 +664,13 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
     BlockChol<K, T> f;
-    if (prec) block_chol<K, M, T, 1>(op, shT, i, f);
+    if (prec) {
+      if constexpr (sizeof(T) == 8) {
+        load_factor64<K>(op, i, f);
+      } else {
+        block_chol<K, M, T, 1>(op, shT, i, f);
+      }
+    }
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
       const size_t off = (size_t)r * K * ld;
@@ -612,7 +684,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
       double xi[K], gx[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) xi[j] = X[j * ldu + i];
-      apply_pixel<K, M, E, double, double, 4>(op, sh, X, ldu, i, xi, gx);
+      apply_pixel_blk64<K, E, double, 4>(op, sh, X, ldu, i, xi, gx);
       double rr64 = 0.0, bb = 0.0, rz = 0.0, rr = 0.0;
       if (valid) {
         T ri[K], zi[K];
@@ -777,27 +849,25 @@ cudaError_t launch_update_x_impl(int k, int ncta, int block, const SysDesc* d, c
   return cudaGetLastError();
 }
 
-// Resident CTAs per SM of the less occupant inner-iteration kernel for the shape.
+// Resident CTAs per SM of the plain inner kernel `kind` (0 apply, 1 update) for a shape.
 template <typename T>
-int occupancy_impl(int k, int m, int e, int block) {
-  int best = 1 << 30;
+int occupancy_impl(int kind, int k, int m, int e, int block) {
+  int nb = 0;
   auto take = [&](const void* fn) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) == cudaSuccess)
-      best = nb < best ? nb : best;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0) != cudaSuccess) nb = 1;
   };
   auto body = [&]() -> cudaError_t {
-#define CALL(K, M, E)                                      \
-  do {                                                     \
-    take((const void*)k_inner_apply<K, M, E, T>);          \
-    take((const void*)k_inner_update<K, M, E, T>);         \
+#define CALL(K, M, E)                                                     \
+  do {                                                                    \
+    if (kind == 0) take((const void*)k_inner_apply<K, M, E, T>);          \
+    else take((const void*)k_inner_update<K, M, E, T>);                   \
   } while (0)
     SYLV_DISPATCH_SHAPE(k, m, e)
 #undef CALL
     return cudaSuccess;
   };
   body();
-  return best == (1 << 30) || best < 1 ? 1 : best;
+  return nb < 1 ? 1 : nb;
 }
 
 }  // namespace sylv

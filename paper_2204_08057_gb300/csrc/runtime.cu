@@ -70,13 +70,18 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // ------------------------------------------------------------------------------------------
 struct Group {
   int k = 0, m = 0, e = 0;  // shape shared by the group's systems
-  int variant = 0;          // 1: bulk-copy staged FP32 inner kernels
-  int block = 256;
+  int has_w = 0;
+  std::vector<int> sys;     // systems of the group
+  int block = TILE_PX;      // pixels per tile = threads per CTA
+  int mult = 1;             // CTA slots = mult x resident CTAs
+  int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (1: staged)
   int ncta = 0;             // CTAs of every iteration launch over this group
+  int cta_cap = 0;
   CtaRef* d_ctas = nullptr;
 };
 
 struct SysWork {
+  int slot_cap = 0;          // partial-sum capacity in CTA slots
   void* vec = nullptr;       // 5 inner vectors
   ColState* st = nullptr;
   double* partial = nullptr;
@@ -84,6 +89,7 @@ struct SysWork {
 };
 
 struct Plan {
+  int device = 0, nsm = 1;
   std::vector<sylv_handle> hs;
   std::vector<int> R;
   int inner_double = 0;
@@ -122,6 +128,8 @@ struct sylv_ctx {
   double* D64 = nullptr;
   float* w32 = nullptr;
   double* w64 = nullptr;
+  double* blk64 = nullptr;
+  double* fac64 = nullptr;
   std::unique_ptr<Plan> plan[2];  // single-system plans, [inner_double]
   double* lam = nullptr;
   size_t lam_bytes = 0;
@@ -156,13 +164,6 @@ Plan::~Plan() {
 
 namespace {
 
-// Staged (bulk-copy) FP32 inner kernels where a shape has them; SYLV_NO_TMA=1 in the
-// environment selects the plain kernels (for comparisons).
-const bool g_use_tma = [] {
-  const char* v = std::getenv("SYLV_NO_TMA");
-  return !(v && v[0] == '1');
-}();
-
 // Batched plans, keyed by the list of (handle, nrhs) and the inner type.
 std::mutex g_plan_mu;
 std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> g_plans;
@@ -170,6 +171,181 @@ std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> g_plans;
 int default_block(int64_t n) {
   (void)n;
   return TILE_PX;
+}
+
+// ------------------------------------------------------------------------------------------
+// tiling of a group and the autotuner
+// ------------------------------------------------------------------------------------------
+// A configuration: tile size (threads per CTA), CTA slots as a multiple of what stays
+// resident, and the variant of each inner kernel.  configure_group computes every system's
+// tile and slot counts, uploads the group's CTA list and records them in the host descriptors
+// (uploaded before each solve).
+template <typename T>
+int configure_group(Plan& P, Group& g, int block, int mult, int va, int vu) {
+  const int oa = occupancy<T>(0, g.k, g.m, g.e, va, block);
+  const int ou = occupancy<T>(1, g.k, g.m, g.e, vu, block);
+  const int64_t budget = (int64_t)P.nsm * std::min(oa, ou) * mult;
+  int64_t total = 0;
+  for (int s : g.sys) total += ceil_div(P.hs[s]->op.n, block);
+  std::vector<CtaRef> cl;
+  for (int s : g.sys) {
+    const int nt = (int)ceil_div(P.hs[s]->op.n, block);
+    int64_t ns = total <= budget ? nt : (budget * nt) / total;
+    ns = std::max<int64_t>(1, std::min<int64_t>(ns, nt));
+    ns = std::min<int64_t>(ns, P.work[s].slot_cap);
+    P.h_desc[s].ntiles = nt;
+    P.h_desc[s].nslots = (int)ns;
+    for (int t = 0; t < ns; ++t) cl.push_back(CtaRef{s, t});
+  }
+  if ((int)cl.size() > g.cta_cap) return fail(SYLV_E_CUDA, "internal: CTA list overflow");
+  CK(cudaMemcpy(g.d_ctas, cl.data(), cl.size() * sizeof(CtaRef), cudaMemcpyHostToDevice));
+  g.ncta = (int)cl.size();
+  g.block = block;
+  g.mult = mult;
+  g.va = va;
+  g.vu = vu;
+  return SYLV_OK;
+}
+
+struct TuneChoice {
+  int block, mult, va, vu;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<int>, TuneChoice> g_tune;
+// SYLV_AUTOTUNE=0 skips timing and takes the default configuration.
+const bool g_autotune = [] {
+  const char* v = std::getenv("SYLV_AUTOTUNE");
+  return !(v && v[0] == '0');
+}();
+
+// Times one inner kernel over the group with every column forced into the inner phase.
+template <typename T>
+int time_inner(Plan& P, Group& g, int kind, int reps, float* ms_out) {
+  cudaStream_t s = P.cap_stream;
+  int rmax = 1;
+  for (int sidx : g.sys) rmax = std::max(rmax, P.R[sidx]);
+  std::vector<ColState> st(rmax, ColState{});
+  {
+    for (auto& c : st) {
+      c.phase = PH_INNER;
+      c.gamma = 1.0;
+      c.alpha = 0.25;
+      c.beta = 0.25;
+      c.rr_in = 1.0;
+      c.thr_in = 0.0;
+      c.first = 0;
+    }
+  }
+  float best = 1e30f;
+  for (int rep = 0; rep < reps + 1; ++rep) {
+    for (int sidx : g.sys) {
+      CK(cudaMemcpyAsync(P.work[sidx].st, st.data(), P.R[sidx] * sizeof(ColState),
+                         cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaEventRecord(P.evr0, s));
+    if (kind == 0)
+      CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta, g.block, P.d_desc, g.d_ctas,
+                               P.d_ctl, s));
+    else
+      CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta, g.block, P.d_desc, g.d_ctas,
+                                P.d_ctl, s));
+    CK(cudaEventRecord(P.evr1, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, P.evr0, P.evr1));
+    if (rep > 0) best = std::min(best, ms);
+  }
+  *ms_out = best;
+  return SYLV_OK;
+}
+
+// Chooses the group's configuration: cached per (device, inner type, shape, right-hand sides,
+// size bucket); otherwise every candidate is timed on the plan's own buffers (the inner
+// vectors hold a finite filler; the solve rewrites them before use).
+template <typename T>
+int tune_group(Plan& P, Group& g) {
+  const bool dbl = sizeof(T) == 8;
+  const bool can_tma = !dbl && !g.has_w && tma_available(g.k, g.m, g.e);
+  int64_t ntot = 0;
+  int rmax = 0;
+  for (int s : g.sys) {
+    ntot += P.hs[s]->op.n;
+    rmax = std::max(rmax, P.R[s]);
+  }
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= ntot) ++lg;
+  const std::vector<int> key = {P.device, (int)dbl, g.k, g.m, g.e, g.has_w, rmax, lg,
+                                (int)g.sys.size()};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      const TuneChoice& c = it->second;
+      return configure_group<T>(P, g, c.block, c.mult, c.va, c.vu);
+    }
+  }
+  const TuneChoice dflt{TILE_PX, 1, 0, can_tma ? 1 : 0, 0.f};
+  // SYLV_TUNE_FORCE="tile,mult,apply_variant,update_variant" pins a configuration (used to
+  // profile exactly the configuration a timed run chose)
+  if (const char* f = std::getenv("SYLV_TUNE_FORCE")) {
+    TuneChoice c = dflt;
+    if (std::sscanf(f, "%d,%d,%d,%d", &c.block, &c.mult, &c.va, &c.vu) == 4 &&
+        (c.block == 128 || c.block == TILE_PX) && c.mult >= 1 && c.mult <= 4) {
+      if (!can_tma || c.block != TILE_PX) c.va = c.vu = 0;
+      return configure_group<T>(P, g, c.block, c.mult, c.va ? 1 : 0, c.vu ? 1 : 0);
+    }
+  }
+  if (!g_autotune) return configure_group<T>(P, g, dflt.block, dflt.mult, dflt.va, dflt.vu);
+  // finite filler in the inner vectors and a permissive control word
+  for (int s : g.sys) {
+    const size_t vb = (size_t)P.R[s] * P.hs[s]->op.k * P.hs[s]->op.ld * sizeof(T);
+    CK(cudaMemsetAsync(P.work[s].vec, 0x3C, 5 * vb, P.cap_stream));
+  }
+  Control c{};
+  c.maxit = 1 << 30;
+  c.max_outer = 1 << 30;
+  c.precond = SYLV_PRECOND_BLOCK_JACOBI;
+  *P.h_ctl = c;
+  CK(cudaMemcpyAsync(P.d_ctl, P.h_ctl, sizeof(Control), cudaMemcpyHostToDevice, P.cap_stream));
+  std::vector<TuneChoice> cands;
+  for (int mult = 1; mult <= 2; ++mult) {
+    cands.push_back({128, mult, 0, 0, 0.f});
+    cands.push_back({TILE_PX, mult, 0, 0, 0.f});
+    if (can_tma) {
+      cands.push_back({TILE_PX, mult, 1, 0, 0.f});
+      cands.push_back({TILE_PX, mult, 0, 1, 0.f});
+      cands.push_back({TILE_PX, mult, 1, 1, 0.f});
+    }
+  }
+  TuneChoice best = dflt;
+  best.ms = 1e30f;
+  for (auto& cnd : cands) {
+    int rc = configure_group<T>(P, g, cnd.block, cnd.mult, cnd.va, cnd.vu);
+    if (rc != SYLV_OK) return rc;
+    CK(cudaMemcpyAsync(P.d_desc, P.h_desc, P.hs.size() * sizeof(SysDesc),
+                       cudaMemcpyHostToDevice, P.cap_stream));
+    float ta = 0, tu = 0;
+    if ((rc = time_inner<T>(P, g, 0, 3, &ta)) != SYLV_OK) return rc;
+    if ((rc = time_inner<T>(P, g, 1, 3, &tu)) != SYLV_OK) return rc;
+    cnd.ms = ta + tu;
+    if (cnd.ms < best.ms) best = cnd;
+  }
+  CK(cudaStreamSynchronize(P.cap_stream));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  if (const char* v = std::getenv("SYLV_TUNE_LOG")) {
+    if (v[0] == '1')
+      std::fprintf(stderr,
+                   "sylv autotune: %s k=%d m=%d E=%d systems=%zu nrhs<=%d n=%lld -> tile %d, "
+                   "slots x%d, apply %s, update %s (%.3f ms per iteration)\n",
+                   dbl ? "fp64" : "fp32", g.k, g.m, g.e, g.sys.size(), rmax, (long long)ntot,
+                   best.block, best.mult, best.va ? "staged" : "direct",
+                   best.vu ? "staged" : "direct", best.ms);
+  }
+  return configure_group<T>(P, g, best.block, best.mult, best.va, best.vu);
 }
 
 int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner_double) {
@@ -184,36 +360,24 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
   int dev = 0, nsm = 1;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  P.device = dev;
+  P.nsm = nsm;
   std::map<std::vector<int>, std::vector<int>> byshape;
   for (int s = 0; s < nsys; ++s)
     byshape[{hs[s]->op.k, hs[s]->op.m, hs[s]->op.E}].push_back(s);
-  std::vector<int> nslots(nsys), ntiles(nsys);
+  for (int s = 0; s < nsys; ++s)
+    P.work[s].slot_cap = (int)std::min<int64_t>(ceil_div(hs[s]->op.n, 128), (int64_t)nsm * 32);
   for (auto& kv : byshape) {
     Group g;
     g.k = kv.first[0];
     g.m = kv.first[1];
     g.e = kv.first[2];
-    g.block = default_block(0);
-    bool any_w = false;
-    for (int s : kv.second) any_w = any_w || hs[s]->op.has_w;
-    g.variant = (!inner_double && !any_w && g_use_tma && tma_available(g.k, g.m, g.e)) ? 1 : 0;
-    const int occ = inner_double ? occupancy<double>(g.k, g.m, g.e, g.variant, g.block)
-                                 : occupancy<float>(g.k, g.m, g.e, g.variant, g.block);
-    const int64_t budget = (int64_t)nsm * std::max(occ, 1);
-    int64_t total = 0;
+    g.sys = kv.second;
     for (int s : kv.second) {
-      ntiles[s] = (int)ceil_div(hs[s]->op.n, g.block);
-      total += ntiles[s];
+      g.has_w = g.has_w || hs[s]->op.has_w;
+      g.cta_cap += P.work[s].slot_cap;
     }
-    std::vector<CtaRef> cl;
-    for (int s : kv.second) {
-      int64_t ns = total <= budget ? ntiles[s] : (budget * ntiles[s]) / total;
-      nslots[s] = (int)std::max<int64_t>(1, std::min<int64_t>(ns, ntiles[s]));
-      for (int t = 0; t < nslots[s]; ++t) cl.push_back(CtaRef{s, t});
-    }
-    g.ncta = (int)cl.size();
-    CK(dalloc(&g.d_ctas, cl.size() * sizeof(CtaRef)));
-    CK(cudaMemcpy(g.d_ctas, cl.data(), cl.size() * sizeof(CtaRef), cudaMemcpyHostToDevice));
+    CK(dalloc(&g.d_ctas, (size_t)g.cta_cap * sizeof(CtaRef)));
     P.groups.push_back(g);
   }
   for (int s = 0; s < nsys; ++s) {
@@ -223,7 +387,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     CK(dalloc(&w.vec, 5 * vbytes));
     CK(cudaMemset(w.vec, 0, 5 * vbytes));
     CK(dalloc(&w.st, R[s] * sizeof(ColState)));
-    CK(dalloc(&w.partial, (size_t)nslots[s] * R[s] * NPART * sizeof(double)));
+    CK(dalloc(&w.partial, (size_t)w.slot_cap * R[s] * NPART * sizeof(double)));
     CK(dalloc(&w.counter, sizeof(unsigned int)));
     CK(cudaMemset(w.counter, 0, sizeof(unsigned int)));
     for (int r = 0; r < R[s]; ++r) {
@@ -248,8 +412,8 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     std::memset(&d, 0, sizeof(SysDesc));
     d.op = hs[s]->op;
     d.R = R[s];
-    d.ntiles = ntiles[s];
-    d.nslots = nslots[s];
+    d.ntiles = 0;  // set by configure_group
+    d.nslots = 0;
     const size_t vbytes = (size_t)R[s] * d.op.k * d.op.ld * tsz;
     char* base = (char*)P.work[s].vec;
     d.vd = base;
@@ -266,6 +430,10 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
   CK(cudaEventCreate(&P.ev1));
   CK(cudaEventCreate(&P.evr0));
   CK(cudaEventCreate(&P.evr1));
+  for (auto& g : P.groups) {
+    int rc = inner_double ? tune_group<double>(P, g) : tune_group<float>(P, g);
+    if (rc != SYLV_OK) return rc;
+  }
   return SYLV_OK;
 }
 
@@ -273,12 +441,12 @@ template <typename T>
 int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
                            bool capture_events) {
   for (auto& g : P.groups)
-    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.variant, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_mid)
     CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_mid, s));
   for (auto& g : P.groups)
-    CK(launch_inner_update<T>(g.k, g.m, g.e, g.variant, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
   if (e_end)
     CK(capture_events ? cudaEventRecordWithFlags(e_end, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_end, s));
@@ -557,6 +725,8 @@ static void free_handle(sylv_ctx* h) {
   cudaFree(h->D64);
   cudaFree(h->w32);
   cudaFree(h->w64);
+  cudaFree(h->blk64);
+  cudaFree(h->fac64);
   cudaFree(h->lam);
   cudaFree(h->grad_ws);
   delete h;
@@ -704,6 +874,18 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return bail(cuda_fail(e, "operator set-up"));
   if (hflags[0]) return bail(fail(SYLV_E_INVALID, "D (>= 0) or w (> 0) has invalid entries"));
+  // FP64 pixel blocks and their factors (FP64 operator and preconditioner)
+  const size_t nb = (size_t)p->k * (p->k + 1) / 2;
+  if ((e = dalloc(&h->blk64, nb * ld * sizeof(double))) != cudaSuccess ||
+      (e = dalloc(&h->fac64, (nb + p->k) * ld * sizeof(double))) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->blk64, 0, nb * ld * sizeof(double), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->fac64, 0, (nb + p->k) * ld * sizeof(double), s)) != cudaSuccess)
+    return bail(cuda_fail(e, "cudaMalloc (pixel blocks)"));
+  op.blk64 = h->blk64;
+  op.fac64 = h->fac64;
+  if ((e = launch_block_setup(op, h->blk64, h->fac64, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return bail(cuda_fail(e, "pixel-block set-up"));
   cudaFree(dflags);
   *out = h;
   (void)rc;

@@ -108,6 +108,39 @@ __global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restric
   }
 }
 
+// Pixel blocks P_i (FP64) and their scaled Cholesky factors, once per handle.
+template <int K>
+__global__ void __launch_bounds__(256) k_block_setup(OpData op, double* __restrict__ blk,
+                                                     double* __restrict__ fac) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= op.n) return;
+  const int64_t ld = op.ld;
+  double P[K * (K + 1) / 2];
+#pragma unroll
+  for (int a = 0; a < K * (K + 1) / 2; ++a) P[a] = 0.0;
+  for (int c = 0; c < op.m; ++c) {
+    const double d = op.D64[c * ld + i];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      const double da = d * op.A64[c * K + a];
+#pragma unroll
+      for (int b = 0; b <= a; ++b) P[a * (a + 1) / 2 + b] += da * op.A64[c * K + b];
+    }
+  }
+  const double wi = op.has_w ? op.w64[i] : 1.0;
+  const double dg = op.diag64[i];
+#pragma unroll
+  for (int a = 0; a < K; ++a) P[a * (a + 1) / 2 + a] += op.tk2_64[a] * wi + op.tau64[a] * dg;
+#pragma unroll
+  for (int a = 0; a < K * (K + 1) / 2; ++a) blk[(size_t)a * ld + i] = P[a];
+  BlockChol<K, double> f;
+  block_chol_factor<K, double>(P, f);
+#pragma unroll
+  for (int a = 0; a < K; ++a) fac[(size_t)a * ld + i] = f.s[a];
+#pragma unroll
+  for (int a = 0; a < K * (K + 1) / 2; ++a) fac[(size_t)(K + a) * ld + i] = f.l[a];
+}
+
 // Stand-alone operator apply Y = G X (eq. block-vector-mapping-matvec with Algorithm 1);
 // grid-stride over pixels.
 template <int K, int M, int E, typename T>
@@ -262,6 +295,14 @@ cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int
   if (tot == 0) return cudaSuccess;
   k_convert_check<<<blocks_for(tot, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(
       src, rows, n, ld_src, ld_dst, dst32, dst64, positive, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, cudaStream_t s) {
+  const int nb = blocks_for(op.n, 256);
+#define CALL(K) k_block_setup<K><<<nb, 256, 0, s>>>(op, blk64, fac64)
+  SYLV_DISPATCH_K(op.k, CALL)
+#undef CALL
   return cudaGetLastError();
 }
 

@@ -70,6 +70,9 @@ struct OpData {
   const double* D64;
   const float* w32;          // ld or null
   const double* w64;
+  const double* blk64;       // K(K+1)/2 x ld: packed lower triangle of the pixel block
+                             // P_i = diag_j(tau_j (kappa_j^2 w_i + L_ii)) + sum_c d_ci a_c a_c^T
+  const double* fac64;       // (K + K(K+1)/2) x ld: scaling and factor of P_i (block_chol)
   float A32[MMAX * KMAX];    // A[c * k + j]
   double A64[MMAX * KMAX];
   float tau32[KMAX];
@@ -137,8 +140,9 @@ cudaError_t launch_residual(int k, int m, int e, int ncta, int block, const SysD
 template <typename T>
 cudaError_t launch_update_x(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
                             cudaStream_t s);
+// Resident CTAs per SM of one inner kernel (kind 0: apply, 1: update) for a shape.
 template <typename T>
-int occupancy(int k, int m, int e, int variant, int block);
+int occupancy(int kind, int k, int m, int e, int variant, int block);
 cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,
                                const SysDesc* d, Control* c, cudaStream_t s);
 
@@ -153,6 +157,7 @@ cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int
                                  int64_t ld_dst, float* dst32, double* dst64, int positive,
                                  unsigned int* flags, cudaStream_t s);
 cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s);
+cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s);
 cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, const double* Y,
