@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one untimed solve and three applies of the workload (for ncu)")
     return ap.parse_args()
 
 
@@ -115,6 +117,36 @@ def bytes_inner_update(k, m, s=4):
 def bytes_apply(k, m, E, R=1, s=4):
     # read X (R k) + D (m) + ELL values (E) + diagonal (1); write Y (R k); ELL cols int32
     return (2 * R * k + m + E + 1) * s + 4 * E
+
+
+KERNEL_SOURCES = ["pcg_kernels.cuh", "pcg_tma.cuh", "sylv_internal.cuh"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2204_08057_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of ``kernel`` recorded in profiles/ by an ncu capture, if the
+    kernel sources are unchanged since (else None)."""
+    import glob
+    import re
+    cur = kernel_source_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read()
+        m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+        if not m or m.group(1) != cur:
+            continue
+        m = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+]+)",
+                      text)
+        if m:
+            return float(m.group(1))
+    return None
 
 
 def load_peaks():
@@ -286,15 +318,18 @@ def run_ours(args, rank, world, local_rank):
     tot_update = sum(i["ms_update"] for i in infos)
     n_ap = sum(i["n_apply"] for i in infos)
     n_up = sum(i["n_update"] for i in infos)
+    shape = f"{p.k},{p.m},{E}" if E else f"{p.k},0,0"
     if tot_apply >= tot_update:
-        kname, avg_ms, per_px = "k_inner_apply<6,float>", tot_apply / n_ap, \
-            bytes_inner_apply(p.k, p.m, E)
+        kname = (f"k_inner_apply_tma<{shape}>" if last["apply_staged"]
+                 else f"k_inner_apply<{shape},float>")
+        avg_ms, per_px = tot_apply / n_ap, bytes_inner_apply(p.k, p.m, E)
     else:
-        kname, avg_ms, per_px = "k_inner_update<6,float>", tot_update / n_up, \
-            bytes_inner_update(p.k, p.m)
+        kname = (f"k_inner_update_tma<{p.k},{p.m}>" if last["update_staged"]
+                 else f"k_inner_update<{shape},float>")
+        avg_ms, per_px = tot_update / n_up, bytes_inner_update(p.k, p.m)
     achieved = per_px * p.n / (avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": kname,
+                "frac": achieved / peak, "traffic": profiled_traffic(kname), "kernel": kname,
                 "bytes_per_launch": per_px * p.n, "avg_launch_ms": avg_ms,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
 
@@ -339,6 +374,12 @@ def run_ours(args, rank, world, local_rank):
                        "per_rank": "independent instance per rank (own seed)"},
             "iterations": last["iterations"], "outer": last["outer"],
             "relres": last["relres"],
+            "autotune": {"tile": last["tile"], "slots_mult": last["slots_mult"],
+                         "apply_staged": last["apply_staged"],
+                         "update_staged": last["update_staged"],
+                         "force_env": "SYLV_TUNE_FORCE=%d,%d,%d,%d" % (
+                             last["tile"], last["slots_mult"], last["apply_staged"],
+                             last["update_staged"])},
             "fp64_pcg": {"ms": ms64, "iterations": info64["iterations"],
                          "relres": info64["relres"], "speedup_mixed": ms64 / ms,
                          "relerr_mixed_vs_fp64": relerr_mixed_vs_fp64},
@@ -360,8 +401,146 @@ def run_ours(args, rank, world, local_rank):
     op.close()
 
 
+def make_operator(p, device=None):
+    from paper_2204_08057_gb300.operator import Operator
+    return Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
+                    kappa=p.kappa, nu=p.nu, beta=p.beta)
+
+
+def run_profile_case(args):
+    """One solve (no graphs, polls every 4 iterations) and three FP32 applies of the workload:
+    the launches an ncu capture of the inner kernels looks at."""
+    import torch
+    import synth
+    from paper_2204_08057_gb300 import build as _build
+    _build.build()
+    p = synth.config_problem(args.config, scale=args.scale)
+    op = make_operator(p)
+    B = op.rhs(torch.from_numpy(p.Yobs).cuda())
+    X, info = op.solve(B, tol=p.tol, use_graph=0, check_every=4)
+    X32 = X.to(torch.float32)
+    for _ in range(3):
+        op.apply(X32)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": p.name, "info": info}), flush=True)
+    op.close()
+
+
+def _timed(stream, fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def _base_line(args, metric, value, unit, config, higher=False):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value, "higher_is_better": higher,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded; see DESIGN.md input recipe)", "config": config}
+
+
+def run_batched(args):
+    """64 independent lattice systems (sides 128..1024, k in 3..6, m = k + 2) in one
+    sylv_solve_batched call vs the same systems solved one by one and vs FP64 batched."""
+    import torch
+    import synth
+    from paper_2204_08057_gb300 import build as _build
+    from paper_2204_08057_gb300.operator import solve_batched
+    _build.build()
+    torch.cuda.set_device(0)
+    probs = synth.batch_problems(64)
+    ops = [make_operator(p) for p in probs]
+    Bs = [op.rhs(torch.from_numpy(p.Yobs).cuda()) for op, p in zip(ops, probs)]
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=1e-8, precision=1, profile=1)
+    for _ in range(args.warmup):
+        Xs, infos = solve_batched(ops, Bs, **kw)
+    clocks = ClockSampler(0) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    ms, (Xs, infos) = _timed(stream, lambda: solve_batched(ops, Bs, **kw), args.steps)
+    clk = clocks.stop() if clocks else None
+    assert all(i["status"] == 0 for i in infos), infos
+    for op, b in zip(ops, Bs):
+        op.solve(b, tol=1e-8)
+    ms_seq, _ = _timed(stream, lambda: [op.solve(b, tol=1e-8) for op, b in zip(ops, Bs)], 1)
+    solve_batched(ops, Bs, tol=1e-8, precision=0)
+    ms64, (X64, i64) = _timed(stream, lambda: solve_batched(ops, Bs, tol=1e-8, precision=0), 1)
+    rel = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(Xs, X64))
+    ntot = sum(p.n for p in probs)
+    line = _base_line(args, "batched solve time to relres 1e-8 (64 systems, one call)", ms, "ms",
+                      {"workload": "batch64_lattice128-1024_k3-6", "systems": len(probs),
+                       "total_pixels": ntot, "tol": 1e-8, "precision": "mixed"})
+    line.update({
+        "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms,
+        "fp64_batched_ms": ms64, "speedup_vs_fp64": ms64 / ms,
+        "max_relerr_mixed_vs_fp64": rel,
+        "iterations_max": max(i["iterations"] for i in infos),
+        "relres_max": max(i["relres"] for i in infos),
+        "kernel_ms_per_solve": {"inner_apply": infos[0]["ms_apply"],
+                                "inner_update": infos[0]["ms_update"],
+                                "residual64": infos[0]["ms_residual"]},
+        "gpu_launches": infos[0]["launches"], "clocks": clk,
+    })
+    print(json.dumps(line), flush=True)
+    for op in ops:
+        op.close()
+
+
+def run_differentiable(args):
+    """Forward solve plus adjoint solve and gradient reduction (loss ||X - X_true||^2) on the
+    512 x 1024 sphere, k = 4, m = 7."""
+    import torch
+    import synth
+    from paper_2204_08057_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(0)
+    p = synth.config_problem(4, scale=args.scale)
+    op = make_operator(p)
+    Y = torch.from_numpy(p.Yobs).cuda()
+    Xt = torch.from_numpy(p.X_true).cuda()[None]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        X, info = op.solve(op.rhs(Y), tol=1e-8)
+        gt, gk, gb, lam, info2 = op.backward(X, 2.0 * (X - Xt), Y, tol=1e-8)
+        return X, gt, gk, gb, info, info2
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(0) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    ms, out = _timed(stream, step, args.steps)
+    clk = clocks.stop() if clocks else None
+    X, gt, gk, gb, info, info2 = out
+    line = _base_line(args, "forward + adjoint gradient step time (tol 1e-8)", ms, "ms",
+                      {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "tol": 1e-8})
+    line.update({"forward_iterations": info["iterations"],
+                 "adjoint_iterations": info2["iterations"],
+                 "g_tau": list(map(float, gt)), "g_kappa": list(map(float, gk)),
+                 "g_beta": list(map(float, gb)), "clocks": clk})
+    print(json.dumps(line), flush=True)
+    op.close()
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    if args.impl == "ours" and args.config in (3, 4):
+        (run_batched if args.config == 3 else run_differentiable)(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

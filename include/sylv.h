@@ -117,6 +117,11 @@ typedef struct {
   int32_t n_update;
   int32_t n_residual;
   int32_t launches;    /* kernels this call launched (inside graphs included)             */
+  /* configuration the autotuner chose for the inner kernels (first shape group)          */
+  int32_t tile;        /* pixels per tile = threads per CTA                                 */
+  int32_t slots_mult;  /* CTA slots as a multiple of the resident CTAs                      */
+  int32_t apply_staged;  /* 1: operator kernel stages its streams with bulk copies         */
+  int32_t update_staged; /* 1: update kernel stages its streams with bulk copies           */
 } sylv_info;
 
 /* Fills *o with the defaults.  Returns SYLV_OK, or SYLV_E_INVALID if o is NULL. */

@@ -216,6 +216,8 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   }
   inf.polls = (int32_t)polls;
   inf.launches = (int32_t)launches;
+  inf.tile = TILE_PX;
+  inf.slots_mult = 1;
   inf.ms_total =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;

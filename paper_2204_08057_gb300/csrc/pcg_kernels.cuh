@@ -417,6 +417,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, Control* ctl) {
   __shared__ CtaShared<T, 1> sh;
   const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
@@ -507,6 +508,7 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
                Control* ctl) {
   __shared__ CtaShared<T, 2> sh;
   const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
@@ -615,6 +617,7 @@ template <int K, typename T>
 __global__ void __launch_bounds__(256)
 k_update_x(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas) {
   const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const int64_t ld = sd.op.ld, ldu = sd.op.ldu, n = sd.op.n;
   for (int r = 0; r < sd.R; ++r) {
@@ -639,6 +642,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
   __shared__ CtaShared<double, 4> sh;     // FP64 operator
   __shared__ CtaShared<T, 1> shT;         // inner-type preconditioner data
   const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;

@@ -133,6 +133,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   __shared__ int s_cols[RMAX];
   __shared__ int s_nact;
   const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
@@ -303,6 +304,7 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
   __shared__ int s_cols[RMAX];
   __shared__ int s_nact;
   const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;

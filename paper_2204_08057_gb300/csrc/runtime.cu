@@ -75,9 +75,11 @@ struct Group {
   int block = TILE_PX;      // pixels per tile = threads per CTA
   int mult = 1;             // CTA slots = mult x resident CTAs
   int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (1: staged)
-  int ncta = 0;             // CTAs of every iteration launch over this group
+  int ncta = 0;             // CTAs of every iteration launch over this group (fixed)
   int cta_cap = 0;
   CtaRef* d_ctas = nullptr;
+  CtaRef* h_ctas = nullptr;  // pinned staging for reassignments
+  std::vector<int> cur_set;  // systems the CTA list currently covers
 };
 
 struct SysWork {
@@ -102,6 +104,8 @@ struct Plan {
   Control* h_ctl = nullptr;     // pinned
   unsigned int* h_poll = nullptr;  // pinned: n_active, n_unfinished, error
   ColState* h_states = nullptr;    // pinned, ncols
+  ColState* d_states = nullptr;    // ncols, contiguous; system s starts at col_off[s]
+  std::vector<int> col_off;
   int* d_col_sys = nullptr;
   int* d_col_rhs = nullptr;
   std::vector<int> col_sys, col_rhs;
@@ -138,10 +142,13 @@ struct sylv_ctx {
 };
 
 Plan::~Plan() {
-  for (auto& g : groups) cudaFree(g.d_ctas);
+  for (auto& g : groups) {
+    cudaFree(g.d_ctas);
+    cudaFreeHost(g.h_ctas);
+  }
+  cudaFree(d_states);
   for (auto& w : work) {
     cudaFree(w.vec);
-    cudaFree(w.st);
     cudaFree(w.partial);
     cudaFree(w.counter);
   }
@@ -200,10 +207,84 @@ int configure_group(Plan& P, Group& g, int block, int mult, int va, int vu) {
   if ((int)cl.size() > g.cta_cap) return fail(SYLV_E_CUDA, "internal: CTA list overflow");
   CK(cudaMemcpy(g.d_ctas, cl.data(), cl.size() * sizeof(CtaRef), cudaMemcpyHostToDevice));
   g.ncta = (int)cl.size();
+  g.cur_set = g.sys;
   g.block = block;
   g.mult = mult;
   g.va = va;
   g.vu = vu;
+  return SYLV_OK;
+}
+
+// Spreads the group's fixed number of CTAs over the systems in `set` only (in proportion to
+// their tiles), padding with idle entries; called between kernels when systems finish, so
+// that the remaining ones get the whole GPU.  Asynchronous on s (pinned staging).
+int reassign_group(Plan& P, Group& g, const std::vector<int>& set, cudaStream_t s) {
+  if (set == g.cur_set) return SYLV_OK;
+  int64_t total = 0;
+  for (int sy : set) total += P.h_desc[sy].ntiles;
+  std::vector<int64_t> ns(set.size());
+  int64_t sum = 0;
+  for (size_t t = 0; t < set.size(); ++t) {
+    const int sy = set[t];
+    const int64_t nt = P.h_desc[sy].ntiles;
+    int64_t v = total <= g.ncta ? nt : ((int64_t)g.ncta * nt) / total;
+    v = std::max<int64_t>(1, std::min<int64_t>({v, nt, (int64_t)P.work[sy].slot_cap}));
+    ns[t] = v;
+    sum += v;
+  }
+  while (sum > g.ncta) {  // the launch grid is fixed (captured graphs): trim the largest shares
+    size_t big = 0;
+    for (size_t t = 1; t < ns.size(); ++t)
+      if (ns[t] > ns[big]) big = t;
+    if (ns[big] <= 1) return fail(SYLV_E_CUDA, "internal: more systems than CTAs");
+    --ns[big];
+    --sum;
+  }
+  int used = 0;
+  for (size_t t = 0; t < set.size(); ++t) {
+    P.h_desc[set[t]].nslots = (int)ns[t];
+    for (int q = 0; q < ns[t]; ++q) g.h_ctas[used++] = CtaRef{set[t], q};
+  }
+  for (int t = used; t < g.ncta; ++t) g.h_ctas[t] = CtaRef{-1, 0};
+  CK(cudaMemcpyAsync(g.d_ctas, g.h_ctas, (size_t)g.ncta * sizeof(CtaRef), cudaMemcpyHostToDevice,
+                     s));
+  g.cur_set = set;
+  return SYLV_OK;
+}
+
+// Systems of group g with a column in one of the given phases (from the last state read).
+std::vector<int> systems_in_phase(const Plan& P, const Group& g, int ph_a, int ph_b) {
+  std::vector<int> out;
+  for (int sy : g.sys) {
+    for (int r = 0; r < P.R[sy]; ++r) {
+      const int ph = P.h_states[P.col_off[sy] + r].phase;
+      if (ph == ph_a || ph == ph_b) {
+        out.push_back(sy);
+        break;
+      }
+    }
+  }
+  return out;
+}
+
+// Before the residual of a refinement step (want_inner false) or before a chunk of inner
+// iterations (true): cover only the systems that have work in that phase, and upload the
+// descriptors whose slot counts changed.
+int rebalance(Plan& P, bool want_inner, cudaStream_t s) {
+  if (P.hs.size() <= 1) return SYLV_OK;
+  bool changed = false;
+  for (auto& g : P.groups) {
+    std::vector<int> set = want_inner ? systems_in_phase(P, g, PH_INNER, PH_INNER)
+                                      : systems_in_phase(P, g, PH_START, PH_INNER_DONE);
+    if (set != g.cur_set) {
+      int rc = reassign_group(P, g, set, s);
+      if (rc != SYLV_OK) return rc;
+      changed = true;
+    }
+  }
+  if (changed)
+    CK(cudaMemcpyAsync(P.d_desc, P.h_desc, P.hs.size() * sizeof(SysDesc),
+                       cudaMemcpyHostToDevice, s));
   return SYLV_OK;
 }
 
@@ -377,7 +458,9 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
       g.has_w = g.has_w || hs[s]->op.has_w;
       g.cta_cap += P.work[s].slot_cap;
     }
+    g.cta_cap += 1;
     CK(dalloc(&g.d_ctas, (size_t)g.cta_cap * sizeof(CtaRef)));
+    CK(cudaMallocHost((void**)&g.h_ctas, (size_t)g.cta_cap * sizeof(CtaRef)));
     P.groups.push_back(g);
   }
   for (int s = 0; s < nsys; ++s) {
@@ -386,7 +469,8 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     const size_t vbytes = (size_t)R[s] * op.k * op.ld * tsz;
     CK(dalloc(&w.vec, 5 * vbytes));
     CK(cudaMemset(w.vec, 0, 5 * vbytes));
-    CK(dalloc(&w.st, R[s] * sizeof(ColState)));
+    P.col_off.push_back(P.ncols);
+    P.ncols += R[s];
     CK(dalloc(&w.partial, (size_t)w.slot_cap * R[s] * NPART * sizeof(double)));
     CK(dalloc(&w.counter, sizeof(unsigned int)));
     CK(cudaMemset(w.counter, 0, sizeof(unsigned int)));
@@ -395,7 +479,8 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
       P.col_rhs.push_back(r);
     }
   }
-  P.ncols = (int)P.col_sys.size();
+  CK(dalloc(&P.d_states, (size_t)P.ncols * sizeof(ColState)));
+  for (int s = 0; s < nsys; ++s) P.work[s].st = P.d_states + P.col_off[s];
   CK(dalloc(&P.d_desc, nsys * sizeof(SysDesc)));
   CK(cudaMallocHost((void**)&P.h_desc, nsys * sizeof(SysDesc)));
   CK(dalloc(&P.d_ctl, sizeof(Control)));
@@ -495,6 +580,9 @@ int ensure_graph(Plan& P, int iters, int profile) {
 int poll(Plan& P, cudaStream_t s) {
   CK(cudaMemcpyAsync(P.h_poll, &P.d_ctl->n_active, 3 * sizeof(unsigned int),
                      cudaMemcpyDeviceToHost, s));
+  if (P.hs.size() > 1)
+    CK(cudaMemcpyAsync(P.h_states, P.d_states, (size_t)P.ncols * sizeof(ColState),
+                       cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (P.h_poll[2]) return fail(SYLV_E_TIMEOUT, "a bounded device-side wait expired");
   return SYLV_OK;
@@ -547,7 +635,15 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
     for (auto& e : direct_events) CK(cudaEventCreate(&e));
   }
   int rc = SYLV_OK;
+  // every system starts in the residual phase: cover all of them
+  for (auto& g : P.groups) {
+    if ((rc = reassign_group(P, g, g.sys, s)) != SYLV_OK) return rc;
+  }
+  CK(cudaMemcpyAsync(P.d_desc, P.h_desc, nsys * sizeof(SysDesc), cudaMemcpyHostToDevice, s));
+  bool first_outer = true;
   while (true) {
+    if (!first_outer && (rc = rebalance(P, false, s)) != SYLV_OK) return rc;
+    first_outer = false;
     for (auto& g : P.groups)
       CK(launch_update_x<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, s));
     if (prof) CK(cudaEventRecord(P.evr0, s));
@@ -569,6 +665,7 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
         gave_up = true;
         break;
       }
+      if ((rc = rebalance(P, true, s)) != SYLV_OK) return rc;
       if (o.use_graph) {
         CK(cudaGraphLaunch(P.graph, s));
       } else {
@@ -639,6 +736,12 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
     inf.n_update = n_update;
     inf.n_residual = n_res;
     inf.launches = (int32_t)std::min<long>(launches, INT32_MAX);
+    if (!P.groups.empty()) {
+      inf.tile = P.groups[0].block;
+      inf.slots_mult = P.groups[0].mult;
+      inf.apply_staged = P.groups[0].va;
+      inf.update_staged = P.groups[0].vu;
+    }
     if (infos) infos[t] = inf;
     if (inf.status != SYLV_OK && (worst == SYLV_OK || inf.status == SYLV_E_BREAKDOWN))
       worst = inf.status;

@@ -116,7 +116,7 @@ struct Control {
 };
 
 struct CtaRef {
-  int sys;   // system of this CTA
+  int sys;   // system of this CTA (-1: idle, the CTA returns at once)
   int slot;  // 0..nslots-1 within the system
 };
 
