@@ -226,6 +226,32 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def rank_problem(config, rank, scale=None):
+    """Weak scaling: rank r solves its own instance of the workload (same grid and shape,
+    its own seeded noise maps, spectral parameters and observations)."""
+    import synth
+    p = synth.config_problem(config, scale=scale)
+    if rank > 0:
+        p = synth.make_problem(p.name, p.graph, p.k, p.nu, None, None, p.tau,
+                               synth.CONFIG_SEED_BASE + 100 * rank + config,
+                               beta_draw=(-3.0, 2.0), kappa_draw=(0.01, 1.0), tol=p.tol,
+                               nrhs=p.nrhs) if config in (2, 4, 5) else \
+            synth.make_problem(p.name, p.graph, p.k, p.nu, p.beta, p.kappa, p.tau,
+                               synth.CONFIG_SEED_BASE + 100 * rank + config, tol=p.tol,
+                               nrhs=p.nrhs)
+    return p
+
+
+def max_over_ranks(value, dist, device="cpu"):
+    """The slowest rank's time (every rank gets it)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import synth
@@ -240,10 +266,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
 
     # weak scaling: every rank solves its own independent instance (own seed)
-    p = synth.config_problem(args.config, scale=args.scale)
-    if rank > 0:
-        p = synth.make_problem(p.name, p.graph, p.k, p.nu, p.beta, p.kappa, p.tau,
-                               synth.CONFIG_SEED_BASE + 100 * rank + args.config)
+    p = rank_problem(args.config, rank, args.scale)
     op = Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
                   kappa=p.kappa, nu=p.nu, beta=p.beta)
     E = int(np.max(np.diff(p.graph.rowptr))) - 1
@@ -276,10 +299,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop() if clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     last = infos[-1]
     assert last["code"] == 0, last
 
@@ -349,10 +369,7 @@ def run_ours(args, rank, world, local_rank):
     g1.record(stream)
     barrier()
     ms_e2e = g0.elapsed_time(g1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ms_e2e, dist, dev)
 
     # ---- CPU oracle baseline (rank 0, N = 1) -------------------------------------------------
     cpu = None
