@@ -45,8 +45,16 @@ def adjoint_gradient(L, D, tau, kappa, nu, beta, Y, X, g, w=None):
     """Returns (g_tau, g_kappa, g_beta, lambda) for loss gradient g = dl/dX."""
     A = model.powerlaw_mixing(nu, beta)
     G = model.assemble_G(L, D, tau, kappa, A, w)
-    Xb, gb, Yb = _as_batch(X), _as_batch(g), _as_batch(Y)
-    lam = solve.solve_direct(G, gb)
+    lam = solve.solve_direct(G, _as_batch(g))
+    gt, gk, gb = gradient_from_adjoint(L, D, tau, kappa, nu, beta, Y, X, lam, w)
+    return gt, gk, gb, (lam[0] if np.ndim(X) == 2 else lam)
+
+
+def gradient_from_adjoint(L, D, tau, kappa, nu, beta, Y, X, lam, w=None):
+    """The three gradient formulas for a given adjoint lambda (= G^{-1} dl/dX)."""
+    A = model.powerlaw_mixing(nu, beta)
+    Xb, Yb = _as_batch(X), _as_batch(Y)
+    lam = _as_batch(lam)
     k = A.shape[1]
     n = L.shape[0]
     wv = np.ones(n) if w is None else np.asarray(w, np.float64)
@@ -66,7 +74,7 @@ def adjoint_gradient(L, D, tau, kappa, nu, beta, Y, X, g, w=None):
             for j in range(k):
                 g_beta[j] += logf[c] * A[c, j] * (
                     lm[j] @ (D[c] * y[c]) - La[c] @ (D[c] * x[j]) - lm[j] @ (D[c] * Xa[c]))
-    return g_tau, g_kappa, g_beta, (lam[0] if np.ndim(X) == 2 else lam)
+    return g_tau, g_kappa, g_beta
 
 
 def sensitivity_gradient(L, D, tau, kappa, nu, beta, Y, g, w=None):
