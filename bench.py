@@ -334,10 +334,12 @@ def run_ours(args, rank, world, local_rank):
     apply_gbs = apply_bytes / (ms_apply * 1e-3) / 1e9
 
     # ---- roofline of the dominant kernel (from the timed steps' events) ---------------------
+    # kernel time summed over every launch of the timed solves (including the few launches at
+    # the end of a graph chunk that find nothing left to do), divided by the launches that
+    # did work (one per inner iteration): a conservative per-launch time
     tot_apply = sum(i["ms_apply"] for i in infos)
     tot_update = sum(i["ms_update"] for i in infos)
-    n_ap = sum(i["n_apply"] for i in infos)
-    n_up = sum(i["n_update"] for i in infos)
+    n_ap = n_up = sum(i["iterations"] for i in infos)
     shape = f"{p.k},{p.m},{E}" if E else f"{p.k},0,0"
     if tot_apply >= tot_update:
         kname = (f"k_inner_apply_tma<{shape}>" if last["apply_staged"]
@@ -351,6 +353,7 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kname), "kernel": kname,
                 "bytes_per_launch": per_px * p.n, "avg_launch_ms": avg_ms,
+                "launches_timed": n_ap, "launches_issued": sum(i["n_update"] for i in infos),
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
 
     # ---- end to end through the public API with host buffers --------------------------------

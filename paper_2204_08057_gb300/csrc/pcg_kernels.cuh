@@ -200,7 +200,11 @@ __device__ __forceinline__ void apply_pixel(const OpData& op, const CtaShared<T,
 // (the exact k x k diagonal block of G at the pixel).  It is factored as P = S C C^T S with
 // S = diag(P_jj)^{-1/2} (symmetric scaling first, so that badly scaled mixing columns do not
 // cost precision) and C lower triangular; pivots are kept positive, so the preconditioner is
-// SPD even where rounding makes the scaled block look singular.
+// SPD even where rounding makes the scaled block look singular.  The factor is computed once
+// per handle in FP64 (k_block_setup); the FP64 iteration uses it as is, the FP32 iteration
+// uses the scaling in FP32 and C in FP16 (off-diagonal entries of C lie in [-1, 1], its
+// stored inverted diagonal in [1, 1e3]).  Applying the rounded factor is applying the exact
+// inverse of another SPD matrix close to P, so PCG stays a valid PCG.
 template <int K, typename T>
 struct BlockChol {
   T s[K];                // scaling
@@ -237,42 +241,6 @@ __device__ __forceinline__ void block_chol_factor(T (&P)[K * (K + 1) / 2], Block
       }
     }
   }
-}
-
-template <int K, int M, typename T, int NV>
-__device__ __forceinline__ void block_chol(const OpData& op, const CtaShared<T, NV>& sh,
-                                           int64_t i, BlockChol<K, T>& f) {
-  const int64_t ld = op.ld;
-  constexpr int MC = M > 0 ? M : 4;
-  const int Mr = M > 0 ? M : op.m;
-  T P[K * (K + 1) / 2];
-#pragma unroll
-  for (int a = 0; a < K * (K + 1) / 2; ++a) P[a] = T(0);
-  for (int c0 = 0; c0 < Mr; c0 += MC) {
-    T dv[MC];
-#pragma unroll
-    for (int t = 0; t < MC; ++t) {
-      const int c = M > 0 ? t : min(c0 + t, Mr - 1);
-      dv[t] = __ldg(OpT<T>::D(op) + c * ld + i);
-      if (M == 0 && c0 + t >= Mr) dv[t] = T(0);
-    }
-#pragma unroll
-    for (int t = 0; t < MC; ++t) {
-      T a[K];
-      load_row<K, T>(sh.A[c0 + t], a);
-#pragma unroll
-      for (int u = 0; u < K; ++u) {
-        const T du = dv[t] * a[u];
-#pragma unroll
-        for (int v = 0; v <= u; ++v) P[u * (u + 1) / 2 + v] += du * a[v];
-      }
-    }
-  }
-  const T dg = __ldg(OpT<T>::diag(op) + i);
-  const T wi = op.has_w ? __ldg(OpT<T>::w(op) + i) : T(1);
-#pragma unroll
-  for (int u = 0; u < K; ++u) P[u * (u + 1) / 2 + u] += sh.tk2[u] * wi + sh.tau[u] * dg;
-  block_chol_factor<K, T>(P, f);
 }
 
 template <int K, typename T>
@@ -351,6 +319,18 @@ __device__ __forceinline__ void load_factor64(const OpData& op, int64_t i,
   for (int a = 0; a < K; ++a) f.s[a] = __ldg(op.fac64 + (size_t)a * ld + i);
 #pragma unroll
   for (int a = 0; a < K * (K + 1) / 2; ++a) f.l[a] = __ldg(op.fac64 + (size_t)(K + a) * ld + i);
+}
+
+// Loads the stored FP32 preconditioner of the pixel: FP32 scaling and FP16 factor.
+template <int K>
+__device__ __forceinline__ void load_factor32(const OpData& op, int64_t i,
+                                              BlockChol<K, float>& f) {
+  const int64_t ld = op.ld;
+#pragma unroll
+  for (int a = 0; a < K; ++a) f.s[a] = __ldg(op.fs32 + (size_t)a * ld + i);
+#pragma unroll
+  for (int a = 0; a < K * (K + 1) / 2; ++a)
+    f.l[a] = __half2float(__ldg(op.fl16 + (size_t)a * ld + i));
 }
 
 // Adds this warp's share of NV sums of column r into the CTA's per-warp accumulators.
@@ -537,7 +517,7 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
       if constexpr (sizeof(T) == 8) {
         load_factor64<K>(op, i, f);
       } else {
-        block_chol<K, M, T, 2>(op, sh, i, f);
+        load_factor32<K>(op, i, f);
       }
     }
     for (int r = 0; r < R; ++r) {
@@ -640,7 +620,6 @@ template <int K, int M, int E, typename T>
 __global__ void __launch_bounds__(256)
 k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, Control* ctl) {
   __shared__ CtaShared<double, 4> sh;     // FP64 operator
-  __shared__ CtaShared<T, 1> shT;         // inner-type preconditioner data
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
@@ -657,7 +636,6 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
     sh.act[r] = act;
   }
   stage_operator<double, 4>(op, K, sh);
-  stage_operator<T, 1>(op, K, shT);
   zero_wacc<double, 4>(sh, R);
   if (!__syncthreads_or(act)) return;
 
@@ -672,7 +650,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
       if constexpr (sizeof(T) == 8) {
         load_factor64<K>(op, i, f);
       } else {
-        block_chol<K, M, T, 1>(op, shT, i, f);
+        load_factor32<K>(op, i, f);
       }
     }
     for (int r = 0; r < R; ++r) {

@@ -97,11 +97,16 @@ struct ApplyLayout {
   static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
 };
 
+// Update stage: d, p, r, q (4K float rows), the preconditioner scaling (K float rows) and its
+// FP16 factor (K(K+1)/2 half rows, packed two per float row).
 template <int K, int M>
 struct UpdateLayout {
-  static constexpr int Dv = 0, P = K, R = 2 * K, Q = 3 * K, D = 4 * K, DIAG = 4 * K + M;
-  static constexpr int ROWS = 4 * K + M + 1;
-  static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
+  static constexpr int Dv = 0, P = K, R = 2 * K, Q = 3 * K, S = 4 * K, L16 = 5 * K;
+  static constexpr int NB = K * (K + 1) / 2;
+  static constexpr int FLOAT_ROWS = 5 * K;
+  static constexpr int STAGE_BYTES = FLOAT_ROWS * TILE_PX * 4 + NB * TILE_PX * 2;
+  static constexpr int COPIES = 5 * K + NB;
+  static constexpr int NOPREC_COPIES = 4 * K;
 };
 
 // On an expired wait: flag the error, drain this CTA's outstanding copies (bounded) and
@@ -299,7 +304,7 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
                    Control* ctl) {
   using L = UpdateLayout<K, M>;
   extern __shared__ __align__(128) unsigned char dsm[];
-  __shared__ CtaShared<float, 2> sh;
+  __shared__ CtaShared<float, 2> sh;  // (mixing rows unused here: the factor is stored)
   __shared__ __align__(8) uint64_t bars[NSTAGE];
   __shared__ int s_cols[RMAX];
   __shared__ int s_nact;
@@ -347,22 +352,29 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
     const int64_t base = (int64_t)tile * TILE_PX;
     float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
     const uint32_t rowb = TILE_PX * 4;
-    const int nrows = prec ? L::ROWS : 4 * K;
+    const int ncopies = prec ? L::COPIES : L::NOPREC_COPIES;
+    const uint32_t bytes = prec ? (uint32_t)L::STAGE_BYTES : (uint32_t)(4 * K * rowb);
     if (lane == 0) {
       fence_proxy_async();
-      mbar_expect_tx(&bars[st], (uint32_t)nrows * rowb);
+      mbar_expect_tx(&bars[st], bytes);
     }
     __syncwarp();
     const size_t voff = (size_t)r * K * ld;
-    for (int q = lane; q < nrows; q += 32) {
-      const float* src;
-      if (q < K) src = dg_ + voff + (size_t)q * ld + base;
-      else if (q < 2 * K) src = pg + voff + (size_t)(q - K) * ld + base;
-      else if (q < 3 * K) src = rg + voff + (size_t)(q - 2 * K) * ld + base;
-      else if (q < 4 * K) src = qg + voff + (size_t)(q - 3 * K) * ld + base;
-      else if (q < L::DIAG) src = op.D32 + (size_t)(q - L::D) * ld + base;
-      else src = op.diag32 + base;
-      bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &bars[st]);
+    __half* stage_l16 = reinterpret_cast<__half*>(stage + (size_t)L::L16 * TILE_PX);
+    for (int q = lane; q < ncopies; q += 32) {
+      if (q < 5 * K) {
+        const float* src;
+        if (q < K) src = dg_ + voff + (size_t)q * ld + base;
+        else if (q < 2 * K) src = pg + voff + (size_t)(q - K) * ld + base;
+        else if (q < 3 * K) src = rg + voff + (size_t)(q - 2 * K) * ld + base;
+        else if (q < 4 * K) src = qg + voff + (size_t)(q - 3 * K) * ld + base;
+        else src = op.fs32 + (size_t)(q - 4 * K) * ld + base;
+        bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &bars[st]);
+      } else {
+        const int a = q - 5 * K;
+        bulk_load(stage_l16 + (size_t)a * TILE_PX, op.fl16 + (size_t)a * ld + base,
+                  TILE_PX * 2, &bars[st]);
+      }
     }
   };
 
@@ -381,26 +393,11 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
     const int64_t i = (int64_t)tile * TILE_PX + t;
     const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
     if (prec && tile != last_tile) {
-      // P = diag(tau_j (kappa_j^2 + L_ii)) + sum_c d_c a_c a_c^T from the staged rows
-      float P[K * (K + 1) / 2];
+      const __half* sl16 = reinterpret_cast<const __half*>(stage + (size_t)L::L16 * TILE_PX);
 #pragma unroll
-      for (int a = 0; a < K * (K + 1) / 2; ++a) P[a] = 0.f;
+      for (int x = 0; x < K; ++x) f.s[x] = stage[(L::S + x) * TILE_PX + t];
 #pragma unroll
-      for (int c = 0; c < M; ++c) {
-        const float d = stage[(L::D + c) * TILE_PX + t];
-        float a[K];
-        load_row<K, float>(sh.A[c], a);
-#pragma unroll
-        for (int x = 0; x < K; ++x) {
-          const float dx = d * a[x];
-#pragma unroll
-          for (int y = 0; y <= x; ++y) P[x * (x + 1) / 2 + y] += dx * a[y];
-        }
-      }
-      const float dgl = stage[L::DIAG * TILE_PX + t];
-#pragma unroll
-      for (int x = 0; x < K; ++x) P[x * (x + 1) / 2 + x] += sh.tk2[x] + sh.tau[x] * dgl;
-      block_chol_factor<K, float>(P, f);
+      for (int x = 0; x < L::NB; ++x) f.l[x] = __half2float(sl16[x * TILE_PX + t]);
       last_tile = tile;
     }
     const float alpha = sh.sc[r];

@@ -134,6 +134,8 @@ struct sylv_ctx {
   double* w64 = nullptr;
   double* blk64 = nullptr;
   double* fac64 = nullptr;
+  float* fs32 = nullptr;
+  __half* fl16 = nullptr;
   std::unique_ptr<Plan> plan[2];  // single-system plans, [inner_double]
   double* lam = nullptr;
   size_t lam_bytes = 0;
@@ -830,6 +832,8 @@ static void free_handle(sylv_ctx* h) {
   cudaFree(h->w64);
   cudaFree(h->blk64);
   cudaFree(h->fac64);
+  cudaFree(h->fs32);
+  cudaFree(h->fl16);
   cudaFree(h->lam);
   cudaFree(h->grad_ws);
   delete h;
@@ -982,11 +986,17 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   if ((e = dalloc(&h->blk64, nb * ld * sizeof(double))) != cudaSuccess ||
       (e = dalloc(&h->fac64, (nb + p->k) * ld * sizeof(double))) != cudaSuccess ||
       (e = cudaMemsetAsync(h->blk64, 0, nb * ld * sizeof(double), s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(h->fac64, 0, (nb + p->k) * ld * sizeof(double), s)) != cudaSuccess)
+      (e = cudaMemsetAsync(h->fac64, 0, (nb + p->k) * ld * sizeof(double), s)) != cudaSuccess ||
+      (e = dalloc(&h->fs32, (size_t)p->k * ld * sizeof(float))) != cudaSuccess ||
+      (e = dalloc(&h->fl16, nb * ld * sizeof(__half))) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->fs32, 0, (size_t)p->k * ld * sizeof(float), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->fl16, 0, nb * ld * sizeof(__half), s)) != cudaSuccess)
     return bail(cuda_fail(e, "cudaMalloc (pixel blocks)"));
   op.blk64 = h->blk64;
   op.fac64 = h->fac64;
-  if ((e = launch_block_setup(op, h->blk64, h->fac64, s)) != cudaSuccess ||
+  op.fs32 = h->fs32;
+  op.fl16 = h->fl16;
+  if ((e = launch_block_setup(op, h->blk64, h->fac64, h->fs32, h->fl16, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return bail(cuda_fail(e, "pixel-block set-up"));
   cudaFree(dflags);

@@ -111,7 +111,9 @@ __global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restric
 // Pixel blocks P_i (FP64) and their scaled Cholesky factors, once per handle.
 template <int K>
 __global__ void __launch_bounds__(256) k_block_setup(OpData op, double* __restrict__ blk,
-                                                     double* __restrict__ fac) {
+                                                     double* __restrict__ fac,
+                                                     float* __restrict__ fs32,
+                                                     __half* __restrict__ fl16) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= op.n) return;
   const int64_t ld = op.ld;
@@ -136,9 +138,15 @@ __global__ void __launch_bounds__(256) k_block_setup(OpData op, double* __restri
   BlockChol<K, double> f;
   block_chol_factor<K, double>(P, f);
 #pragma unroll
-  for (int a = 0; a < K; ++a) fac[(size_t)a * ld + i] = f.s[a];
+  for (int a = 0; a < K; ++a) {
+    fac[(size_t)a * ld + i] = f.s[a];
+    fs32[(size_t)a * ld + i] = (float)f.s[a];
+  }
 #pragma unroll
-  for (int a = 0; a < K * (K + 1) / 2; ++a) fac[(size_t)(K + a) * ld + i] = f.l[a];
+  for (int a = 0; a < K * (K + 1) / 2; ++a) {
+    fac[(size_t)(K + a) * ld + i] = f.l[a];
+    fl16[(size_t)a * ld + i] = __double2half(f.l[a]);
+  }
 }
 
 // Stand-alone operator apply Y = G X (eq. block-vector-mapping-matvec with Algorithm 1);
@@ -298,9 +306,10 @@ cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, cudaStream_t s) {
+cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, float* fs32,
+                               __half* fl16, cudaStream_t s) {
   const int nb = blocks_for(op.n, 256);
-#define CALL(K) k_block_setup<K><<<nb, 256, 0, s>>>(op, blk64, fac64)
+#define CALL(K) k_block_setup<K><<<nb, 256, 0, s>>>(op, blk64, fac64, fs32, fl16)
   SYLV_DISPATCH_K(op.k, CALL)
 #undef CALL
   return cudaGetLastError();

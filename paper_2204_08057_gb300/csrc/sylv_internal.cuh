@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "sylv.h"
@@ -73,6 +74,9 @@ struct OpData {
   const double* blk64;       // K(K+1)/2 x ld: packed lower triangle of the pixel block
                              // P_i = diag_j(tau_j (kappa_j^2 w_i + L_ii)) + sum_c d_ci a_c a_c^T
   const double* fac64;       // (K + K(K+1)/2) x ld: scaling and factor of P_i (block_chol)
+  const float* fs32;         // K x ld: the scaling of that factor in FP32
+  const __half* fl16;        // K(K+1)/2 x ld: its triangular factor in FP16 (the FP32 inner
+                             // preconditioner; entries lie in [-1, 1e3], see block_chol_factor)
   float A32[MMAX * KMAX];    // A[c * k + j]
   double A64[MMAX * KMAX];
   float tau32[KMAX];
@@ -157,7 +161,8 @@ cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int
                                  int64_t ld_dst, float* dst32, double* dst64, int positive,
                                  unsigned int* flags, cudaStream_t s);
 cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s);
-cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, cudaStream_t s);
+cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, float* fs32,
+                               __half* fl16, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s);
 cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, const double* Y,
