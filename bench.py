@@ -110,8 +110,9 @@ def bytes_inner_apply(k, m, E, s=4):
 
 
 def bytes_inner_update(k, m, s=4):
-    # read d, p, r, q (4k) + D (m) + diagonal (1); write d, r, z (3k)
-    return (7 * k + m + 1) * s
+    # read d, p, r, q (4k) + preconditioner scaling (k, FP32) + factor (k(k+1)/2, FP16);
+    # write d, r, z (3k)
+    return (8 * k) * s + 2 * (k * (k + 1) // 2)
 
 
 def bytes_apply(k, m, E, R=1, s=4):

@@ -26,7 +26,7 @@ cudaError_t apply_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tma::k_inner_apply_tma<K, M, E><<<ncta, TILE_PX, smem, s>>>(d, c, ctl);
+  tma::k_inner_apply_tma<K, M, E><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
   return cudaGetLastError();
 }
 
@@ -41,7 +41,7 @@ cudaError_t update_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tma::k_inner_update_tma<K, M><<<ncta, TILE_PX, smem, s>>>(d, c, ctl);
+  tma::k_inner_update_tma<K, M><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
   return cudaGetLastError();
 }
 
@@ -52,14 +52,14 @@ int tma_occupancy(int kind) {
     cudaFuncSetAttribute(tma::k_inner_apply_tma<K, M, E>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)apply_tma_smem<K, M, E>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_apply_tma<K, M, E>, TILE_PX,
-                                                  apply_tma_smem<K, M, E>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_apply_tma<K, M, E>,
+                                                  tma::WS_THREADS, apply_tma_smem<K, M, E>());
   } else {
     cudaFuncSetAttribute(tma::k_inner_update_tma<K, M>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)update_tma_smem<K, M>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_update_tma<K, M>, TILE_PX,
-                                                  update_tma_smem<K, M>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_update_tma<K, M>,
+                                                  tma::WS_THREADS, update_tma_smem<K, M>());
   }
   return nb < 1 ? 1 : nb;
 }

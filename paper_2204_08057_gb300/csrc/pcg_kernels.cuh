@@ -90,7 +90,7 @@ struct CtaShared {
   T sc[RMAX];        // per-column scalar (beta or alpha)
   int act[RMAX];     // column takes part in this kernel
   int aux[RMAX];     // per-column flag (first iteration)
-  double wacc[RMAX][MAX_BLOCK / 32][NV];  // per-warp partial sums
+  double wacc[RMAX][MAX_WARPS][NV];  // per-warp partial sums
   double red[32 * NV];
   int flag;
 };
@@ -329,8 +329,11 @@ __device__ __forceinline__ void load_factor32(const OpData& op, int64_t i,
 #pragma unroll
   for (int a = 0; a < K; ++a) f.s[a] = __ldg(op.fs32 + (size_t)a * ld + i);
 #pragma unroll
-  for (int a = 0; a < K * (K + 1) / 2; ++a)
-    f.l[a] = __half2float(__ldg(op.fl16 + (size_t)a * ld + i));
+  for (int a = 0; a < K * (K + 1) / 2; a += 2) {
+    const float2 v = __half22float2(op.fl16[(size_t)(a / 2) * ld + i]);
+    f.l[a] = v.x;
+    if (a + 1 < K * (K + 1) / 2) f.l[a + 1] = v.y;
+  }
 }
 
 // Adds this warp's share of NV sums of column r into the CTA's per-warp accumulators.

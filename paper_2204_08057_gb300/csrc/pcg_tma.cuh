@@ -1,16 +1,23 @@
-// FP32 inner-iteration kernels with bulk-copy (TMA) staging of each tile's streams.
+// FP32 inner-iteration kernels with bulk-copy (TMA) staging and warp specialisation.
 //
-// Same arithmetic as k_inner_apply / k_inner_update, restructured for the memory system:
-// every contiguous stream a tile needs (its own rows of z, p, q or d, p, r, q, the noise maps
-// D, the ELL rows of L and its diagonal; TILE_PX values each) is brought into shared memory by
-// cp.async.bulk copies that complete on an mbarrier, two units ahead of the computation.
-// A unit is one (tile, column) pair.  The loads therefore need no registers while in flight,
-// and the only per-thread global loads left are the stencil gathers that fall outside the
-// tile (the neighbours one image row away); gathers inside the tile read the staged rows.
+// Same arithmetic as k_inner_apply / k_inner_update, restructured for the memory system.
+// A unit is one (tile, column) pair; every contiguous stream a unit needs (its rows of z, p, q
+// or d, p, r, q, the noise maps D, the ELL rows of L and its diagonal, or the stored
+// preconditioner factor; TILE_PX values each) is brought into shared memory by cp.async.bulk
+// copies.  One producer warp issues the copies of unit u into stage u % NSTAGE once the
+// consumers have released that stage (an "empty" mbarrier with one arrival per consumer
+// warp), and the copies complete on the stage's "full" mbarrier.  Eight consumer warps (one
+// pixel per thread) wait only on "full", compute, and release the stage: there is no
+// CTA-wide barrier per unit, so warps drift independently and the copies stay in flight.
+// The loads need no registers while in flight; the only per-thread global loads left are the
+// stencil gathers that fall outside the tile (neighbours one image row away).
 //
-// Waits on an mbarrier are bounded (about a second of SM clock); when one expires the CTA
-// records SYLV_E_TIMEOUT in Control::error, drains its own copies (again bounded) and leaves
-// without publishing partial sums, so the host sees the error at its next poll.
+// Units run column by column (all tiles of one right-hand side, then the next), so dot
+// products accumulate in registers and are folded into the per-warp sums once per column.
+//
+// Every mbarrier wait is bounded (about a second of SM clock).  When one expires the warp
+// stops, the CTA records SYLV_E_TIMEOUT in Control::error, thread 0 waits (bounded) for the
+// copies still in flight, and the CTA leaves without publishing partial sums.
 #pragma once
 
 #include "pcg_kernels.cuh"
@@ -73,22 +80,82 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Units of a CTA: its tiles (slot, slot + nslots, ...) times its active columns.
+// Units of a CTA: its tiles (slot, slot + nslots, ...) for each of its active columns, in
+// column-major order.
 struct Units {
-  int ntl;     // tiles of this CTA
-  int nact;    // active columns
-  int n;       // units
+  int ntl;   // tiles of this CTA
+  int n;     // units = ntl * active columns
 };
 
 __device__ __forceinline__ Units count_units(const SysDesc& sd, int slot, int nact) {
   Units u;
   u.ntl = slot < sd.ntiles ? (sd.ntiles - slot + sd.nslots - 1) / sd.nslots : 0;
-  u.nact = nact;
   u.n = u.ntl * nact;
   return u;
 }
 
-// Shared-memory stage layouts (rows of TILE_PX entries of 4 bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+constexpr int NCONS = TILE_PX / 32;     // consumer warps
+constexpr int WS_THREADS = TILE_PX + 32;
+
+// Shared state of a warp-specialised CTA.
+struct PipeShared {
+  uint64_t full[NSTAGE];
+  uint64_t empty[NSTAGE];
+  int cols[RMAX];
+  int nact;
+  int bad;
+  int issued;
+};
+
+__device__ __forceinline__ void pipe_init(PipeShared& ps) {
+  for (int s = 0; s < NSTAGE; ++s) {
+    mbar_init(&ps.full[s], 1);
+    mbar_init(&ps.empty[s], NCONS);
+  }
+  ps.bad = 0;
+  ps.issued = 0;
+  fence_mbar_init();
+}
+
+// Producer loop: waits for stage release, then issues unit u with issue(u, stage).
+template <typename Issue>
+__device__ __forceinline__ void producer_loop(PipeShared& ps, int nunits, Issue&& issue) {
+  const int lane = threadIdx.x & 31;
+  for (int u = 0; u < nunits; ++u) {
+    const int st = u % NSTAGE;
+    if (u >= NSTAGE) {
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NSTAGE) - 1) & 1);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || ps.bad) {
+        if (lane == 0) ps.bad = 1;
+        break;
+      }
+    }
+    issue(u, st);
+    if (lane == 0) ps.issued = u + 1;
+  }
+}
+
+// After both roles are done: on a recorded timeout, flag it, wait (bounded) for the copies
+// still in flight and report true (the caller leaves without partial sums).
+__device__ __forceinline__ bool pipe_failed(PipeShared& ps, int consumed, Control* ctl) {
+  __syncthreads();
+  if (!ps.bad) return false;
+  if (threadIdx.x == 0) {
+    atomicOr(&ctl->error, 1u);
+    for (int u = consumed; u < ps.issued; ++u)
+      mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+  }
+  __syncthreads();
+  return true;
+}
+
+// Stage layouts.  Rows hold TILE_PX entries of 4 bytes (FP16 factor rows hold half2 pairs).
 template <int K, int M, int E>
 struct ApplyLayout {
   static constexpr int Z = 0, P = K, Q = 2 * K, D = 3 * K, VAL = 3 * K + M,
@@ -97,46 +164,26 @@ struct ApplyLayout {
   static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
 };
 
-// Update stage: d, p, r, q (4K float rows), the preconditioner scaling (K float rows) and its
-// FP16 factor (K(K+1)/2 half rows, packed two per float row).
 template <int K, int M>
 struct UpdateLayout {
+  static constexpr int NB = K * (K + 1) / 2, NB2 = (NB + 1) / 2;
   static constexpr int Dv = 0, P = K, R = 2 * K, Q = 3 * K, S = 4 * K, L16 = 5 * K;
-  static constexpr int NB = K * (K + 1) / 2;
-  static constexpr int FLOAT_ROWS = 5 * K;
-  static constexpr int STAGE_BYTES = FLOAT_ROWS * TILE_PX * 4 + NB * TILE_PX * 2;
-  static constexpr int COPIES = 5 * K + NB;
-  static constexpr int NOPREC_COPIES = 4 * K;
+  static constexpr int ROWS = 5 * K + NB2;
+  static constexpr int NOPREC_ROWS = 4 * K;
+  static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
 };
-
-// On an expired wait: flag the error, drain this CTA's outstanding copies (bounded) and
-// return true (the caller leaves).
-__device__ __forceinline__ bool handle_timeout(bool ok, uint64_t* bars, int next_unit,
-                                               int nunits, Control* ctl) {
-  const bool bad = __syncthreads_or(!ok);
-  if (!bad) return false;
-  if (threadIdx.x == 0) {
-    atomicOr(&ctl->error, 1u);
-    for (int u = next_unit; u < nunits && u < next_unit + NSTAGE; ++u)
-      mbar_wait_bounded(&bars[u % NSTAGE], (u / NSTAGE) & 1);
-  }
-  __syncthreads();
-  return true;
-}
 
 // ---------------------------------------------------------------------------------------------
 // inner_apply (staged): p = z + beta p, q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
 template <int K, int M, int E>
-__global__ void __launch_bounds__(TILE_PX, 2)
+__global__ void __launch_bounds__(WS_THREADS, 2)
 k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
                   Control* ctl) {
   using L = ApplyLayout<K, M, E>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 1> sh;
-  __shared__ __align__(8) uint64_t bars[NSTAGE];
-  __shared__ int s_cols[RMAX];
-  __shared__ int s_nact;
+  __shared__ __align__(8) PipeShared ps;
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
@@ -158,119 +205,125 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   if (threadIdx.x == 0) {
     int na = 0;
     for (int r = 0; r < R; ++r)
-      if (sh.act[r]) s_cols[na++] = r;
-    s_nact = na;
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
-    fence_mbar_init();
+      if (sh.act[r]) ps.cols[na++] = r;
+    ps.nact = na;
+    pipe_init(ps);
   }
   if (!__syncthreads_or(act)) return;
 
   const int64_t ld = op.ld, n = op.n;
-  const Units U = count_units(sd, cr.slot, s_nact);
+  const Units U = count_units(sd, cr.slot, ps.nact);
   const float* zg = (const float*)sd.vz;
   float* pg = (float*)sd.vp;
   float* qg = (float*)sd.vq;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int consumed = 0;
 
-  // warp 0 issues the copies of unit u into stage u % NSTAGE
-  auto issue = [&](int u) {
-    const int st = u % NSTAGE;
-    const int tile = cr.slot + (u / U.nact) * sd.nslots;
-    const int r = s_cols[u % U.nact];
-    const bool first = sh.aux[r] != 0;
-    const int64_t base = (int64_t)tile * TILE_PX;
-    float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
-    const uint32_t rowb = TILE_PX * 4;
-    const int nrows = first ? L::ROWS - 2 * K : L::ROWS;
-    if (lane == 0) {
-      fence_proxy_async();
-      mbar_expect_tx(&bars[st], (uint32_t)nrows * rowb);
-    }
-    __syncwarp();
-    const size_t voff = (size_t)r * K * ld;
-    for (int q = lane; q < L::ROWS; q += 32) {
-      const void* src = nullptr;
-      if (q < K) src = zg + voff + (size_t)q * ld + base;
-      else if (q < 2 * K) src = first ? nullptr : pg + voff + (size_t)(q - K) * ld + base;
-      else if (q < 3 * K) src = first ? nullptr : qg + voff + (size_t)(q - 2 * K) * ld + base;
-      else if (q < L::VAL) src = op.D32 + (size_t)(q - L::D) * ld + base;
-      else if (q < L::DIAG) src = op.ell_val32 + (size_t)(q - L::VAL) * ld + base;
-      else if (q == L::DIAG) src = op.diag32 + base;
-      else src = op.ell_col + (size_t)(q - L::COL) * ld + base;
-      if (src) bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &bars[st]);
-    }
-  };
-
-  if (warp == 0) {
-    for (int u = 0; u < NSTAGE && u < U.n; ++u) issue(u);
-  }
-  for (int u = 0; u < U.n; ++u) {
-    const int st = u % NSTAGE;
-    const bool ok = mbar_wait_bounded(&bars[st], (u / NSTAGE) & 1);
-    if (handle_timeout(ok, bars, u, U.n, ctl)) return;
-    const int tile = cr.slot + (u / U.nact) * sd.nslots;
-    const int r = s_cols[u % U.nact];
-    const int64_t base = (int64_t)tile * TILE_PX;
+  if (warp == NCONS) {
+    producer_loop(ps, U.n, [&](int u, int st) {
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int r = ps.cols[u / U.ntl];
+      const bool first = sh.aux[r] != 0;
+      const int64_t base = (int64_t)tile * TILE_PX;
+      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+      const uint32_t rowb = TILE_PX * 4;
+      const int nrows = first ? L::ROWS - 2 * K : L::ROWS;
+      if (lane == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
+      }
+      __syncwarp();
+      const size_t voff = (size_t)r * K * ld;
+      for (int q = lane; q < L::ROWS; q += 32) {
+        const void* src = nullptr;
+        if (q < K) src = zg + voff + (size_t)q * ld + base;
+        else if (q < 2 * K) src = first ? nullptr : pg + voff + (size_t)(q - K) * ld + base;
+        else if (q < 3 * K) src = first ? nullptr : qg + voff + (size_t)(q - 2 * K) * ld + base;
+        else if (q < L::VAL) src = op.D32 + (size_t)(q - L::D) * ld + base;
+        else if (q < L::DIAG) src = op.ell_val32 + (size_t)(q - L::VAL) * ld + base;
+        else if (q == L::DIAG) src = op.diag32 + base;
+        else src = op.ell_col + (size_t)(q - L::COL) * ld + base;
+        if (src) bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
+      }
+    });
+  } else {
     const int t = threadIdx.x;
-    const int64_t i = base + t;
-    const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
-    const int32_t* scol = reinterpret_cast<const int32_t*>(stage + (size_t)L::COL * TILE_PX);
-    const size_t voff = (size_t)r * K * ld;
-    float zi[K], lap[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) zi[j] = stage[(L::Z + j) * TILE_PX + t];
-    const float dg = stage[L::DIAG * TILE_PX + t];
-#pragma unroll
-    for (int j = 0; j < K; ++j) lap[j] = dg * zi[j];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int64_t c = scol[e * TILE_PX + t];
-      const float v = stage[(L::VAL + e) * TILE_PX + t];
-      const uint32_t loc = (uint32_t)(c - base);
-      if (loc < (uint32_t)TILE_PX) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) lap[j] += v * stage[(L::Z + j) * TILE_PX + loc];
-      } else {
-#pragma unroll
-        for (int j = 0; j < K; ++j) lap[j] += v * __ldg(zg + voff + (size_t)j * ld + c);
+    double acc = 0.0;
+    for (int u = 0; u < U.n; ++u) {
+      const int st = u % NSTAGE;
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+        ps.bad = 1;
+        break;
       }
-    }
-    float w[K];
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int r = ps.cols[u / U.ntl];
+      const int64_t base = (int64_t)tile * TILE_PX;
+      const int64_t i = base + t;
+      const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
+      const int32_t* scol = reinterpret_cast<const int32_t*>(stage + (size_t)L::COL * TILE_PX);
+      const size_t voff = (size_t)r * K * ld;
+      float zi[K], lap[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) w[j] = sh.tk2[j] * zi[j] + sh.tau[j] * lap[j];
+      for (int j = 0; j < K; ++j) zi[j] = stage[(L::Z + j) * TILE_PX + t];
+      const float dg = stage[L::DIAG * TILE_PX + t];
 #pragma unroll
-    for (int c = 0; c < M; ++c) {
-      const float d = stage[(L::D + c) * TILE_PX + t];
-      float a[K];
-      load_row<K, float>(sh.A[c], a);
-      float s = 0.f;
+      for (int j = 0; j < K; ++j) lap[j] = dg * zi[j];
 #pragma unroll
-      for (int j = 0; j < K; ++j) s += a[j] * zi[j];
-      s *= d;
+      for (int e = 0; e < E; ++e) {
+        const int64_t c = scol[e * TILE_PX + t];
+        const float v = stage[(L::VAL + e) * TILE_PX + t];
+        const uint32_t loc = (uint32_t)(c - base);
+        if (loc < (uint32_t)TILE_PX) {
 #pragma unroll
-      for (int j = 0; j < K; ++j) w[j] += a[j] * s;
-    }
-    const bool first = sh.aux[r] != 0;
-    const float beta = sh.sc[r];
-    float pq = 0.f;
-    if (i < n) {
+          for (int j = 0; j < K; ++j) lap[j] += v * stage[(L::Z + j) * TILE_PX + loc];
+        } else {
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        float pj = zi[j], qj = w[j];
-        if (!first) {
-          pj += beta * stage[(L::P + j) * TILE_PX + t];
-          qj += beta * stage[(L::Q + j) * TILE_PX + t];
+          for (int j = 0; j < K; ++j) lap[j] += v * __ldg(zg + voff + (size_t)j * ld + c);
         }
-        pg[voff + (size_t)j * ld + i] = pj;
-        qg[voff + (size_t)j * ld + i] = qj;
-        pq += pj * qj;
+      }
+      float w[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) w[j] = sh.tk2[j] * zi[j] + sh.tau[j] * lap[j];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        const float d = stage[(L::D + c) * TILE_PX + t];
+        float a[K];
+        load_row<K, float>(sh.A[c], a);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) s += a[j] * zi[j];
+        s *= d;
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j] += a[j] * s;
+      }
+      const bool first = sh.aux[r] != 0;
+      const float beta = sh.sc[r];
+      float pq = 0.f;
+      if (i < n) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          float pj = zi[j], qj = w[j];
+          if (!first) {
+            pj += beta * stage[(L::P + j) * TILE_PX + t];
+            qj += beta * stage[(L::Q + j) * TILE_PX + t];
+          }
+          pg[voff + (size_t)j * ld + i] = pj;
+          qg[voff + (size_t)j * ld + i] = qj;
+          pq += pj * qj;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ps.empty[st]);
+      consumed = u + 1;
+      acc += double(pq);
+      if ((u + 1) % U.ntl == 0) {   // last tile of this column
+        const double v1[1] = {acc};
+        warp_accumulate<float, 1>(sh, r, v1);
+        acc = 0.0;
       }
     }
-    const double v1[1] = {double(pq)};
-    warp_accumulate<float, 1>(sh, r, v1);
-    __syncthreads();  // stage st fully read
-    if (warp == 0 && u + NSTAGE < U.n) issue(u + NSTAGE);
   }
+  if (pipe_failed(ps, consumed, ctl)) return;
   double tot[RMAX][1];
   if (!finish_partials<float, 1>(sd, cr.slot, sh, R, tot)) return;
   if (threadIdx.x == 0) {
@@ -299,15 +352,13 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
 // inner_update (staged): d += alpha p, r -= alpha q, z = P^{-1} r, partial r . z and r . r
 // ---------------------------------------------------------------------------------------------
 template <int K, int M>
-__global__ void __launch_bounds__(TILE_PX, 2)
+__global__ void __launch_bounds__(WS_THREADS, 2)
 k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
                    Control* ctl) {
   using L = UpdateLayout<K, M>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 2> sh;  // (mixing rows unused here: the factor is stored)
-  __shared__ __align__(8) uint64_t bars[NSTAGE];
-  __shared__ int s_cols[RMAX];
-  __shared__ int s_nact;
+  __shared__ __align__(8) PipeShared ps;
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
@@ -323,113 +374,113 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
     }
     sh.act[r] = act;
   }
-  stage_operator<float, 2>(op, K, sh);
   zero_wacc<float, 2>(sh, R);
   if (threadIdx.x == 0) {
     int na = 0;
     for (int r = 0; r < R; ++r)
-      if (sh.act[r]) s_cols[na++] = r;
-    s_nact = na;
-    for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
-    fence_mbar_init();
+      if (sh.act[r]) ps.cols[na++] = r;
+    ps.nact = na;
+    pipe_init(ps);
   }
   if (!__syncthreads_or(act)) return;
 
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
-  const Units U = count_units(sd, cr.slot, s_nact);
-  float* dg_ = (float*)sd.vd;
+  const Units U = count_units(sd, cr.slot, ps.nact);
+  float* dgl = (float*)sd.vd;
   float* rg = (float*)sd.vr;
   float* zg = (float*)sd.vz;
   const float* pg = (const float*)sd.vp;
   const float* qg = (const float*)sd.vq;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int consumed = 0;
 
-  auto issue = [&](int u) {
-    const int st = u % NSTAGE;
-    const int tile = cr.slot + (u / U.nact) * sd.nslots;
-    const int r = s_cols[u % U.nact];
-    const int64_t base = (int64_t)tile * TILE_PX;
-    float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
-    const uint32_t rowb = TILE_PX * 4;
-    const int ncopies = prec ? L::COPIES : L::NOPREC_COPIES;
-    const uint32_t bytes = prec ? (uint32_t)L::STAGE_BYTES : (uint32_t)(4 * K * rowb);
-    if (lane == 0) {
-      fence_proxy_async();
-      mbar_expect_tx(&bars[st], bytes);
-    }
-    __syncwarp();
-    const size_t voff = (size_t)r * K * ld;
-    __half* stage_l16 = reinterpret_cast<__half*>(stage + (size_t)L::L16 * TILE_PX);
-    for (int q = lane; q < ncopies; q += 32) {
-      if (q < 5 * K) {
-        const float* src;
-        if (q < K) src = dg_ + voff + (size_t)q * ld + base;
+  if (warp == NCONS) {
+    producer_loop(ps, U.n, [&](int u, int st) {
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int r = ps.cols[u / U.ntl];
+      const int64_t base = (int64_t)tile * TILE_PX;
+      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+      const uint32_t rowb = TILE_PX * 4;
+      const int nrows = prec ? L::ROWS : L::NOPREC_ROWS;
+      if (lane == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
+      }
+      __syncwarp();
+      const size_t voff = (size_t)r * K * ld;
+      for (int q = lane; q < nrows; q += 32) {
+        const void* src;
+        if (q < K) src = dgl + voff + (size_t)q * ld + base;
         else if (q < 2 * K) src = pg + voff + (size_t)(q - K) * ld + base;
         else if (q < 3 * K) src = rg + voff + (size_t)(q - 2 * K) * ld + base;
         else if (q < 4 * K) src = qg + voff + (size_t)(q - 3 * K) * ld + base;
-        else src = op.fs32 + (size_t)(q - 4 * K) * ld + base;
-        bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &bars[st]);
-      } else {
-        const int a = q - 5 * K;
-        bulk_load(stage_l16 + (size_t)a * TILE_PX, op.fl16 + (size_t)a * ld + base,
-                  TILE_PX * 2, &bars[st]);
+        else if (q < 5 * K) src = op.fs32 + (size_t)(q - 4 * K) * ld + base;
+        else src = op.fl16 + (size_t)(q - 5 * K) * ld + base;
+        bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
       }
-    }
-  };
-
-  if (warp == 0) {
-    for (int u = 0; u < NSTAGE && u < U.n; ++u) issue(u);
-  }
-  int last_tile = -1;
-  BlockChol<K, float> f;
-  for (int u = 0; u < U.n; ++u) {
-    const int st = u % NSTAGE;
-    const bool ok = mbar_wait_bounded(&bars[st], (u / NSTAGE) & 1);
-    if (handle_timeout(ok, bars, u, U.n, ctl)) return;
-    const int tile = cr.slot + (u / U.nact) * sd.nslots;
-    const int r = s_cols[u % U.nact];
+    });
+  } else {
     const int t = threadIdx.x;
-    const int64_t i = (int64_t)tile * TILE_PX + t;
-    const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
-    if (prec && tile != last_tile) {
-      const __half* sl16 = reinterpret_cast<const __half*>(stage + (size_t)L::L16 * TILE_PX);
-#pragma unroll
-      for (int x = 0; x < K; ++x) f.s[x] = stage[(L::S + x) * TILE_PX + t];
-#pragma unroll
-      for (int x = 0; x < L::NB; ++x) f.l[x] = __half2float(sl16[x * TILE_PX + t]);
-      last_tile = tile;
-    }
-    const float alpha = sh.sc[r];
-    const size_t voff = (size_t)r * K * ld;
-    float rz = 0.f, rr = 0.f;
-    if (i < n) {
-      float ri[K], zi[K];
+    double acc_rz = 0.0, acc_rr = 0.0;
+    for (int u = 0; u < U.n; ++u) {
+      const int st = u % NSTAGE;
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+        ps.bad = 1;
+        break;
+      }
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int r = ps.cols[u / U.ntl];
+      const int64_t i = (int64_t)tile * TILE_PX + t;
+      const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
+      const float alpha = sh.sc[r];
+      const size_t voff = (size_t)r * K * ld;
+      float ri[K], zi[K], dn[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        const float dn = stage[(L::Dv + j) * TILE_PX + t] + alpha * stage[(L::P + j) * TILE_PX + t];
+        dn[j] = stage[(L::Dv + j) * TILE_PX + t] + alpha * stage[(L::P + j) * TILE_PX + t];
         ri[j] = stage[(L::R + j) * TILE_PX + t] - alpha * stage[(L::Q + j) * TILE_PX + t];
-        dg_[voff + (size_t)j * ld + i] = dn;
-        rg[voff + (size_t)j * ld + i] = ri[j];
       }
       if (prec) {
+        BlockChol<K, float> f;
+        const __half2* sl = reinterpret_cast<const __half2*>(stage + (size_t)L::L16 * TILE_PX);
+#pragma unroll
+        for (int x = 0; x < K; ++x) f.s[x] = stage[(L::S + x) * TILE_PX + t];
+#pragma unroll
+        for (int x = 0; x < L::NB; x += 2) {
+          const float2 v = __half22float2(sl[(x / 2) * TILE_PX + t]);
+          f.l[x] = v.x;
+          if (x + 1 < L::NB) f.l[x + 1] = v.y;
+        }
         block_solve<K, float>(f, ri, zi);
       } else {
 #pragma unroll
         for (int j = 0; j < K; ++j) zi[j] = ri[j];
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ps.empty[st]);   // stage fully read
+      consumed = u + 1;
+      float rz = 0.f, rr = 0.f;
+      if (i < n) {
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        zg[voff + (size_t)j * ld + i] = zi[j];
-        rz += ri[j] * zi[j];
-        rr += ri[j] * ri[j];
+        for (int j = 0; j < K; ++j) {
+          dgl[voff + (size_t)j * ld + i] = dn[j];
+          rg[voff + (size_t)j * ld + i] = ri[j];
+          zg[voff + (size_t)j * ld + i] = zi[j];
+          rz += ri[j] * zi[j];
+          rr += ri[j] * ri[j];
+        }
+      }
+      acc_rz += double(rz);
+      acc_rr += double(rr);
+      if ((u + 1) % U.ntl == 0) {
+        const double v2[2] = {acc_rz, acc_rr};
+        warp_accumulate<float, 2>(sh, r, v2);
+        acc_rz = acc_rr = 0.0;
       }
     }
-    const double v2[2] = {double(rz), double(rr)};
-    warp_accumulate<float, 2>(sh, r, v2);
-    __syncthreads();
-    if (warp == 0 && u + NSTAGE < U.n) issue(u + NSTAGE);
   }
+  if (pipe_failed(ps, consumed, ctl)) return;
   double tot[RMAX][2];
   if (!finish_partials<float, 2>(sd, cr.slot, sh, R, tot)) return;
   if (threadIdx.x == 0) {

@@ -135,7 +135,7 @@ struct sylv_ctx {
   double* blk64 = nullptr;
   double* fac64 = nullptr;
   float* fs32 = nullptr;
-  __half* fl16 = nullptr;
+  __half2* fl16 = nullptr;
   std::unique_ptr<Plan> plan[2];  // single-system plans, [inner_double]
   double* lam = nullptr;
   size_t lam_bytes = 0;
@@ -988,9 +988,10 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
       (e = cudaMemsetAsync(h->blk64, 0, nb * ld * sizeof(double), s)) != cudaSuccess ||
       (e = cudaMemsetAsync(h->fac64, 0, (nb + p->k) * ld * sizeof(double), s)) != cudaSuccess ||
       (e = dalloc(&h->fs32, (size_t)p->k * ld * sizeof(float))) != cudaSuccess ||
-      (e = dalloc(&h->fl16, nb * ld * sizeof(__half))) != cudaSuccess ||
+      (e = dalloc(&h->fl16, ((nb + 1) / 2) * ld * sizeof(__half2))) != cudaSuccess ||
       (e = cudaMemsetAsync(h->fs32, 0, (size_t)p->k * ld * sizeof(float), s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(h->fl16, 0, nb * ld * sizeof(__half), s)) != cudaSuccess)
+      (e = cudaMemsetAsync(h->fl16, 0, ((nb + 1) / 2) * ld * sizeof(__half2), s)) !=
+          cudaSuccess)
     return bail(cuda_fail(e, "cudaMalloc (pixel blocks)"));
   op.blk64 = h->blk64;
   op.fac64 = h->fac64;

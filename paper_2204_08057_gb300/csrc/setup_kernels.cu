@@ -113,7 +113,7 @@ template <int K>
 __global__ void __launch_bounds__(256) k_block_setup(OpData op, double* __restrict__ blk,
                                                      double* __restrict__ fac,
                                                      float* __restrict__ fs32,
-                                                     __half* __restrict__ fl16) {
+                                                     __half2* __restrict__ fl16) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= op.n) return;
   const int64_t ld = op.ld;
@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(256) k_block_setup(OpData op, double* __restri
     fs32[(size_t)a * ld + i] = (float)f.s[a];
   }
 #pragma unroll
-  for (int a = 0; a < K * (K + 1) / 2; ++a) {
-    fac[(size_t)(K + a) * ld + i] = f.l[a];
-    fl16[(size_t)a * ld + i] = __double2half(f.l[a]);
+  for (int a = 0; a < K * (K + 1) / 2; ++a) fac[(size_t)(K + a) * ld + i] = f.l[a];
+#pragma unroll
+  for (int a = 0; a < K * (K + 1) / 2; a += 2) {
+    const double hi = a + 1 < K * (K + 1) / 2 ? f.l[a + 1] : 0.0;
+    fl16[(size_t)(a / 2) * ld + i] = __halves2half2(__double2half(f.l[a]), __double2half(hi));
   }
 }
 
@@ -307,7 +309,7 @@ cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int
 }
 
 cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, float* fs32,
-                               __half* fl16, cudaStream_t s) {
+                               __half2* fl16, cudaStream_t s) {
   const int nb = blocks_for(op.n, 256);
 #define CALL(K) k_block_setup<K><<<nb, 256, 0, s>>>(op, blk64, fac64, fs32, fl16)
   SYLV_DISPATCH_K(op.k, CALL)

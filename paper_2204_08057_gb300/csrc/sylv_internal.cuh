@@ -26,6 +26,7 @@ constexpr int EMAX = SYLV_MAX_DEGREE;
 constexpr int RMAX = SYLV_MAX_RHS;
 constexpr int NPART = 4;          // partial sums per (tile, column)
 constexpr int MAX_BLOCK = 256;
+constexpr int MAX_WARPS = 16;     // warps per CTA, producer warps included
 constexpr int TILE_PX = 256;      // pixels per tile = threads per CTA of the iteration kernels
 
 enum Phase : int {
@@ -75,8 +76,9 @@ struct OpData {
                              // P_i = diag_j(tau_j (kappa_j^2 w_i + L_ii)) + sum_c d_ci a_c a_c^T
   const double* fac64;       // (K + K(K+1)/2) x ld: scaling and factor of P_i (block_chol)
   const float* fs32;         // K x ld: the scaling of that factor in FP32
-  const __half* fl16;        // K(K+1)/2 x ld: its triangular factor in FP16 (the FP32 inner
-                             // preconditioner; entries lie in [-1, 1e3], see block_chol_factor)
+  const __half2* fl16;       // ceil(K(K+1)/2 / 2) x ld: its triangular factor in FP16, two
+                             // entries per pixel and row (entry a in row a/2, lane a%2); the
+                             // FP32 inner preconditioner; entries lie in [-1, 1e3]
   float A32[MMAX * KMAX];    // A[c * k + j]
   double A64[MMAX * KMAX];
   float tau32[KMAX];
@@ -162,7 +164,7 @@ cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int
                                  unsigned int* flags, cudaStream_t s);
 cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s);
 cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, float* fs32,
-                               __half* fl16, cudaStream_t s);
+                               __half2* fl16, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s);
 cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, const double* Y,
