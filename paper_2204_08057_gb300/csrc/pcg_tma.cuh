@@ -177,7 +177,7 @@ struct UpdateLayout {
 // inner_apply (staged): p = z + beta p, q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
 template <int K, int M, int E>
-__global__ void __launch_bounds__(WS_THREADS, 2)
+__global__ void __launch_bounds__(WS_THREADS, 3)
 k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
                   Control* ctl) {
   using L = ApplyLayout<K, M, E>;

@@ -26,7 +26,7 @@ constexpr int EMAX = SYLV_MAX_DEGREE;
 constexpr int RMAX = SYLV_MAX_RHS;
 constexpr int NPART = 4;          // partial sums per (tile, column)
 constexpr int MAX_BLOCK = 256;
-constexpr int MAX_WARPS = 16;     // warps per CTA, producer warps included
+constexpr int MAX_WARPS = 9;      // warps per CTA, producer warp included
 constexpr int TILE_PX = 256;      // pixels per tile = threads per CTA of the iteration kernels
 
 enum Phase : int {

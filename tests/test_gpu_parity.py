@@ -49,6 +49,8 @@ CASES = [
     ("sphere", 16, 17, 8, 16, 0),     # largest k and m of this build
     ("lattice", 12, 30, 4, 7, 64),
     ("sphere", 3, 4, 2, 3, 1),        # smaller than one tile
+    ("sphere", 16, 64, 6, 9, 0),      # whole tiles, aligned rows: staged FP32 apply
+    ("lattice", 32, 32, 4, 7, 0),     # idem, lattice (neighbour windows two tiles away)
 ]
 
 
