@@ -123,6 +123,7 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   ctl.maxit = o.maxit;
   ctl.max_outer = o.max_outer;
   ctl.precond = o.precond;
+  ctl.x0_zero = o.use_x0 ? 0 : 1;
 
   SysDesc sd;
   std::memset(&sd, 0, sizeof sd);

@@ -637,6 +637,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
       act = (ph == PH_START || ph == PH_INNER_DONE);
     }
     sh.act[r] = act;
+    sh.aux[r] = ph;
   }
   stage_operator<double, 4>(op, K, sh);
   zero_wacc<double, 4>(sh, R);
@@ -644,6 +645,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
 
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
+  const bool x0_zero = ctl->x0_zero != 0;
   for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
     const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
     const bool valid = i0 < n;
@@ -667,9 +669,15 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
       T* rv = (T*)sd.vr + off;
       T* z = (T*)sd.vz + off;
       double xi[K], gx[K];
+      if (x0_zero && sh.aux[r] == PH_START) {
+        // X = 0: the residual is B itself (no operator application needed)
 #pragma unroll
-      for (int j = 0; j < K; ++j) xi[j] = X[j * ldu + i];
-      apply_pixel_blk64<K, E, double, 4>(op, sh, X, ldu, i, xi, gx);
+        for (int j = 0; j < K; ++j) gx[j] = 0.0;
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) xi[j] = X[j * ldu + i];
+        apply_pixel_blk64<K, E, double, 4>(op, sh, X, ldu, i, xi, gx);
+      }
       double rr64 = 0.0, bb = 0.0, rz = 0.0, rr = 0.0;
       if (valid) {
         T ri[K], zi[K];

@@ -607,6 +607,7 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   c.maxit = o.maxit;
   c.max_outer = o.max_outer;
   c.precond = o.precond;
+  c.x0_zero = o.use_x0 ? 0 : 1;
   const int iters = o.check_every > 0 ? o.check_every : 16;
   const bool prof = o.profile != 0;
   double ms_apply = 0, ms_update = 0, ms_res = 0;

@@ -118,7 +118,7 @@ struct Control {
   int maxit;
   int max_outer;
   int precond;
-  int pad;
+  int x0_zero;                // X starts at zero: the first residual is B itself
 };
 
 struct CtaRef {
