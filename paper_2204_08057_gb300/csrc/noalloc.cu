@@ -130,7 +130,8 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   sd.op = op;
   sd.R = R;
   sd.ntiles = ntiles;
-  sd.nslots = nslots;
+  sd.nslots[0] = nslots;
+  sd.nslots[1] = nslots;
   sd.B = B;
   sd.X = X;
   unsigned char* vec = base + o_vec;

@@ -351,7 +351,7 @@ __device__ __forceinline__ void warp_accumulate(CtaShared<T, NV>& sh, int r,
 // Writes this CTA's partials, then returns true in the last CTA of the system to arrive, which
 // then holds the fixed-order totals of every active column in sh.red[r * NV + t] (thread 0).
 template <typename T, int NV>
-__device__ __forceinline__ bool finish_partials(const SysDesc& sd, int slot,
+__device__ __forceinline__ bool finish_partials(const SysDesc& sd, int slot, int nslots,
                                                 CtaShared<T, NV>& sh, int R,
                                                 double (&tot)[RMAX][NV]) {
   const int nw = blockDim.x >> 5;
@@ -366,7 +366,7 @@ __device__ __forceinline__ bool finish_partials(const SysDesc& sd, int slot,
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned prev = atomicAdd(sd.counter, 1u);
-    sh.flag = (prev == (unsigned)sd.nslots - 1u) ? 1 : 0;
+    sh.flag = (prev == (unsigned)nslots - 1u) ? 1 : 0;
   }
   __syncthreads();
   if (!sh.flag) return false;
@@ -376,7 +376,7 @@ __device__ __forceinline__ bool finish_partials(const SysDesc& sd, int slot,
     double acc[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) acc[t] = 0.0;
-    for (int sl = threadIdx.x; sl < sd.nslots; sl += blockDim.x) {
+    for (int sl = threadIdx.x; sl < nslots; sl += blockDim.x) {
       const double* p = sd.partial + ((size_t)sl * R + r) * NPART;
 #pragma unroll
       for (int t = 0; t < NV; ++t) acc[t] += __ldcg(p + t);
@@ -420,7 +420,7 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
   if (!__syncthreads_or(act)) return;
 
   const int64_t ld = op.ld, n = op.n;
-  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[0]) {
     const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
@@ -459,7 +459,7 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
     }
   }
   double tot[RMAX][1];
-  if (!finish_partials<T, 1>(sd, cr.slot, sh, R, tot)) return;
+  if (!finish_partials<T, 1>(sd, cr.slot, sd.nslots[0], sh, R, tot)) return;
   if (threadIdx.x == 0) {
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
@@ -511,7 +511,7 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
 
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
-  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[1]) {
     const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
@@ -559,7 +559,7 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
     }
   }
   double tot[RMAX][2];
-  if (!finish_partials<T, 2>(sd, cr.slot, sh, R, tot)) return;
+  if (!finish_partials<T, 2>(sd, cr.slot, sd.nslots[1], sh, R, tot)) return;
   if (threadIdx.x == 0) {
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
@@ -607,7 +607,7 @@ k_update_x(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas) {
     if (sd.st[r].phase != PH_INNER_DONE) continue;
     const T* d = (const T*)sd.vd + (size_t)r * K * ld;
     double* X = sd.X + (size_t)r * K * ldu;
-    for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+    for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[1]) {
       const int64_t i = (int64_t)tile * blockDim.x + threadIdx.x;
       if (i >= n) continue;
 #pragma unroll
@@ -646,7 +646,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
   const bool x0_zero = ctl->x0_zero != 0;
-  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots) {
+  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[1]) {
     const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
@@ -709,7 +709,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
     }
   }
   double tot[RMAX][4];
-  if (!finish_partials<double, 4>(sd, cr.slot, sh, R, tot)) return;
+  if (!finish_partials<double, 4>(sd, cr.slot, sd.nslots[1], sh, R, tot)) return;
   if (threadIdx.x == 0) {
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;

@@ -87,9 +87,9 @@ struct Units {
   int n;     // units = ntl * active columns
 };
 
-__device__ __forceinline__ Units count_units(const SysDesc& sd, int slot, int nact) {
+__device__ __forceinline__ Units count_units(const SysDesc& sd, int slot, int nslots, int nact) {
   Units u;
-  u.ntl = slot < sd.ntiles ? (sd.ntiles - slot + sd.nslots - 1) / sd.nslots : 0;
+  u.ntl = slot < sd.ntiles ? (sd.ntiles - slot + nslots - 1) / nslots : 0;
   u.n = u.ntl * nact;
   return u;
 }
@@ -212,7 +212,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   if (!__syncthreads_or(act)) return;
 
   const int64_t ld = op.ld, n = op.n;
-  const Units U = count_units(sd, cr.slot, ps.nact);
+  const Units U = count_units(sd, cr.slot, sd.nslots[0], ps.nact);
   const float* zg = (const float*)sd.vz;
   float* pg = (float*)sd.vp;
   float* qg = (float*)sd.vq;
@@ -221,7 +221,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
 
   if (warp == NCONS) {
     producer_loop(ps, U.n, [&](int u, int st) {
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots[0];
       const int r = ps.cols[u / U.ntl];
       const bool first = sh.aux[r] != 0;
       const int64_t base = (int64_t)tile * TILE_PX;
@@ -255,7 +255,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
         ps.bad = 1;
         break;
       }
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots[0];
       const int r = ps.cols[u / U.ntl];
       const int64_t base = (int64_t)tile * TILE_PX;
       const int64_t i = base + t;
@@ -325,7 +325,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   }
   if (pipe_failed(ps, consumed, ctl)) return;
   double tot[RMAX][1];
-  if (!finish_partials<float, 1>(sd, cr.slot, sh, R, tot)) return;
+  if (!finish_partials<float, 1>(sd, cr.slot, sd.nslots[0], sh, R, tot)) return;
   if (threadIdx.x == 0) {
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
@@ -386,7 +386,7 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
 
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
-  const Units U = count_units(sd, cr.slot, ps.nact);
+  const Units U = count_units(sd, cr.slot, sd.nslots[1], ps.nact);
   float* dgl = (float*)sd.vd;
   float* rg = (float*)sd.vr;
   float* zg = (float*)sd.vz;
@@ -397,7 +397,7 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
 
   if (warp == NCONS) {
     producer_loop(ps, U.n, [&](int u, int st) {
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots[1];
       const int r = ps.cols[u / U.ntl];
       const int64_t base = (int64_t)tile * TILE_PX;
       float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
@@ -429,7 +429,7 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
         ps.bad = 1;
         break;
       }
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots;
+      const int tile = cr.slot + (u % U.ntl) * sd.nslots[1];
       const int r = ps.cols[u / U.ntl];
       const int64_t i = (int64_t)tile * TILE_PX + t;
       const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
@@ -482,7 +482,7 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
   }
   if (pipe_failed(ps, consumed, ctl)) return;
   double tot[RMAX][2];
-  if (!finish_partials<float, 2>(sd, cr.slot, sh, R, tot)) return;
+  if (!finish_partials<float, 2>(sd, cr.slot, sd.nslots[1], sh, R, tot)) return;
   if (threadIdx.x == 0) {
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;

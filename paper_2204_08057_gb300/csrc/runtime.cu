@@ -75,11 +75,13 @@ struct Group {
   int block = TILE_PX;      // pixels per tile = threads per CTA
   int mult = 1;             // CTA slots = mult x resident CTAs
   int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (1: staged)
-  int ncta = 0;             // CTAs of every iteration launch over this group (fixed)
+  // Two CTA lists: [0] for operator (inner_apply) launches, [1] for update, residual and
+  // update_x launches (their kernels keep different numbers of CTAs resident).
+  int ncta[2] = {0, 0};     // CTAs of every launch of that kind (fixed per configuration)
   int cta_cap = 0;
-  CtaRef* d_ctas = nullptr;
-  CtaRef* h_ctas = nullptr;  // pinned staging for reassignments
-  std::vector<int> cur_set;  // systems the CTA list currently covers
+  CtaRef* d_ctas[2] = {nullptr, nullptr};
+  CtaRef* h_ctas[2] = {nullptr, nullptr};  // pinned staging for reassignments
+  std::vector<int> cur_set;  // systems the CTA lists currently cover
 };
 
 struct SysWork {
@@ -145,8 +147,10 @@ struct sylv_ctx {
 
 Plan::~Plan() {
   for (auto& g : groups) {
-    cudaFree(g.d_ctas);
-    cudaFreeHost(g.h_ctas);
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(g.d_ctas[k]);
+      cudaFreeHost(g.h_ctas[k]);
+    }
   }
   cudaFree(d_states);
   for (auto& w : work) {
@@ -191,24 +195,29 @@ int default_block(int64_t n) {
 // (uploaded before each solve).
 template <typename T>
 int configure_group(Plan& P, Group& g, int block, int mult, int va, int vu) {
-  const int oa = occupancy<T>(0, g.k, g.m, g.e, va, block);
-  const int ou = occupancy<T>(1, g.k, g.m, g.e, vu, block);
-  const int64_t budget = (int64_t)P.nsm * std::min(oa, ou) * mult;
+  const int occ[2] = {occupancy<T>(0, g.k, g.m, g.e, va, block),
+                      occupancy<T>(1, g.k, g.m, g.e, vu, block)};
   int64_t total = 0;
   for (int s : g.sys) total += ceil_div(P.hs[s]->op.n, block);
-  std::vector<CtaRef> cl;
-  for (int s : g.sys) {
-    const int nt = (int)ceil_div(P.hs[s]->op.n, block);
-    int64_t ns = total <= budget ? nt : (budget * nt) / total;
-    ns = std::max<int64_t>(1, std::min<int64_t>(ns, nt));
-    ns = std::min<int64_t>(ns, P.work[s].slot_cap);
-    P.h_desc[s].ntiles = nt;
-    P.h_desc[s].nslots = (int)ns;
-    for (int t = 0; t < ns; ++t) cl.push_back(CtaRef{s, t});
+  for (int kind = 0; kind < 2; ++kind) {
+    const int64_t budget = (int64_t)P.nsm * occ[kind] * mult;
+    int used = 0;
+    for (int s : g.sys) {
+      const int nt = (int)ceil_div(P.hs[s]->op.n, block);
+      int64_t ns = total <= budget ? nt : (budget * nt) / total;
+      ns = std::max<int64_t>(1, std::min<int64_t>(ns, nt));
+      ns = std::min<int64_t>(ns, P.work[s].slot_cap);
+      P.h_desc[s].ntiles = nt;
+      P.h_desc[s].nslots[kind] = (int)ns;
+      for (int t = 0; t < ns; ++t) {
+        if (used >= g.cta_cap) return fail(SYLV_E_CUDA, "internal: CTA list overflow");
+        g.h_ctas[kind][used++] = CtaRef{s, t};
+      }
+    }
+    CK(cudaMemcpy(g.d_ctas[kind], g.h_ctas[kind], (size_t)used * sizeof(CtaRef),
+                  cudaMemcpyHostToDevice));
+    g.ncta[kind] = used;
   }
-  if ((int)cl.size() > g.cta_cap) return fail(SYLV_E_CUDA, "internal: CTA list overflow");
-  CK(cudaMemcpy(g.d_ctas, cl.data(), cl.size() * sizeof(CtaRef), cudaMemcpyHostToDevice));
-  g.ncta = (int)cl.size();
   g.cur_set = g.sys;
   g.block = block;
   g.mult = mult;
@@ -224,32 +233,35 @@ int reassign_group(Plan& P, Group& g, const std::vector<int>& set, cudaStream_t 
   if (set == g.cur_set) return SYLV_OK;
   int64_t total = 0;
   for (int sy : set) total += P.h_desc[sy].ntiles;
-  std::vector<int64_t> ns(set.size());
-  int64_t sum = 0;
-  for (size_t t = 0; t < set.size(); ++t) {
-    const int sy = set[t];
-    const int64_t nt = P.h_desc[sy].ntiles;
-    int64_t v = total <= g.ncta ? nt : ((int64_t)g.ncta * nt) / total;
-    v = std::max<int64_t>(1, std::min<int64_t>({v, nt, (int64_t)P.work[sy].slot_cap}));
-    ns[t] = v;
-    sum += v;
+  for (int kind = 0; kind < 2; ++kind) {
+    const int ncta = g.ncta[kind];
+    std::vector<int64_t> ns(set.size());
+    int64_t sum = 0;
+    for (size_t t = 0; t < set.size(); ++t) {
+      const int sy = set[t];
+      const int64_t nt = P.h_desc[sy].ntiles;
+      int64_t v = total <= ncta ? nt : ((int64_t)ncta * nt) / total;
+      v = std::max<int64_t>(1, std::min<int64_t>({v, nt, (int64_t)P.work[sy].slot_cap}));
+      ns[t] = v;
+      sum += v;
+    }
+    while (sum > ncta) {  // the launch grid is fixed (captured graphs): trim the largest shares
+      size_t big = 0;
+      for (size_t t = 1; t < ns.size(); ++t)
+        if (ns[t] > ns[big]) big = t;
+      if (ns[big] <= 1) return fail(SYLV_E_CUDA, "internal: more systems than CTAs");
+      --ns[big];
+      --sum;
+    }
+    int used = 0;
+    for (size_t t = 0; t < set.size(); ++t) {
+      P.h_desc[set[t]].nslots[kind] = (int)ns[t];
+      for (int q = 0; q < ns[t]; ++q) g.h_ctas[kind][used++] = CtaRef{set[t], q};
+    }
+    for (int t = used; t < ncta; ++t) g.h_ctas[kind][t] = CtaRef{-1, 0};
+    CK(cudaMemcpyAsync(g.d_ctas[kind], g.h_ctas[kind], (size_t)ncta * sizeof(CtaRef),
+                       cudaMemcpyHostToDevice, s));
   }
-  while (sum > g.ncta) {  // the launch grid is fixed (captured graphs): trim the largest shares
-    size_t big = 0;
-    for (size_t t = 1; t < ns.size(); ++t)
-      if (ns[t] > ns[big]) big = t;
-    if (ns[big] <= 1) return fail(SYLV_E_CUDA, "internal: more systems than CTAs");
-    --ns[big];
-    --sum;
-  }
-  int used = 0;
-  for (size_t t = 0; t < set.size(); ++t) {
-    P.h_desc[set[t]].nslots = (int)ns[t];
-    for (int q = 0; q < ns[t]; ++q) g.h_ctas[used++] = CtaRef{set[t], q};
-  }
-  for (int t = used; t < g.ncta; ++t) g.h_ctas[t] = CtaRef{-1, 0};
-  CK(cudaMemcpyAsync(g.d_ctas, g.h_ctas, (size_t)g.ncta * sizeof(CtaRef), cudaMemcpyHostToDevice,
-                     s));
   g.cur_set = set;
   return SYLV_OK;
 }
@@ -328,10 +340,10 @@ int time_inner(Plan& P, Group& g, int kind, int reps, float* ms_out) {
     }
     CK(cudaEventRecord(P.evr0, s));
     if (kind == 0)
-      CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta, g.block, P.d_desc, g.d_ctas,
+      CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta[0], g.block, P.d_desc, g.d_ctas[0],
                                P.d_ctl, s));
     else
-      CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta, g.block, P.d_desc, g.d_ctas,
+      CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta[1], g.block, P.d_desc, g.d_ctas[1],
                                 P.d_ctl, s));
     CK(cudaEventRecord(P.evr1, s));
     CK(cudaStreamSynchronize(s));
@@ -461,8 +473,10 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
       g.cta_cap += P.work[s].slot_cap;
     }
     g.cta_cap += 1;
-    CK(dalloc(&g.d_ctas, (size_t)g.cta_cap * sizeof(CtaRef)));
-    CK(cudaMallocHost((void**)&g.h_ctas, (size_t)g.cta_cap * sizeof(CtaRef)));
+    for (int k = 0; k < 2; ++k) {
+      CK(dalloc(&g.d_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
+      CK(cudaMallocHost((void**)&g.h_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
+    }
     P.groups.push_back(g);
   }
   for (int s = 0; s < nsys; ++s) {
@@ -500,7 +514,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     d.op = hs[s]->op;
     d.R = R[s];
     d.ntiles = 0;  // set by configure_group
-    d.nslots = 0;
+    d.nslots[0] = d.nslots[1] = 0;
     const size_t vbytes = (size_t)R[s] * d.op.k * d.op.ld * tsz;
     char* base = (char*)P.work[s].vec;
     d.vd = base;
@@ -528,12 +542,12 @@ template <typename T>
 int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
                            bool capture_events) {
   for (auto& g : P.groups)
-    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta[0], g.block, P.d_desc, g.d_ctas[0], P.d_ctl, s));
   if (e_mid)
     CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_mid, s));
   for (auto& g : P.groups)
-    CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+    CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta[1], g.block, P.d_desc, g.d_ctas[1], P.d_ctl, s));
   if (e_end)
     CK(capture_events ? cudaEventRecordWithFlags(e_end, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_end, s));
@@ -648,10 +662,10 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
     if (!first_outer && (rc = rebalance(P, false, s)) != SYLV_OK) return rc;
     first_outer = false;
     for (auto& g : P.groups)
-      CK(launch_update_x<T>(g.k, g.ncta, g.block, P.d_desc, g.d_ctas, s));
+      CK(launch_update_x<T>(g.k, g.ncta[1], g.block, P.d_desc, g.d_ctas[1], s));
     if (prof) CK(cudaEventRecord(P.evr0, s));
     for (auto& g : P.groups)
-      CK(launch_residual<T>(g.k, g.m, g.e, g.ncta, g.block, P.d_desc, g.d_ctas, P.d_ctl, s));
+      CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[1], g.block, P.d_desc, g.d_ctas[1], P.d_ctl, s));
     if (prof) CK(cudaEventRecord(P.evr1, s));
     launches += 2 * ng;
     if ((rc = poll(P, s)) != SYLV_OK) break;

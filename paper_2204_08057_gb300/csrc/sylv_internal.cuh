@@ -93,8 +93,8 @@ struct SysDesc {
   OpData op;
   int R;                 // right-hand sides
   int ntiles;            // tiles of blockDim.x pixels
-  int nslots;            // CTAs working on this system in every iteration kernel
-  int pad;
+  int nslots[2];         // CTAs working on this system: [0] in operator (inner_apply) launches,
+                         // [1] in update, residual and update_x launches
   const double* B;       // R x k x ld
   double* X;             // R x k x ld
   void* vd;              // inner vectors, R x k x ld of the inner type
