@@ -268,19 +268,29 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       const float dg = stage[L::DIAG * TILE_PX + t];
 #pragma unroll
       for (int j = 0; j < K; ++j) lap[j] = dg * zi[j];
+      // neighbour values: from the staged tile when the neighbour is in it, else from global
+      // memory; generic pointers keep the loads branch-free so all E*K of them issue at once
+      const float* src[E];
+      int64_t stride[E];
+      float v[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int64_t c = scol[e * TILE_PX + t];
-        const float v = stage[(L::VAL + e) * TILE_PX + t];
+        v[e] = stage[(L::VAL + e) * TILE_PX + t];
         const uint32_t loc = (uint32_t)(c - base);
-        if (loc < (uint32_t)TILE_PX) {
-#pragma unroll
-          for (int j = 0; j < K; ++j) lap[j] += v * stage[(L::Z + j) * TILE_PX + loc];
-        } else {
-#pragma unroll
-          for (int j = 0; j < K; ++j) lap[j] += v * __ldg(zg + voff + (size_t)j * ld + c);
-        }
+        const bool in_tile = loc < (uint32_t)TILE_PX;
+        src[e] = in_tile ? stage + (size_t)L::Z * TILE_PX + loc : zg + voff + c;
+        stride[e] = in_tile ? (int64_t)TILE_PX : ld;
       }
+      float nb[E][K];
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
       float w[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) w[j] = sh.tk2[j] * zi[j] + sh.tau[j] * lap[j];
