@@ -64,7 +64,47 @@ int tma_occupancy(int kind) {
   return nb < 1 ? 1 : nb;
 }
 
+template <int K, int M, int E>
+cudaError_t apply_x_tma(const OpData& op, const float* X, float* Y, int R, unsigned int* err,
+                        cudaStream_t s) {
+  static bool attr = false;
+  static int grid = 0;
+  const size_t smem = (size_t)tma::NSTAGE * tma::ApplyXLayout<K, M, E>::STAGE_BYTES;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tma::k_apply_tma<K, M, E>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, dev = 0, nsm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tma::k_apply_tma<K, M, E>,
+                                                  tma::WS_THREADS, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    grid = nsm * (occ < 1 ? 1 : occ);
+    attr = true;
+  }
+  const int ntiles = (int)(op.n / TILE_PX);
+  const int g = ntiles < grid ? ntiles : grid;
+  tma::k_apply_tma<K, M, E><<<g, tma::WS_THREADS, smem, s>>>(op, X, Y, R, err);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+#define SYLV_TMA_APPLY_X_(K_, M_, E_) \
+  if (k == K_ && m == M_ && e == E_) return apply_x_tma<K_, M_, E_>(op, X, Y, R, err, s);
+
+// Staged stand-alone FP32 apply; cudaErrorNotSupported when the shape or the alignment does
+// not allow it (the caller then uses the direct kernel).
+cudaError_t launch_apply_staged(const OpData& op, const float* X, float* Y, int R,
+                                unsigned int* err, cudaStream_t s) {
+  const int k = op.k, m = op.m, e = op.E;
+  const bool aligned = op.n > 0 && op.n % TILE_PX == 0 && op.ldu % 4 == 0 &&
+                       ((uintptr_t)X & 15u) == 0 && ((uintptr_t)Y & 15u) == 0 && !op.has_w;
+  if (aligned) {
+    SYLV_SPECIAL_SHAPES(SYLV_TMA_APPLY_X_)
+  }
+  return cudaErrorNotSupported;
+}
 
 #define SYLV_TMA_APPLY_(K_, M_, E_) \
   if (k == K_ && m == M_ && e == E_) return apply_tma<K_, M_, E_>(ncta, d, c, ctl, s);

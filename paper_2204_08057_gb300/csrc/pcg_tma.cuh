@@ -526,5 +526,130 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// stand-alone operator apply (staged): Y = G X for FP32 caller vectors (nrhs columns)
+// ---------------------------------------------------------------------------------------------
+// Stage: x of the tile (K rows), D, ELL values, diagonal, ELL columns.  Used when n is a
+// multiple of TILE_PX and every caller row starts 16-byte aligned (whole-tile copies then stay
+// inside the caller's rows).
+template <int K, int M, int E>
+struct ApplyXLayout {
+  static constexpr int X = 0, D = K, VAL = K + M, DIAG = K + M + E, COL = K + M + E + 1;
+  static constexpr int ROWS = K + M + 2 * E + 1;
+  static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
+};
+
+template <int K, int M, int E>
+__global__ void __launch_bounds__(WS_THREADS, 3)
+k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R,
+            unsigned int* error) {
+  using L = ApplyXLayout<K, M, E>;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ CtaShared<float, 1> sh;
+  __shared__ __align__(8) PipeShared ps;
+  stage_operator<float, 1>(op, K, sh);
+  if (threadIdx.x == 0) pipe_init(ps);
+  __syncthreads();
+  const int64_t ldu = op.ldu;
+  const int ntiles = (int)(op.n / TILE_PX);
+  const int ntl = (int)blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int nunits = ntl * R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int consumed = 0;
+  if (warp == NCONS) {
+    producer_loop(ps, nunits, [&](int u, int st) {
+      const int tile = blockIdx.x + (u % ntl) * gridDim.x;
+      const int r = u / ntl;
+      const int64_t base = (int64_t)tile * TILE_PX;
+      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+      const uint32_t rowb = TILE_PX * 4;
+      if (lane == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&ps.full[st], (uint32_t)L::ROWS * rowb);
+      }
+      __syncwarp();
+      const size_t xoff = (size_t)r * K * ldu;
+      for (int q = lane; q < L::ROWS; q += 32) {
+        const void* src;
+        if (q < K) src = X + xoff + (size_t)q * ldu + base;
+        else if (q < L::VAL) src = op.D32 + (size_t)(q - L::D) * op.ld + base;
+        else if (q < L::DIAG) src = op.ell_val32 + (size_t)(q - L::VAL) * op.ld + base;
+        else if (q == L::DIAG) src = op.diag32 + base;
+        else src = op.ell_col + (size_t)(q - L::COL) * op.ld + base;
+        bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
+      }
+    });
+  } else {
+    const int t = threadIdx.x;
+    for (int u = 0; u < nunits; ++u) {
+      const int st = u % NSTAGE;
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+        ps.bad = 1;
+        break;
+      }
+      const int tile = blockIdx.x + (u % ntl) * gridDim.x;
+      const int r = u / ntl;
+      const int64_t base = (int64_t)tile * TILE_PX;
+      const int64_t i = base + t;
+      const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
+      const int32_t* scol = reinterpret_cast<const int32_t*>(stage + (size_t)L::COL * TILE_PX);
+      const size_t xoff = (size_t)r * K * ldu;
+      float xi[K], lap[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) xi[j] = stage[(L::X + j) * TILE_PX + t];
+      const float dg = stage[L::DIAG * TILE_PX + t];
+#pragma unroll
+      for (int j = 0; j < K; ++j) lap[j] = dg * xi[j];
+      const float* src[E];
+      int64_t stride[E];
+      float v[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t c = scol[e * TILE_PX + t];
+        v[e] = stage[(L::VAL + e) * TILE_PX + t];
+        const uint32_t loc = (uint32_t)(c - base);
+        const bool in_tile = loc < (uint32_t)TILE_PX;
+        src[e] = in_tile ? stage + (size_t)L::X * TILE_PX + loc : X + xoff + c;
+        stride[e] = in_tile ? (int64_t)TILE_PX : ldu;
+      }
+      float nb[E][K];
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
+      float w[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) w[j] = sh.tk2[j] * xi[j] + sh.tau[j] * lap[j];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        const float d = stage[(L::D + c) * TILE_PX + t];
+        float a[K];
+        load_row<K, float>(sh.A[c], a);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < K; ++j) s += a[j] * xi[j];
+        s *= d;
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j] += a[j] * s;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ps.empty[st]);
+      consumed = u + 1;
+#pragma unroll
+      for (int j = 0; j < K; ++j) Y[xoff + (size_t)j * ldu + i] = w[j];
+    }
+  }
+  __syncthreads();
+  if (ps.bad && threadIdx.x == 0) {
+    atomicOr(error, 1u);
+    for (int u = consumed; u < ps.issued; ++u)
+      mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+  }
+}
+
 }  // namespace tma
 }  // namespace sylv

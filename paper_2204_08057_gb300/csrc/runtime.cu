@@ -136,6 +136,7 @@ struct sylv_ctx {
   double* w64 = nullptr;
   double* blk64 = nullptr;
   double* fac64 = nullptr;
+  unsigned int* apply_err = nullptr;  // timeout flag of the staged stand-alone apply
   float* fs32 = nullptr;
   __half2* fl16 = nullptr;
   std::unique_ptr<Plan> plan[2];  // single-system plans, [inner_double]
@@ -176,6 +177,12 @@ Plan::~Plan() {
 }
 
 namespace {
+
+// SYLV_STAGED_APPLY=0 keeps the stand-alone FP32 apply on the direct kernel.
+const bool g_staged_apply = [] {
+  const char* v = std::getenv("SYLV_STAGED_APPLY");
+  return !(v && v[0] == '0');
+}();
 
 // Batched plans, keyed by the list of (handle, nrhs) and the inner type.
 std::mutex g_plan_mu;
@@ -849,6 +856,7 @@ static void free_handle(sylv_ctx* h) {
   cudaFree(h->fac64);
   cudaFree(h->fs32);
   cudaFree(h->fl16);
+  cudaFree(h->apply_err);
   cudaFree(h->lam);
   cudaFree(h->grad_ws);
   delete h;
@@ -1048,7 +1056,19 @@ int sylv_apply(sylv_handle h, const void* X, void* Y, int nrhs, int dtype, sylv_
   if (nrhs < 1) return fail(SYLV_E_INVALID, "nrhs must be >= 1");
   DeviceGuard g(h->device);
   if (dtype == SYLV_F32) {
-    CK(launch_apply<float>(h->op, (const float*)X, (float*)Y, nrhs, (cudaStream_t)s));
+    if (!h->apply_err) {
+      CK(dalloc(&h->apply_err, sizeof(unsigned int)));
+      CK(cudaMemset(h->apply_err, 0, sizeof(unsigned int)));
+    }
+    cudaError_t e = g_staged_apply ? launch_apply_staged(h->op, (const float*)X, (float*)Y, nrhs,
+                                                         h->apply_err, (cudaStream_t)s)
+                                   : cudaErrorNotSupported;
+    if (e == cudaErrorNotSupported) {
+      (void)cudaGetLastError();
+      CK(launch_apply<float>(h->op, (const float*)X, (float*)Y, nrhs, (cudaStream_t)s));
+    } else if (e != cudaSuccess) {
+      return cuda_fail(e, "staged apply");
+    }
   } else if (dtype == SYLV_F64) {
     CK(launch_apply<double>(h->op, (const double*)X, (double*)Y, nrhs, (cudaStream_t)s));
   } else {

@@ -167,6 +167,8 @@ cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, f
                                __half2* fl16, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s);
+cudaError_t launch_apply_staged(const OpData& op, const float* X, float* Y, int R,
+                                unsigned int* err, cudaStream_t s);
 cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, const double* Y,
                         int R, int want_beta, double* partial, int ntiles, double* out,
                         cudaStream_t s);
