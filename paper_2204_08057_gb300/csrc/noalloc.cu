@@ -132,6 +132,7 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   sd.ntiles = ntiles;
   sd.nslots[0] = nslots;
   sd.nslots[1] = nslots;
+  sd.nslots[2] = nslots;
   sd.B = B;
   sd.X = X;
   unsigned char* vec = base + o_vec;

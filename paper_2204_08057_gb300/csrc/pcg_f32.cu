@@ -145,7 +145,7 @@ cudaError_t launch_update_x<float>(int k, int ncta, int block, const SysDesc* d,
 }
 template <>
 int occupancy<float>(int kind, int k, int m, int e, int variant, int block) {
-  if (variant == 1) {
+  if (variant == 1 && kind < 2) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_OCC_)
   }
   return occupancy_impl<float>(kind, k, m, e, block);

@@ -607,7 +607,7 @@ k_update_x(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas) {
     if (sd.st[r].phase != PH_INNER_DONE) continue;
     const T* d = (const T*)sd.vd + (size_t)r * K * ld;
     double* X = sd.X + (size_t)r * K * ldu;
-    for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[1]) {
+    for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[2]) {
       const int64_t i = (int64_t)tile * blockDim.x + threadIdx.x;
       if (i >= n) continue;
 #pragma unroll
@@ -646,7 +646,7 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
   const bool x0_zero = ctl->x0_zero != 0;
-  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[1]) {
+  for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[2]) {
     const int64_t i0 = (int64_t)tile * blockDim.x + threadIdx.x;
     const bool valid = i0 < n;
     const int64_t i = valid ? i0 : 0;
@@ -697,19 +697,22 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
 #pragma unroll
           for (int j = 0; j < K; ++j) zi[j] = ri[j];
         }
+        T rzt = T(0), rrt = T(0);   // products in the inner type, like the inner kernels
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           z[j * ld + i] = zi[j];
-          rz += double(ri[j]) * double(zi[j]);
-          rr += double(ri[j]) * double(ri[j]);
+          rzt += ri[j] * zi[j];
+          rrt += ri[j] * ri[j];
         }
+        rz = double(rzt);
+        rr = double(rrt);
       }
       const double v[4] = {rr64, bb, rz, rr};
       warp_accumulate<double, 4>(sh, r, v);
     }
   }
   double tot[RMAX][4];
-  if (!finish_partials<double, 4>(sd, cr.slot, sd.nslots[1], sh, R, tot)) return;
+  if (!finish_partials<double, 4>(sd, cr.slot, sd.nslots[2], sh, R, tot)) return;
   if (threadIdx.x == 0) {
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
@@ -842,7 +845,7 @@ cudaError_t launch_update_x_impl(int k, int ncta, int block, const SysDesc* d, c
   return cudaGetLastError();
 }
 
-// Resident CTAs per SM of the plain inner kernel `kind` (0 apply, 1 update) for a shape.
+// Resident CTAs per SM of the plain kernel `kind` (0 apply, 1 update, 2 residual).
 template <typename T>
 int occupancy_impl(int kind, int k, int m, int e, int block) {
   int nb = 0;
@@ -853,7 +856,8 @@ int occupancy_impl(int kind, int k, int m, int e, int block) {
 #define CALL(K, M, E)                                                     \
   do {                                                                    \
     if (kind == 0) take((const void*)k_inner_apply<K, M, E, T>);          \
-    else take((const void*)k_inner_update<K, M, E, T>);                   \
+    else if (kind == 1) take((const void*)k_inner_update<K, M, E, T>);    \
+    else take((const void*)k_residual<K, M, E, T>);                       \
   } while (0)
     SYLV_DISPATCH_SHAPE(k, m, e)
 #undef CALL

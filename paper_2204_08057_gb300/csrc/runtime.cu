@@ -75,12 +75,12 @@ struct Group {
   int block = TILE_PX;      // pixels per tile = threads per CTA
   int mult = 1;             // CTA slots = mult x resident CTAs
   int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (1: staged)
-  // Two CTA lists: [0] for operator (inner_apply) launches, [1] for update, residual and
-  // update_x launches (their kernels keep different numbers of CTAs resident).
-  int ncta[2] = {0, 0};     // CTAs of every launch of that kind (fixed per configuration)
+  // Three CTA lists: [0] for operator (inner_apply) launches, [1] for update launches, [2] for
+  // residual and update_x launches (their kernels keep different numbers of CTAs resident).
+  int ncta[3] = {0, 0, 0};  // CTAs of every launch of that kind (fixed per configuration)
   int cta_cap = 0;
-  CtaRef* d_ctas[2] = {nullptr, nullptr};
-  CtaRef* h_ctas[2] = {nullptr, nullptr};  // pinned staging for reassignments
+  CtaRef* d_ctas[3] = {nullptr, nullptr, nullptr};
+  CtaRef* h_ctas[3] = {nullptr, nullptr, nullptr};  // pinned staging for reassignments
   std::vector<int> cur_set;  // systems the CTA lists currently cover
 };
 
@@ -148,7 +148,7 @@ struct sylv_ctx {
 
 Plan::~Plan() {
   for (auto& g : groups) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
       cudaFree(g.d_ctas[k]);
       cudaFreeHost(g.h_ctas[k]);
     }
@@ -202,11 +202,12 @@ int default_block(int64_t n) {
 // (uploaded before each solve).
 template <typename T>
 int configure_group(Plan& P, Group& g, int block, int mult, int va, int vu) {
-  const int occ[2] = {occupancy<T>(0, g.k, g.m, g.e, va, block),
-                      occupancy<T>(1, g.k, g.m, g.e, vu, block)};
+  const int occ[3] = {occupancy<T>(0, g.k, g.m, g.e, va, block),
+                      occupancy<T>(1, g.k, g.m, g.e, vu, block),
+                      occupancy<T>(2, g.k, g.m, g.e, 0, block)};
   int64_t total = 0;
   for (int s : g.sys) total += ceil_div(P.hs[s]->op.n, block);
-  for (int kind = 0; kind < 2; ++kind) {
+  for (int kind = 0; kind < 3; ++kind) {
     const int64_t budget = (int64_t)P.nsm * occ[kind] * mult;
     int used = 0;
     for (int s : g.sys) {
@@ -240,7 +241,7 @@ int reassign_group(Plan& P, Group& g, const std::vector<int>& set, cudaStream_t 
   if (set == g.cur_set) return SYLV_OK;
   int64_t total = 0;
   for (int sy : set) total += P.h_desc[sy].ntiles;
-  for (int kind = 0; kind < 2; ++kind) {
+  for (int kind = 0; kind < 3; ++kind) {
     const int ncta = g.ncta[kind];
     std::vector<int64_t> ns(set.size());
     int64_t sum = 0;
@@ -480,7 +481,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
       g.cta_cap += P.work[s].slot_cap;
     }
     g.cta_cap += 1;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
       CK(dalloc(&g.d_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
       CK(cudaMallocHost((void**)&g.h_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
     }
@@ -521,7 +522,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     d.op = hs[s]->op;
     d.R = R[s];
     d.ntiles = 0;  // set by configure_group
-    d.nslots[0] = d.nslots[1] = 0;
+    d.nslots[0] = d.nslots[1] = d.nslots[2] = 0;
     const size_t vbytes = (size_t)R[s] * d.op.k * d.op.ld * tsz;
     char* base = (char*)P.work[s].vec;
     d.vd = base;
@@ -669,10 +670,10 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
     if (!first_outer && (rc = rebalance(P, false, s)) != SYLV_OK) return rc;
     first_outer = false;
     for (auto& g : P.groups)
-      CK(launch_update_x<T>(g.k, g.ncta[1], g.block, P.d_desc, g.d_ctas[1], s));
+      CK(launch_update_x<T>(g.k, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], s));
     if (prof) CK(cudaEventRecord(P.evr0, s));
     for (auto& g : P.groups)
-      CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[1], g.block, P.d_desc, g.d_ctas[1], P.d_ctl, s));
+      CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], P.d_ctl, s));
     if (prof) CK(cudaEventRecord(P.evr1, s));
     launches += 2 * ng;
     if ((rc = poll(P, s)) != SYLV_OK) break;

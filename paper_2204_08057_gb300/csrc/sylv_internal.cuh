@@ -93,8 +93,9 @@ struct SysDesc {
   OpData op;
   int R;                 // right-hand sides
   int ntiles;            // tiles of blockDim.x pixels
-  int nslots[2];         // CTAs working on this system: [0] in operator (inner_apply) launches,
-                         // [1] in update, residual and update_x launches
+  int nslots[3];         // CTAs working on this system: [0] in operator (inner_apply) launches,
+                         // [1] in update launches, [2] in residual and update_x launches
+  int pad;
   const double* B;       // R x k x ld
   double* X;             // R x k x ld
   void* vd;              // inner vectors, R x k x ld of the inner type
@@ -146,7 +147,8 @@ cudaError_t launch_residual(int k, int m, int e, int ncta, int block, const SysD
 template <typename T>
 cudaError_t launch_update_x(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
                             cudaStream_t s);
-// Resident CTAs per SM of one inner kernel (kind 0: apply, 1: update) for a shape.
+// Resident CTAs per SM of one kernel (kind 0: inner apply, 1: inner update, 2: residual)
+// for a shape.
 template <typename T>
 int occupancy(int kind, int k, int m, int e, int variant, int block);
 cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,
