@@ -12,8 +12,10 @@
 // The loads need no registers while in flight; the only per-thread global loads left are the
 // stencil gathers that fall outside the tile (neighbours one image row away).
 //
-// Units run column by column (all tiles of one right-hand side, then the next), so dot
-// products accumulate in registers and are folded into the per-warp sums once per column.
+// With one active column, units run tile after tile and dot products accumulate in registers
+// until the end; with several, the columns of a tile run back to back (so the tile's operator
+// rows are re-read from L2, not HBM) and each unit's products are folded into the per-warp
+// sums of its column.
 //
 // Every mbarrier wait is bounded (about a second of SM clock).  When one expires the warp
 // stops, the CTA records SYLV_E_TIMEOUT in Control::error, thread 0 waits (bounded) for the
@@ -80,16 +82,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Units of a CTA: its tiles (slot, slot + nslots, ...) for each of its active columns, in
-// column-major order.
+// Units of a CTA: its tiles (slot, slot + nslots, ...) times its active columns; unit u is
+// tile u / nact and active column u % nact.
 struct Units {
   int ntl;   // tiles of this CTA
-  int n;     // units = ntl * active columns
+  int nact;  // active columns
+  int n;     // units = ntl * nact
 };
 
 __device__ __forceinline__ Units count_units(const SysDesc& sd, int slot, int nslots, int nact) {
   Units u;
   u.ntl = slot < sd.ntiles ? (sd.ntiles - slot + nslots - 1) / nslots : 0;
+  u.nact = nact;
   u.n = u.ntl * nact;
   return u;
 }
@@ -221,8 +225,8 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
 
   if (warp == NCONS) {
     producer_loop(ps, U.n, [&](int u, int st) {
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots[0];
-      const int r = ps.cols[u / U.ntl];
+      const int tile = cr.slot + (u / U.nact) * sd.nslots[0];
+      const int r = ps.cols[u % U.nact];
       const bool first = sh.aux[r] != 0;
       const int64_t base = (int64_t)tile * TILE_PX;
       float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
@@ -255,8 +259,8 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
         ps.bad = 1;
         break;
       }
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots[0];
-      const int r = ps.cols[u / U.ntl];
+      const int tile = cr.slot + (u / U.nact) * sd.nslots[0];
+      const int r = ps.cols[u % U.nact];
       const int64_t base = (int64_t)tile * TILE_PX;
       const int64_t i = base + t;
       const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
@@ -326,7 +330,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       if (lane == 0) mbar_arrive(&ps.empty[st]);
       consumed = u + 1;
       acc += double(pq);
-      if ((u + 1) % U.ntl == 0) {   // last tile of this column
+      if (U.nact > 1 || u + 1 == U.n) {
         const double v1[1] = {acc};
         warp_accumulate<float, 1>(sh, r, v1);
         acc = 0.0;
@@ -407,8 +411,8 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
 
   if (warp == NCONS) {
     producer_loop(ps, U.n, [&](int u, int st) {
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots[1];
-      const int r = ps.cols[u / U.ntl];
+      const int tile = cr.slot + (u / U.nact) * sd.nslots[1];
+      const int r = ps.cols[u % U.nact];
       const int64_t base = (int64_t)tile * TILE_PX;
       float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
       const uint32_t rowb = TILE_PX * 4;
@@ -439,8 +443,8 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
         ps.bad = 1;
         break;
       }
-      const int tile = cr.slot + (u % U.ntl) * sd.nslots[1];
-      const int r = ps.cols[u / U.ntl];
+      const int tile = cr.slot + (u / U.nact) * sd.nslots[1];
+      const int r = ps.cols[u % U.nact];
       const int64_t i = (int64_t)tile * TILE_PX + t;
       const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
       const float alpha = sh.sc[r];
@@ -483,7 +487,7 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
       }
       acc_rz += double(rz);
       acc_rr += double(rr);
-      if ((u + 1) % U.ntl == 0) {
+      if (U.nact > 1 || u + 1 == U.n) {
         const double v2[2] = {acc_rz, acc_rr};
         warp_accumulate<float, 2>(sh, r, v2);
         acc_rz = acc_rr = 0.0;
@@ -531,7 +535,8 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
 // ---------------------------------------------------------------------------------------------
 // Stage: x of the tile (K rows), D, ELL values, diagonal, ELL columns.  Used when n is a
 // multiple of TILE_PX and every caller row starts 16-byte aligned (whole-tile copies then stay
-// inside the caller's rows).
+// inside the caller's rows).  Units run tile-major, so with several right-hand sides the
+// tile's operator rows come from L2 after the first.
 template <int K, int M, int E>
 struct ApplyXLayout {
   static constexpr int X = 0, D = K, VAL = K + M, DIAG = K + M + E, COL = K + M + E + 1;
@@ -558,8 +563,8 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
   int consumed = 0;
   if (warp == NCONS) {
     producer_loop(ps, nunits, [&](int u, int st) {
-      const int tile = blockIdx.x + (u % ntl) * gridDim.x;
-      const int r = u / ntl;
+      const int tile = blockIdx.x + (u / R) * gridDim.x;   // a tile's columns back to back
+      const int r = u % R;
       const int64_t base = (int64_t)tile * TILE_PX;
       float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
       const uint32_t rowb = TILE_PX * 4;
@@ -587,8 +592,8 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
         ps.bad = 1;
         break;
       }
-      const int tile = blockIdx.x + (u % ntl) * gridDim.x;
-      const int r = u / ntl;
+      const int tile = blockIdx.x + (u / R) * gridDim.x;   // a tile's columns back to back
+      const int r = u % R;
       const int64_t base = (int64_t)tile * TILE_PX;
       const int64_t i = base + t;
       const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
