@@ -268,13 +268,27 @@ def run_ours(args, rank, world, local_rank):
 
     # weak scaling: every rank solves its own independent instance (own seed)
     p = rank_problem(args.config, rank, args.scale)
-    op = Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
-                  kappa=p.kappa, nu=p.nu, beta=p.beta)
+    # set-up (sylv_create: CSR check, sliced ELL, copies of D, FP64 pixel blocks and factors)
+    Op0 = Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
+                   kappa=p.kappa, nu=p.nu, beta=p.beta)
+    Op0.close()
+    rp = torch.as_tensor(p.graph.rowptr, device=dev)
+    cl = torch.as_tensor(p.graph.col, device=dev)
+    vl = torch.as_tensor(p.graph.val, device=dev)
+    Dd = torch.as_tensor(p.D, device=dev)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
+    op = Operator(rowptr=rp, col=cl, val=vl, D=Dd, tau=p.tau, kappa=p.kappa, nu=p.nu,
+                  beta=p.beta)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t_setup) * 1e3
     E = int(np.max(np.diff(p.graph.rowptr))) - 1
     Yh = torch.from_numpy(p.Yobs).pin_memory()
     Y = Yh.to(dev)
     B = op.rhs(Y)
     stream = torch.cuda.current_stream()
+    ms_rhs, _ = _timed(stream, lambda: op.rhs(Y), 10)
+    rhs_bytes = (p.m * 8 + p.m * 8 + p.k * 8) * p.n      # Y, D (FP64) in, B out
 
     def barrier():
         if dist is not None:
@@ -401,6 +415,8 @@ def run_ours(args, rank, world, local_rank):
                          "force_env": "SYLV_TUNE_FORCE=%d,%d,%d,%d" % (
                              last["tile"], last["slots_mult"], last["apply_staged"],
                              last["update_staged"])},
+            "setup_ms": setup_ms,
+            "rhs": {"ms": ms_rhs, "gbs": rhs_bytes / (ms_rhs * 1e-3) / 1e9},
             "fp64_pcg": {"ms": ms64, "iterations": info64["iterations"],
                          "relres": info64["relres"], "speedup_mixed": ms64 / ms,
                          "relerr_mixed_vs_fp64": relerr_mixed_vs_fp64},
@@ -588,7 +604,13 @@ def run_multirhs(args):
     apply_bytes = bytes_apply(p.k, p.m, E, R=p.nrhs) * p.n
     peak, _ = load_peaks()
     its = info["iterations"]
-    per_px_it = p.nrhs * (bytes_inner_apply(p.k, p.m, E) + bytes_inner_update(p.k, p.m))
+    # per pixel and iteration: the vectors of every right-hand side plus the operator data
+    # (noise maps, ELL, diagonal, preconditioner factor) once, as the tile-major units read
+    # it from HBM once and from L2 for the other right-hand sides
+    op_apply = (p.m + E + 1) * 4 + 4 * E
+    op_update = 4 * p.k + 2 * (p.k * (p.k + 1) // 2)
+    per_px_it = (p.nrhs * (bytes_inner_apply(p.k, p.m, E) - op_apply) + op_apply
+                 + p.nrhs * (bytes_inner_update(p.k, p.m) - op_update) + op_update)
     line = _base_line(args, "multi-RHS solve time to relres 1e-8 (8 right-hand sides together)",
                       ms, "ms", {"workload": p.name, "n": p.n, "k": p.k, "m": p.m,
                                  "nrhs": p.nrhs, "tol": 1e-8, "precision": "mixed"})
