@@ -22,4 +22,6 @@ What it computes (all in float64, unknowns stored as X with shape (k, n), so tha
 * ``gradient``: derivatives of a loss on the posterior mean with respect to tau_j, kappa_j and
   beta_j through one adjoint solve, and central finite differences of the direct solve.
 * ``physical_mixing``: the physical mixing matrix of App. B (CMB, synchrotron, dust, free-free).
+* ``sylvester``: the block-Lanczos solver of the Sylvester form eq. Axb-Sylv for separable noise
+  and a common prior shape (Algorithms 4 and 5, Sec. 3.3).
 """

@@ -19,5 +19,6 @@ from .problems import (  # noqa: F401
     make_problem,
     config_problem,
     batch_problems,
+    separable_problem,
     CONFIG_SEED_BASE,
 )

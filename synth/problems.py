@@ -159,6 +159,25 @@ def config_problem(config_id: int, *, scale: Optional[int] = None, noise="lognor
     raise ValueError(f"unknown config {config_id}")
 
 
+def separable_problem(config_id: int = 2, *, scale: Optional[int] = None, kappa0: float = 0.1,
+                      nrhs: Optional[int] = None) -> Problem:
+    """The separable special case of workload ``config_id`` (2, 4 or 5): the same grid,
+    channels and spectral-index draw, noise precision d_ci = t_c nu_i (C = T kron N) and one
+    prior shape for every source (all kappa_j = kappa0, the geometric middle of 0.01..1), so
+    that the system is the Sylvester equation eq. Axb-Sylv."""
+    sides = {2: (1024, 2048, 6, 9), 4: (512, 1024, 4, 7), 5: (4096, 12288, 6, 9)}
+    if config_id not in sides:
+        raise ValueError(f"no separable variant of config {config_id}")
+    H, W, k, m = sides[config_id]
+    s = 1 if scale is None else int(scale)
+    g = _grid("sphere", H // s, W // s)
+    return make_problem(f"sphere{H // s}x{W // s}_k{k}_m{m}_separable", g, k, _nu_for(m), None,
+                        [kappa0] * k, 1.0, CONFIG_SEED_BASE + 20 + config_id,
+                        beta_draw=(-3.0, 2.0), noise="separable",
+                        nrhs=nrhs or (8 if config_id == 5 else 1), tol=1e-8,
+                        meta={"config": config_id, "separable": True})
+
+
 def batch_problems(count=64, side_range=(128, 1024), *, seed=None) -> List[Problem]:
     """Batched workload: ``count`` independent periodic lattices of log-uniform side, k in
     {3,4,5,6} uniform, m = k + 2, own kappa (log-spaced 0.01..1, permuted), beta and noise."""
