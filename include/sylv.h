@@ -181,6 +181,31 @@ int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const d
                   int nrhs, double* lambda, double* g_tau, double* g_kappa, double* g_beta,
                   const sylv_opts* o, sylv_info* info, sylv_stream s);
 
+/* Solves the same system through its Sylvester form (Sec. 3.3, eq. Axb-Sylv) with the block
+ * Lanczos method of Algorithms 4 and 5.  Applies when the noise precision is separable,
+ * d_ci = t_c nu_i (C = T kron N, nu_i > 0), and every source shares one prior shape
+ * (all kappa_j equal, so Q_j = tau_j Q_0 with Q_0 = kappa^2 W + L and P = diag(tau)); otherwise
+ * returns SYLV_E_UNSUPPORTED (sylv_last_error says which condition fails; d_ci / d_0i may
+ * vary by 1e-10 relative).  The handle detects the structure on the first call.  Then
+ *   N^{-1} Q_0 M + M Lhat = Yhat,  Lhat = A^T T A P^{-1},  Yhat = N^{-1} B P^{-1},
+ * with M (n x k) the solution: a block Krylov space of N^{-1} Q_0 (symmetric in the inner
+ * product y^T N x) is built from Yhat; the residual estimate of Algorithm 5 stops it; the
+ * coefficients Z of eq. soln-constr come from the small block-tridiagonal T_j; and
+ * M = sum_i V_i G_i (eq. soln-darstellung) is formed from the basis kept in device memory
+ * (the paper's second Lanczos pass is not run).  An outer loop forms the true FP64 residual
+ * b - G X and restarts the Lanczos run on it until ||b - G X||_F / ||b||_F <= o->tol.
+ * o->precision SYLV_PREC_MIXED keeps the basis and the operator in FP32 (each run reduces the
+ * residual by o->inner_tol at most), SYLV_PREC_F64 keeps them in FP64.  o->precond is ignored
+ * (the method has none); o->maxit caps the Lanczos steps summed over runs, o->max_outer the
+ * runs, o->check_every the steps between polls.  The basis takes k * ld * 4 (or 8) bytes per
+ * step, up to 384 steps per run and 60 % of the free device memory (environment variable
+ * SYLV_LZ_BASIS_MB sets the budget); a run that fills it ends there and the outer loop
+ * restarts.  B, X, nrhs, info and the statuses as in sylv_solve (info->iterations counts
+ * Lanczos steps, info->ms_apply and info->ms_update time the two passes of a step,
+ * info->ms_residual the FP64 residual and the assembly).  Synchronises s. */
+int sylv_solve_sylvester(sylv_handle h, const double* B, double* X, int nrhs,
+                         const sylv_opts* o, sylv_info* info, sylv_stream s);
+
 /* Allocation-free variant of sylv_solve (the paper has no counterpart; this is a service for
  * callers that cannot allocate).  Some callers cannot call cudaMalloc, or any routine that
  * allocates, at the point where they solve: a real-time pipeline whose memory is reserved

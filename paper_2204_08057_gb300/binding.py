@@ -32,7 +32,7 @@ MAX_K, MAX_M, MAX_DEGREE, MAX_RHS = 8, 16, 8, 16
 
 EXPORTED = ["sylv_opts_default", "sylv_create", "sylv_rhs", "sylv_apply", "sylv_solve",
             "sylv_solve_batched", "sylv_backward", "sylv_destroy", "sylv_strerror",
-            "sylv_last_error", "sylv_solve_noalloc"]
+            "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester"]
 
 
 class sylv_problem(ctypes.Structure):
@@ -99,6 +99,8 @@ def load(path=None):
                                   POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
     lib.sylv_solve_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_int,
                                        POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
+    lib.sylv_solve_sylvester.argtypes = [c_void_p, c_void_p, c_void_p, c_int,
+                                         POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
     lib.sylv_destroy.argtypes = [c_void_p]
     lib.sylv_destroy.restype = None
     lib.sylv_strerror.argtypes = [c_int]
@@ -292,4 +294,18 @@ def sylv_solve_noalloc(h, B, X, nrhs, opts=None, *, k, ld, n, stream=None, allow
                                      ctypes.byref(opts) if opts is not None else None,
                                      ctypes.byref(info), _stream(stream))
     _check(code, "sylv_solve_noalloc", ok=(SYLV_OK,) + tuple(allow))
+    return code, info
+
+
+def sylv_solve_sylvester(h, B, X, nrhs, opts=None, *, k, ld, n, stream=None, allow=()):
+    """Block-Lanczos solve of the Sylvester form (see sylv.h); same arguments and result as
+    ``sylv_solve``.  Returns (status, info)."""
+    import torch
+    need = ((nrhs - 1) * k + k - 1) * ld + n
+    info = sylv_info()
+    code = load().sylv_solve_sylvester(c_void_p(h), _dev_ptr(B, torch.float64, need, "B"),
+                                       _dev_ptr(X, torch.float64, need, "X"), int(nrhs),
+                                       ctypes.byref(opts) if opts is not None else None,
+                                       ctypes.byref(info), _stream(stream))
+    _check(code, "sylv_solve_sylvester", ok=(SYLV_OK,) + tuple(allow))
     return code, info

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libsylv.so")
-SOURCES = ["runtime.cu", "setup_kernels.cu", "pcg_f32.cu", "pcg_f64.cu", "noalloc.cu"]
+SOURCES = ["runtime.cu", "setup_kernels.cu", "pcg_f32.cu", "pcg_f64.cu", "noalloc.cu",
+           "lanczos.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -842,6 +842,7 @@ const char* sylv_last_error(void) { return g_last_error.c_str(); }
 
 static void free_handle(sylv_ctx* h) {
   if (!h) return;
+  lanczos_release(h);
   h->plan[0].reset();
   h->plan[1].reset();
   cudaFree(h->ell_col);

@@ -178,5 +178,7 @@ cudaError_t launch_grad(const OpData& op, const double* X, const double* lam, co
 // Handle internals for other translation units (runtime.cu).
 int handle_view(sylv_handle h, OpData* op, int* device);
 void set_last_error(const char* msg);
+// Frees what the Sylvester solver cached for a handle (lanczos.cu).
+void lanczos_release(sylv_handle h);
 
 }  // namespace sylv

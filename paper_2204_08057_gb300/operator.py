@@ -112,6 +112,23 @@ class Operator:
         d["code"] = code
         return X, d
 
+    def solve_sylvester(self, Bv, X0=None, *, opts=None, stream=None,
+                        allow_not_converged=False, allow=(), **kw):
+        """X = G^{-1} B through the Sylvester form and block Lanczos (separable noise, one
+        prior shape); returns (X, info dict)."""
+        Bb = self._batch(Bv, self.k)
+        if opts is None:
+            opts = B.make_opts(**kw)
+        X = Bb.new_zeros(Bb.shape) if X0 is None else self._batch(X0, self.k).clone()
+        if X0 is not None:
+            opts.use_x0 = 1
+        allow = tuple(allow) + ((B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ())
+        code, info = B.sylv_solve_sylvester(self.handle, Bb, X, Bb.shape[0], opts, k=self.k,
+                                            ld=self.ld, n=self.n, stream=stream, allow=allow)
+        d = info.as_dict()
+        d["code"] = code
+        return X, d
+
     def backward(self, Xhat, dLdX, Yobs=None, *, opts=None, want=("tau", "kappa", "beta"),
                  stream=None, **kw):
         """Gradients (g_tau, g_kappa, g_beta) of a loss with dl/dX = dLdX at X = Xhat."""
