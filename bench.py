@@ -299,7 +299,9 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     # ---- mixed-precision solve (the step) ------------------------------------------------------
-    kw = dict(tol=1e-8, precision=1, profile=1)
+    # timed without per-kernel events (an event pair around every launch inside the captured
+    # graphs costs ~8 % of the solve); the kernel breakdown comes from a profiled pass below
+    kw = dict(tol=1e-8, precision=1, profile=0)
     for _ in range(args.warmup):
         X, info = op.solve(B, **kw)
     clocks = ClockSampler(local_rank) if not args.no_clocks else None
@@ -318,6 +320,21 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop() if clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
     ms = max_over_ranks(ms, dist, dev)
+    assert infos[-1]["code"] == 0, infos[-1]
+    launches_timed = int(sum(i["launches"] for i in infos))
+
+    # ---- profiled pass: the same solves with CUDA events around every kernel launch --------
+    kwp = dict(tol=1e-8, precision=1, profile=1)
+    infos = []
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    p0.record(stream)
+    for _ in range(args.steps):
+        X, info = op.solve(B, **kwp)
+        infos.append(info)
+    p1.record(stream)
+    barrier()
+    ms_profiled = p0.elapsed_time(p1) / args.steps
     last = infos[-1]
     assert last["code"] == 0, last
 
@@ -372,7 +389,9 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / peak, "traffic": profiled_traffic(kname), "kernel": kname,
                 "bytes_per_launch": per_px * p.n, "avg_launch_ms": avg_ms,
                 "launches_timed": n_ap, "launches_issued": sum(i["n_update"] for i in infos),
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                "timing": "CUDA events around every launch, in a pass of the same K solves "
+                          "run right after the timed region"}
 
     # ---- end to end through the public API with host buffers --------------------------------
     Xh = torch.empty((1, p.k, p.n), dtype=torch.float64).pin_memory()
@@ -433,7 +452,8 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": ms_e2e, "unit": "ms",
                     "h2d_bytes_per_step": int(Yh.numel() * 8),
                     "d2h_bytes_per_step": int(Xh.numel() * 8)},
-            "gpu_launches": int(sum(i["launches"] for i in infos)),
+            "gpu_launches": launches_timed,
+            "ms_per_step_profiled": ms_profiled,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -668,10 +688,12 @@ def run_sylvester(args):
     B = op.rhs(torch.from_numpy(p.Yobs).cuda())
     stream = torch.cuda.current_stream()
     E = int(np.max(np.diff(p.graph.rowptr))) - 1
-    kw = dict(tol=1e-8, profile=1)
+    # the FP32 Lanczos run reaches 1e-5 in one restart, which saves one FP64 residual and one
+    # restart against the default 1e-4 (measured: 154 steps in 2 runs against 163 in 3)
+    kw = dict(tol=1e-8, profile=0)
 
-    def lz(prec):
-        return op.solve_sylvester(B, precision=prec, **kw)
+    def lz(prec, **extra):
+        return op.solve_sylvester(B, precision=prec, inner_tol=1e-5, **{**kw, **extra})
 
     def cg(prec):
         return op.solve(B, precision=prec, **kw)
@@ -691,12 +713,14 @@ def run_sylvester(args):
     ms_cg64, (_, info_cg64) = _timed(stream, lambda: cg(0), args.fp64_steps)
     for inf in (info_lz, info_cg, info_lz64, info_cg64):
         assert inf["code"] == 0, inf
-    its = info_lz["iterations"]
+    # kernel breakdown from one more solve with CUDA events around every launch
+    _, info_prof = lz(1, profile=1)
+    its = info_prof["iterations"]
     peak, _ = load_peaks()
     ba = bytes_lanczos_a(p.k, E) * p.n
     bb = bytes_lanczos_b(p.k) * p.n
-    ms_a = info_lz["ms_apply"] / max(its, 1)
-    ms_b = info_lz["ms_update"] / max(its, 1)
+    ms_a = info_prof["ms_apply"] / max(its, 1)
+    ms_b = info_prof["ms_update"] / max(its, 1)
     rel = float(torch.linalg.norm(X_lz - X_cg) / torch.linalg.norm(X_cg))
 
     def summary(ms, inf):
@@ -706,7 +730,7 @@ def run_sylvester(args):
     line = _base_line(args, "solve time to relres 1e-8, separable special case "
                             "(block-Lanczos Sylvester solver, mixed)", ms_lz, "ms",
                       {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "nrhs": 1,
-                       "tol": 1e-8, "kappa0": float(p.kappa[0]),
+                       "tol": 1e-8, "kappa0": float(p.kappa[0]), "lanczos_inner_tol": 1e-5,
                        "l2": "inputs larger than L2"})
     line.update({
         "lanczos_mixed": summary(ms_lz, info_lz),
@@ -715,8 +739,9 @@ def run_sylvester(args):
         "pcg_fp64": summary(ms_cg64, info_cg64),
         "speedup_vs_pcg_mixed": ms_cg / ms_lz, "speedup_vs_pcg_fp64": ms_cg64 / ms_lz,
         "relerr_lanczos_vs_pcg": rel,
-        "kernel_ms_per_solve": {"pass_a": info_lz["ms_apply"], "pass_b": info_lz["ms_update"],
-                                "residual64_and_assembly": info_lz["ms_residual"]},
+        "kernel_ms_per_solve": {"pass_a": info_prof["ms_apply"], "pass_b": info_prof["ms_update"],
+                                "residual64_and_assembly": info_prof["ms_residual"],
+                                "timing": "CUDA events around every launch, one extra solve"},
         "roofline": {"bound": "hbm", "kernel": f"k_lz_a<{p.k},{E},float>",
                      "achieved": ba / (ms_a * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": ba / (ms_a * 1e-3) / 1e9 / peak, "traffic": None,

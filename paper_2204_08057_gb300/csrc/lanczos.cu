@@ -130,8 +130,9 @@ struct Smem {
 // of every CTA costs more than the CTA's streaming work.  The FP32 passes therefore keep their
 // per-thread sums, warp trees and per-CTA sums in FP32, and only the sum over CTAs is carried in
 // two-float (hi + lo) arithmetic, by error-free transformations (Knuth's TwoSum), to about
-// 2^-48 relative; the FP64 kernels reduce in FP64.  Partial sums go to partial[blockIdx.x]; the
-// last CTA to arrive (atomic counter, no waiting) forms the totals in a fixed order that depends
+// 2^-48 relative; the FP64 kernels reduce in FP64.  Partial sums are stored value-major,
+// partial[t * gridDim.x + blockIdx.x], so that the last CTA to arrive (atomic counter, no
+// waiting) reads them with coalesced loads; it forms the totals in a fixed order that depends
 // only on the grid size, so they are reproducible.
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -157,6 +158,43 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   r.lo = r.lo - (s - r.hi);
   r.hi = s;
   return r;
+}
+
+// Dekker's exact product with a fused multiply-add, and the products, sums, reciprocal square
+// root (FP32 seed, one Newton step in two-float arithmetic) used by the small k x k algebra
+__device__ __forceinline__ FF ff_fast(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return FF{s, b - (s - a)};
+}
+
+__device__ __forceinline__ FF ff_sum(FF x, FF y) {
+  const float s = x.hi + y.hi;
+  const float bb = s - x.hi;
+  const float e = (x.hi - (s - bb)) + (y.hi - bb);
+  return ff_fast(s, e + x.lo + y.lo);
+}
+
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return ff_fast(p, e);
+}
+
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
+
+__device__ __forceinline__ FF ff_of(double d) {
+  const float hi = float(d);
+  return FF{hi, float(d - double(hi))};
+}
+
+__device__ __forceinline__ double ff_dbl(FF x) { return double(x.hi) + double(x.lo); }
+
+__device__ __forceinline__ FF ff_rsqrt(FF x) {
+  const FF r{rsqrtf(x.hi), 0.f};
+  const FF e = ff_sum(FF{1.f, 0.f}, ff_neg(ff_mul(x, ff_mul(r, r))));   // 1 - x r^2
+  return ff_sum(r, ff_mul(r, FF{0.5f * e.hi, 0.5f * e.lo}));
 }
 
 __device__ __forceinline__ FF warp_sum_ff(FF v) {
@@ -202,15 +240,36 @@ __device__ __forceinline__ bool reduce_last(const float (&v)[NV], S& sh, double*
   if (threadIdx.x < NV) {
     float s = 0.f;
     for (int w = 0; w < nw; ++w) s += redf[w * NV + threadIdx.x];
-    pf[(size_t)blockIdx.x * NVMAX + threadIdx.x] = s;
+    pf[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
   }
   if (!arrive_last(sh, counter)) return false;
-  // warp w sums values w, w + nw, ...; its lanes stride over the CTAs
-  for (int t = warp; t < NV; t += nw) {
-    FF acc{0.f, 0.f};
-    for (unsigned b = lane; b < gridDim.x; b += 32) acc = ff_add(acc, __ldcg(pf + (size_t)b * NVMAX + t));
-    acc = warp_sum_ff(acc);
-    if (lane == 0) sh.tot[t] = double(acc.hi) + double(acc.lo);
+  // thread x takes the partials of CTAs x, x + blockDim.x, ... (all their loads independent, so
+  // they are in flight together), then two-float trees over the warp and over the warps
+  FF acc[NV];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) acc[t] = FF{0.f, 0.f};
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    float x[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) x[t] = __ldcg(pf + (size_t)t * gridDim.x + b);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] = ff_add(acc[t], x[t]);
+  }
+  __syncthreads();   // redf is reused
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const FF w = warp_sum_ff(acc[t]);
+    if (lane == 0) {
+      redf[(warp * NV + t) * 2] = w.hi;
+      redf[(warp * NV + t) * 2 + 1] = w.lo;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    FF tot{0.f, 0.f};
+    for (int w = 0; w < nw; ++w)
+      tot = ff_add(tot, FF{redf[(w * NV + threadIdx.x) * 2], redf[(w * NV + threadIdx.x) * 2 + 1]});
+    sh.tot[threadIdx.x] = double(tot.hi) + double(tot.lo);
   }
   __syncthreads();
   return true;
@@ -231,70 +290,111 @@ __device__ __forceinline__ bool reduce_last(const double (&v)[NV], S& sh, double
   if (threadIdx.x < NV) {
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += sh.red[w * NV + threadIdx.x];
-    partial[(size_t)blockIdx.x * NVMAX + threadIdx.x] = s;
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
   }
   if (!arrive_last(sh, counter)) return false;
-  for (int t = warp; t < NV; t += nw) {
-    double acc = 0.0;
-    for (unsigned b = lane; b < gridDim.x; b += 32) acc += __ldcg(partial + (size_t)b * NVMAX + t);
-    acc = warp_sum(acc);
-    if (lane == 0) sh.tot[t] = acc;
+  double acc[NV];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) acc[t] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    double x[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) x[t] = __ldcg(partial + (size_t)t * gridDim.x + b);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] += x[t];
+  }
+  __syncthreads();   // sh.red is reused
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const double w = warp_sum(acc[t]);
+    if (lane == 0) sh.red[warp * NV + t] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double tot = 0.0;
+    for (int w = 0; w < nw; ++w) tot += sh.red[w * NV + threadIdx.x];
+    sh.tot[threadIdx.x] = tot;
   }
   __syncthreads();
   return true;
 }
 
 // Last CTA of pass B, warp 0: B_{s+1} = chol(S) (S = B^T B, the N-orthonormal QR of the new
-// block), its inverse as the next normalizer, and their history.  Lanes work on the rows of a
-// column at a time; the diagonal uses one reciprocal square root per column, which serves
-// both the Cholesky step and the inverse (so no divisions: FP64 is the scarce unit).  False
+// block), its inverse as the next normalizer, and their history.  Right-looking Cholesky: per
+// column one reciprocal square root of the pivot (which also gives the inverse's diagonal, so no
+// divisions) and a rank-one update of the trailing block by the lanes; then lane c forms column
+// c of the inverse by back substitution.  Dependent FP64 operations take 100-200 cycles each on
+// GB300, so the FP32 path runs this algebra in two-float arithmetic on the FP32 pipe (about 44
+// significant bits after the Newton step of the square root); the FP64 path uses FP64.  False
 // when a pivot falls to the rounding level of the inner type (the block Krylov space is
 // numerically exhausted).
+template <typename R> struct Arith;
+template <> struct Arith<double> {
+  using V = double;
+  static __device__ __forceinline__ V of(double d) { return d; }
+  static __device__ __forceinline__ double dbl(V x) { return x; }
+  static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+  static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
+  static __device__ __forceinline__ V neg(V a) { return -a; }
+  static __device__ __forceinline__ V rsq(V a) { return rsqrt(a); }
+  static __device__ __forceinline__ float lead(V a) { return float(a); }
+};
+template <> struct Arith<float> {
+  using V = FF;
+  static __device__ __forceinline__ V of(double d) { return ff_of(d); }
+  static __device__ __forceinline__ double dbl(V x) { return ff_dbl(x); }
+  static __device__ __forceinline__ V add(V a, V b) { return ff_sum(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return ff_mul(a, b); }
+  static __device__ __forceinline__ V neg(V a) { return ff_neg(a); }
+  static __device__ __forceinline__ V rsq(V a) { return ff_rsqrt(a); }
+  static __device__ __forceinline__ float lead(V a) { return a.hi; }
+};
+
 template <int K, typename T, typename SM>
 __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
-  __shared__ double S[KMAX][KMAX], R[KMAX][KMAX], Ri[KMAX][KMAX], rinv[KMAX];
+  using AR = Arith<T>;
+  using V = typename AR::V;
+  __shared__ V A[KMAX][KMAX], R[KMAX][KMAX], Ri[KMAX][KMAX], rinv[KMAX];
   __shared__ int bad;
   const int lane = threadIdx.x & 31;
+  double tr = 0.0;
+  for (int p = 0; p < K; ++p) tr += sh.tot[p * K - p * (p - 1) / 2];
   if (lane < K) {
     // packed upper triangle, row by row: entry (p, q), q >= p, at p K - p (p - 1) / 2 + q - p
     for (int q = 0; q < K; ++q) {
       const int p0 = lane < q ? lane : q, q0 = lane < q ? q : lane;
-      S[lane][q] = sh.tot[p0 * K - p0 * (p0 - 1) / 2 + (q0 - p0)];
-      R[lane][q] = 0.0;
+      A[lane][q] = AR::of(sh.tot[p0 * K - p0 * (p0 - 1) / 2 + (q0 - p0)]);
+      R[lane][q] = AR::of(0.0);
     }
   }
   if (lane == 0) bad = 0;
   __syncwarp();
-  double tr = 0.0;
-  for (int p = 0; p < K; ++p) tr += S[p][p];
-  const double rel = sizeof(T) == 4 ? 1e-12 : 1e-26;
+  const float thr = float((sizeof(T) == 4 ? 1e-12 : 1e-26) * tr);
   for (int j = 0; j < K; ++j) {
     if (lane == j) {
-      double d = S[j][j];
-      for (int p = 0; p < j; ++p) d -= R[p][j] * R[p][j];
-      if (!(d > rel * tr) || !isfinite(d)) {
+      V d = A[j][j];
+      if (!(AR::lead(d) > thr) || !isfinite(AR::lead(d))) {
         bad = 1;
-        d = 1.0;
+        d = AR::of(1.0);
       }
-      const double r = rsqrt(d);
-      R[j][j] = d * r;
+      const V r = AR::rsq(d);
+      R[j][j] = AR::mul(d, r);
       rinv[j] = r;
     }
     __syncwarp();
-    if (lane > j && lane < K) {
-      double v = S[j][lane];
-      for (int p = 0; p < j; ++p) v -= R[p][j] * R[p][lane];
-      R[j][lane] = v * rinv[j];
-    }
+    if (lane > j && lane < K) R[j][lane] = AR::mul(A[j][lane], rinv[j]);
+    __syncwarp();
+    if (lane > j && lane < K)   // trailing update of column `lane`, rows j+1..lane
+      for (int i = j + 1; i <= lane; ++i) A[i][lane] = AR::add(A[i][lane], AR::neg(AR::mul(R[j][i], R[j][lane])));
     __syncwarp();
   }
   if (bad) return false;
   if (lane < K) {   // column `lane` of R^{-1} by back substitution
     const int c = lane;
     for (int r = K - 1; r >= 0; --r) {
-      double v = r == c ? 1.0 : 0.0;
-      for (int p = r + 1; p <= c; ++p) v -= R[r][p] * Ri[p][c];
-      Ri[r][c] = r > c ? 0.0 : v * rinv[r];
+      V v = AR::of(r == c ? 1.0 : 0.0);
+      for (int p = r + 1; p <= c; ++p) v = AR::add(v, AR::neg(AR::mul(R[r][p], Ri[p][c])));
+      Ri[r][c] = r > c ? AR::of(0.0) : AR::mul(v, rinv[r]);
     }
   }
   __syncwarp();
@@ -303,11 +403,12 @@ __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
   Coef* co = a.co;
   for (int t = lane; t < K * K; t += 32) {
     const int p = t / K, q = t % K;
-    hb[t] = R[p][q];
-    hn[t] = Ri[p][q];
-    co->Bc[p * KMAX + q] = R[p][q];
+    const double rb = AR::dbl(R[p][q]), ri = AR::dbl(Ri[p][q]);
+    hb[t] = rb;
+    hn[t] = ri;
+    co->Bc[p * KMAX + q] = rb;
     co->Np[p * KMAX + q] = co->Nc[p * KMAX + q];
-    co->Nc[p * KMAX + q] = Ri[p][q];
+    co->Nc[p * KMAX + q] = ri;
   }
   return true;
 }
@@ -560,14 +661,54 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_lz_b(const Args 
 // ---- staged FP32 passes ----------------------------------------------------------------------
 // The same two passes with every contiguous row a tile needs (the raw blocks, W, the ELL rows,
 // the Laplacian diagonal, nu and 1/nu; TILE_PX values each) brought into shared memory by
-// cp.async.bulk copies: one producer warp fills a two-stage ring on "full" mbarriers, eight
+// cp.async.bulk copies: one producer warp fills a ring of stages on "full" mbarriers, eight
 // consumer warps (one pixel per thread) compute from it and release each stage on an "empty"
 // mbarrier.  Stencil neighbours inside the tile are read from the staged block, the others
 // (one image row away) from global memory.  Every wait is bounded; on expiry the CTA sets
 // Ctl::err, waits (bounded) for its copies in flight and leaves without its partial sums.
-using tma::NSTAGE;
 using tma::NCONS;
 using tma::WS_THREADS;
+constexpr int NST_A = 3;   // stages of the pass-A ring (3 x 23 KB for k = 6)
+constexpr int NST_B = 4;   // stages of the pass-B ring (4 x 13 KB for k = 6)
+
+template <int NST>
+struct Pipe {
+  uint64_t full[NST];
+  uint64_t empty[NST];
+  int bad;
+  int issued;
+};
+
+template <int NST>
+__device__ __forceinline__ void pipe_init(Pipe<NST>& ps) {
+  for (int q = 0; q < NST; ++q) {
+    tma::mbar_init(&ps.full[q], 1);
+    tma::mbar_init(&ps.empty[q], NCONS);
+  }
+  ps.bad = 0;
+  ps.issued = 0;
+  tma::fence_mbar_init();
+}
+
+// Producer warp: waits until the consumers released stage u % NST, then issues unit u.
+template <int NST, typename Issue>
+__device__ __forceinline__ void producer(Pipe<NST>& ps, int nunits, Issue&& issue) {
+  const int lane = threadIdx.x & 31;
+  for (int u = 0; u < nunits; ++u) {
+    const int st = u % NST;
+    if (u >= NST) {
+      bool ok = true;
+      if (lane == 0) ok = tma::mbar_wait_bounded(&ps.empty[st], ((u / NST) - 1) & 1);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok || ps.bad) {
+        if (lane == 0) ps.bad = 1;
+        break;
+      }
+    }
+    issue(u, st);
+    if (lane == 0) ps.issued = u + 1;
+  }
+}
 
 template <int K, int E>
 struct LayoutA {
@@ -584,13 +725,14 @@ struct LayoutB {
   static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
 };
 
-__device__ __forceinline__ bool staged_failed(tma::PipeShared& ps, int consumed, Ctl* ctl) {
+template <int NST>
+__device__ __forceinline__ bool staged_failed(Pipe<NST>& ps, int consumed, Ctl* ctl) {
   __syncthreads();
   if (!ps.bad) return false;
   if (threadIdx.x == 0) {
     atomicOr(&ctl->err, 1u);
     for (int u = consumed; u < ps.issued; ++u)
-      tma::mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+      tma::mbar_wait_bounded(&ps.full[u % NST], (u / NST) & 1);
   }
   __syncthreads();
   return true;
@@ -602,7 +744,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
   constexpr int NS = K * (K + 1) / 2;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ Smem<float, WS_THREADS / 32> sh;
-  __shared__ __align__(8) tma::PipeShared ps;
+  __shared__ __align__(8) Pipe<NST_A> ps;
   if (a.ctl->done != RUNNING) return;
   const int s = a.ctl->step + 1;
   for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
@@ -611,7 +753,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
     sh.Np[p][q] = float(a.co->Np[p * KMAX + q]);
     sh.Bc[p][q] = float(a.co->Bc[p * KMAX + q]);
   }
-  if (threadIdx.x == 0) tma::pipe_init(ps);
+  if (threadIdx.x == 0) pipe_init(ps);
   __syncthreads();
   const OpData& op = a.op;
   const int64_t ld = op.ld, n = op.n;
@@ -627,7 +769,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
 #pragma unroll
   for (int t = 0; t < NS; ++t) acc[t] = 0.f;
   if (warp == NCONS) {
-    tma::producer_loop(ps, nunits, [&](int u, int st) {
+    producer(ps, nunits, [&](int u, int st) {
       const int64_t base = ((int64_t)blockIdx.x + (int64_t)u * gridDim.x) * TILE_PX;
       float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
       const uint32_t rowb = TILE_PX * 4;
@@ -652,8 +794,8 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
   } else {
     const int t = threadIdx.x;
     for (int u = 0; u < nunits; ++u) {
-      const int st = u % NSTAGE;
-      if (!tma::mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+      const int st = u % NST_A;
+      if (!tma::mbar_wait_bounded(&ps.full[st], (u / NST_A) & 1) || ps.bad) {
         ps.bad = 1;
         break;
       }
@@ -761,7 +903,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ Smem<float, WS_THREADS / 32> sh;
   __shared__ float Hs[KMAX][KMAX];
-  __shared__ __align__(8) tma::PipeShared ps;
+  __shared__ __align__(8) Pipe<NST_B> ps;
   if (a.ctl->done != RUNNING) return;
   const int s = a.ctl->step + 1;
   for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
@@ -769,7 +911,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
     sh.Nc[p][q] = float(a.co->Nc[p * KMAX + q]);
     Hs[p][q] = float(a.co->H[p * KMAX + q]);
   }
-  if (threadIdx.x == 0) tma::pipe_init(ps);
+  if (threadIdx.x == 0) pipe_init(ps);
   __syncthreads();
   const int64_t ld = a.op.ld, n = a.op.n;
   const float* cur = (const float*)a.basis + (size_t)(s - 1) * a.bstride;
@@ -783,7 +925,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
 #pragma unroll
   for (int t = 0; t < NS; ++t) acc[t] = 0.f;
   if (warp == NCONS) {
-    tma::producer_loop(ps, nunits, [&](int u, int st) {
+    producer(ps, nunits, [&](int u, int st) {
       const int64_t base = ((int64_t)blockIdx.x + (int64_t)u * gridDim.x) * TILE_PX;
       float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
       const uint32_t rowb = TILE_PX * 4;
@@ -803,8 +945,8 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
   } else {
     const int t = threadIdx.x;
     for (int u = 0; u < nunits; ++u) {
-      const int st = u % NSTAGE;
-      if (!tma::mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+      const int st = u % NST_B;
+      if (!tma::mbar_wait_bounded(&ps.full[st], (u / NST_B) & 1) || ps.bad) {
         ps.bad = 1;
         break;
       }
@@ -1000,10 +1142,10 @@ bool staged_available(const OpData& op) { return op.E == 4 && !op.has_w && op.ld
 template <int K>
 cudaError_t set_smem_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_lz_a_tma<K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       NSTAGE * LayoutA<K, 4>::STAGE_BYTES);
+                                       NST_A * LayoutA<K, 4>::STAGE_BYTES);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_lz_b_tma<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              NSTAGE * LayoutB<K>::STAGE_BYTES);
+                              NST_B * LayoutB<K>::STAGE_BYTES);
 }
 
 cudaError_t launch_a_tma(const Args& a, int ncta, cudaStream_t s) {
@@ -1011,7 +1153,7 @@ cudaError_t launch_a_tma(const Args& a, int ncta, cudaStream_t s) {
   do {                                                                                       \
     static const cudaError_t attr = set_smem_attrs<K>();                                     \
     if (attr != cudaSuccess) return attr;                                                    \
-    k_lz_a_tma<K, 4><<<ncta, WS_THREADS, NSTAGE * LayoutA<K, 4>::STAGE_BYTES, s>>>(a);        \
+    k_lz_a_tma<K, 4><<<ncta, WS_THREADS, NST_A * LayoutA<K, 4>::STAGE_BYTES, s>>>(a);        \
   } while (0)
   LZ_DISPATCH_K(a.op.k, CALL)
 #undef CALL
@@ -1023,7 +1165,7 @@ cudaError_t launch_b_tma(const Args& a, int ncta, cudaStream_t s) {
   do {                                                                                       \
     static const cudaError_t attr = set_smem_attrs<K>();                                     \
     if (attr != cudaSuccess) return attr;                                                    \
-    k_lz_b_tma<K><<<ncta, WS_THREADS, NSTAGE * LayoutB<K>::STAGE_BYTES, s>>>(a);             \
+    k_lz_b_tma<K><<<ncta, WS_THREADS, NST_B * LayoutB<K>::STAGE_BYTES, s>>>(a);             \
   } while (0)
   LZ_DISPATCH_K(a.op.k, CALL)
 #undef CALL
@@ -1058,10 +1200,10 @@ int occupancy(int kind, int k, int E) {
       take(E == 4 ? (const void*)k_lz_start<K, 4, T> : (const void*)k_lz_start<K, 0, T>); \
     else if (kind == 4) {                                                         \
       if (set_smem_attrs<K>() != cudaSuccess) nb = 1;                             \
-      else take_ws((const void*)k_lz_a_tma<K, 4>, NSTAGE * LayoutA<K, 4>::STAGE_BYTES); \
+      else take_ws((const void*)k_lz_a_tma<K, 4>, NST_A * LayoutA<K, 4>::STAGE_BYTES); \
     } else {                                                                      \
       if (set_smem_attrs<K>() != cudaSuccess) nb = 1;                             \
-      else take_ws((const void*)k_lz_b_tma<K>, NSTAGE * LayoutB<K>::STAGE_BYTES); \
+      else take_ws((const void*)k_lz_b_tma<K>, NST_B * LayoutB<K>::STAGE_BYTES); \
     }                                                                             \
   } while (0)
     LZ_DISPATCH_K(k, CALL)
