@@ -72,9 +72,11 @@ struct Ctl {
 
 // Small k x k quantities shared by the passes (row-major, KMAX x KMAX storage).
 struct Coef {
-  double Nc[KMAX * KMAX];         // normalizer of the current raw block: V_s = Vt_s Nc
-  double Np[KMAX * KMAX];         // normalizer of the previous raw block
-  double Bc[KMAX * KMAX];         // B_s (upper triangular), step s subtracts V_{s-1} B_s^T
+  double Rc[KMAX * KMAX];         // B_s, upper triangular: raw block Vt_s = V_s B_s; step s also
+                                  // subtracts V_{s-1} B_s^T
+  double Rp[KMAX * KMAX];         // B_{s-1}
+  double rci[KMAX];               // 1 / diagonal of B_s
+  double rpi[KMAX];               // 1 / diagonal of B_{s-1}
   double H[KMAX * KMAX];          // H_s
   double tot[NVMAX];              // start kernel: Gram matrix of the start block, ||r||^2, ||B||^2
 };
@@ -93,7 +95,7 @@ struct Args {
   Coef* co;
   double* histH;           // cap x k*k: H_s
   double* histB;           // cap x k*k: B_{s+1}
-  double* histN;           // cap x k*k: N_s (normalizer of raw block s)
+  double* histN;           // cap x k*k: unused by the kernels (host-side N_s = B_s^{-1})
   const double* G;         // nsteps x k*k: assembly coefficients N_s G_s
   const double* B;         // caller right-hand side, k x ldu
   double* X;               // caller solution, k x ldu
@@ -117,13 +119,41 @@ template <> struct NuT<double> {
 
 template <typename T, int NW = NT / 32>
 struct Smem {
-  T Nc[KMAX][KMAX];
-  T Np[KMAX][KMAX];
-  T Bc[KMAX][KMAX];
+  T Rc[KMAX][KMAX];   // B_s
+  T Rp[KMAX][KMAX];   // B_{s-1}
+  T rci[KMAX];
+  T rpi[KMAX];
   double red[NW * NVMAX];
   double tot[NVMAX];
   int flag;
 };
+
+// v B = x for upper triangular B given with the reciprocals of its diagonal: the basis vector
+// of a raw block row, v = x B^{-1}, by forward substitution (no explicit inverse).
+template <int K, typename T>
+__device__ __forceinline__ void solve_right(const T (&x)[K], const T (&R)[KMAX][KMAX],
+                                            const T (&ri)[KMAX], T (&v)[K]) {
+#pragma unroll
+  for (int l = 0; l < K; ++l) {
+    T y = x[l];
+#pragma unroll
+    for (int p = 0; p < l; ++p) y -= v[p] * R[p][l];
+    v[l] = y * ri[l];
+  }
+}
+
+template <int K, typename T, typename SM>
+__device__ __forceinline__ void load_factors(const Coef* co, SM& sh, bool prev) {
+  for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+    const int p = t / K, q = t % K;
+    sh.Rc[p][q] = T(co->Rc[p * KMAX + q]);
+    if (prev) sh.Rp[p][q] = T(co->Rp[p * KMAX + q]);
+  }
+  if (threadIdx.x < K) {
+    sh.rci[threadIdx.x] = T(co->rci[threadIdx.x]);
+    if (prev) sh.rpi[threadIdx.x] = T(co->rpi[threadIdx.x]);
+  }
+}
 
 // ---- reductions -----------------------------------------------------------------------------
 // GB300 executes FP64 at 1/64 of the FP32 rate, so a CTA-wide tree of FP64 shuffles at the end
@@ -320,13 +350,12 @@ __device__ __forceinline__ bool reduce_last(const double (&v)[NV], S& sh, double
 }
 
 // Last CTA of pass B, warp 0: B_{s+1} = chol(S) (S = B^T B, the N-orthonormal QR of the new
-// block), its inverse as the next normalizer, and their history.  Right-looking Cholesky: per
-// column one reciprocal square root of the pivot (which also gives the inverse's diagonal, so no
-// divisions) and a rank-one update of the trailing block by the lanes; then lane c forms column
-// c of the inverse by back substitution.  Dependent FP64 operations take 100-200 cycles each on
-// GB300, so the FP32 path runs this algebra in two-float arithmetic on the FP32 pipe (about 44
-// significant bits after the Newton step of the square root); the FP64 path uses FP64.  False
-// when a pivot falls to the rounding level of the inner type (the block Krylov space is
+// block), the reciprocals of its diagonal, and its history.  Right-looking Cholesky with the
+// columns in the lanes' registers: per column one reciprocal square root of the pivot and a
+// rank-one update of the trailing block; no explicit inverse (the passes apply B^{-1} by
+// forward substitution).  Dependent FP64 operations take 100-200 cycles each on GB300 and S is
+// an FP32-accurate sum on the FP32 path, so that path factors in FP32; the FP64 path in FP64.
+// False when a pivot falls to the rounding level of the inner type (the block Krylov space is
 // numerically exhausted).
 template <typename R> struct Arith;
 template <> struct Arith<double> {
@@ -340,75 +369,85 @@ template <> struct Arith<double> {
   static __device__ __forceinline__ float lead(V a) { return float(a); }
 };
 template <> struct Arith<float> {
-  using V = FF;
-  static __device__ __forceinline__ V of(double d) { return ff_of(d); }
-  static __device__ __forceinline__ double dbl(V x) { return ff_dbl(x); }
-  static __device__ __forceinline__ V add(V a, V b) { return ff_sum(a, b); }
-  static __device__ __forceinline__ V mul(V a, V b) { return ff_mul(a, b); }
-  static __device__ __forceinline__ V neg(V a) { return ff_neg(a); }
-  static __device__ __forceinline__ V rsq(V a) { return ff_rsqrt(a); }
-  static __device__ __forceinline__ float lead(V a) { return a.hi; }
+  using V = float;
+  static __device__ __forceinline__ V of(double d) { return float(d); }
+  static __device__ __forceinline__ double dbl(V x) { return double(x); }
+  static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+  static __device__ __forceinline__ V mul(V a, V b) { return a * b; }
+  static __device__ __forceinline__ V neg(V a) { return -a; }
+  static __device__ __forceinline__ V rsq(V a) {   // one Newton step on the approximate rsqrt
+    const float r = rsqrtf(a);
+    return r * (1.5f - 0.5f * a * r * r);
+  }
+  static __device__ __forceinline__ float lead(V a) { return a; }
 };
 
+template <typename V>
+__device__ __forceinline__ V shfl_v(V x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+template <>
+__device__ __forceinline__ FF shfl_v<FF>(FF x, int src) {
+  return FF{__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
+}
+
+// Lane l of warp 0 holds column l of S, R and R^{-1} in registers; rows move between lanes by
+// shuffles.  Called by all 32 lanes of warp 0 (lanes >= K carry zero columns).
 template <int K, typename T, typename SM>
 __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
   using AR = Arith<T>;
   using V = typename AR::V;
-  __shared__ V A[KMAX][KMAX], R[KMAX][KMAX], Ri[KMAX][KMAX], rinv[KMAX];
-  __shared__ int bad;
   const int lane = threadIdx.x & 31;
   double tr = 0.0;
+#pragma unroll
   for (int p = 0; p < K; ++p) tr += sh.tot[p * K - p * (p - 1) / 2];
-  if (lane < K) {
+  V col[K], Rc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
     // packed upper triangle, row by row: entry (p, q), q >= p, at p K - p (p - 1) / 2 + q - p
-    for (int q = 0; q < K; ++q) {
-      const int p0 = lane < q ? lane : q, q0 = lane < q ? q : lane;
-      A[lane][q] = AR::of(sh.tot[p0 * K - p0 * (p0 - 1) / 2 + (q0 - p0)]);
-      R[lane][q] = AR::of(0.0);
-    }
+    const int p0 = i < lane ? i : lane, q0 = i < lane ? lane : i;
+    col[i] = lane < K ? AR::of(sh.tot[p0 * K - p0 * (p0 - 1) / 2 + (q0 - p0)]) : AR::of(0.0);
+    Rc[i] = AR::of(0.0);
   }
-  if (lane == 0) bad = 0;
-  __syncwarp();
   const float thr = float((sizeof(T) == 4 ? 1e-12 : 1e-26) * tr);
+  V rinv[K];
+  bool bad = false;
+#pragma unroll
   for (int j = 0; j < K; ++j) {
-    if (lane == j) {
-      V d = A[j][j];
-      if (!(AR::lead(d) > thr) || !isfinite(AR::lead(d))) {
-        bad = 1;
-        d = AR::of(1.0);
-      }
-      const V r = AR::rsq(d);
-      R[j][j] = AR::mul(d, r);
-      rinv[j] = r;
+    V d = shfl_v(col[j], j);                       // trailing pivot, held by lane j
+    if (!(AR::lead(d) > thr) || !isfinite(AR::lead(d))) {
+      bad = true;
+      d = AR::of(1.0);
     }
-    __syncwarp();
-    if (lane > j && lane < K) R[j][lane] = AR::mul(A[j][lane], rinv[j]);
-    __syncwarp();
-    if (lane > j && lane < K)   // trailing update of column `lane`, rows j+1..lane
-      for (int i = j + 1; i <= lane; ++i) A[i][lane] = AR::add(A[i][lane], AR::neg(AR::mul(R[j][i], R[j][lane])));
-    __syncwarp();
+    const V r = AR::rsq(d);
+    rinv[j] = r;
+    Rc[j] = lane > j ? AR::mul(col[j], r) : (lane == j ? AR::mul(d, r) : AR::of(0.0));
+#pragma unroll
+    for (int i = j + 1; i < K; ++i) {              // col[i] -= R[j][i] R[j][lane]
+      const V rji = shfl_v(Rc[j], i);
+      col[i] = AR::add(col[i], AR::neg(AR::mul(rji, Rc[j])));
+    }
   }
   if (bad) return false;
-  if (lane < K) {   // column `lane` of R^{-1} by back substitution
-    const int c = lane;
-    for (int r = K - 1; r >= 0; --r) {
-      V v = AR::of(r == c ? 1.0 : 0.0);
-      for (int p = r + 1; p <= c; ++p) v = AR::add(v, AR::neg(AR::mul(R[r][p], Ri[p][c])));
-      Ri[r][c] = r > c ? AR::of(0.0) : AR::mul(v, rinv[r]);
+  if (lane < K) {
+    double* hb = a.histB + (size_t)(s - 1) * K * K;
+    Coef* co = a.co;
+    double prev[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) prev[i] = co->Rc[i * KMAX + lane];
+    const double prevri = co->rci[lane];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const double rb = AR::dbl(Rc[i]);
+      hb[i * K + lane] = rb;
+      co->Rp[i * KMAX + lane] = prev[i];
+      co->Rc[i * KMAX + lane] = rb;
     }
-  }
-  __syncwarp();
-  double* hb = a.histB + (size_t)(s - 1) * K * K;
-  double* hn = a.histN + (size_t)s * K * K;
-  Coef* co = a.co;
-  for (int t = lane; t < K * K; t += 32) {
-    const int p = t / K, q = t % K;
-    const double rb = AR::dbl(R[p][q]), ri = AR::dbl(Ri[p][q]);
-    hb[t] = rb;
-    hn[t] = ri;
-    co->Bc[p * KMAX + q] = rb;
-    co->Np[p * KMAX + q] = co->Nc[p * KMAX + q];
-    co->Nc[p * KMAX + q] = ri;
+    co->rpi[lane] = prevri;
+    // rinv[j] is uniform over the lanes: lane j publishes its own
+    double own = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j == lane) own = AR::dbl(rinv[j]);
+    co->rci[lane] = own;
   }
   return true;
 }
@@ -478,12 +517,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_lz_a(const Args 
   constexpr int NS = K * (K + 1) / 2;
   if (a.ctl->done != RUNNING) return;
   const int s = a.ctl->step + 1;
-  for (int t = threadIdx.x; t < K * K; t += NT) {
-    const int p = t / K, q = t % K;
-    sh.Nc[p][q] = T(a.co->Nc[p * KMAX + q]);
-    sh.Np[p][q] = T(a.co->Np[p * KMAX + q]);
-    sh.Bc[p][q] = T(a.co->Bc[p * KMAX + q]);
-  }
+  load_factors<K, T>(a.co, sh, s > 1);
   __syncthreads();
   const OpData& op = a.op;
   const int64_t ld = op.ld, n = op.n;
@@ -525,35 +559,22 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_lz_a(const Args 
 #pragma unroll
         for (int j = 0; j < K; ++j) lap[j] += v[t] * __ldg(cur + j * ld + col[t]);
     }
-    T vv[K], w[K];
+    T vv[K], qv[K], w[K];
     const T ninv = NuT<T>::inv(a, i), nu = NuT<T>::nu(a, i);
+    solve_right<K, T>(u, sh.Rc, sh.rci, vv);
+    solve_right<K, T>(lap, sh.Rc, sh.rci, qv);
 #pragma unroll
-    for (int l = 0; l < K; ++l) {
-      T x = T(0), q = T(0);
-#pragma unroll
-      for (int p = 0; p <= l; ++p) {
-        x += u[p] * sh.Nc[p][l];
-        q += lap[p] * sh.Nc[p][l];
-      }
-      vv[l] = x;
-      w[l] = q * ninv;
-    }
+    for (int l = 0; l < K; ++l) w[l] = qv[l] * ninv;
     if (s > 1) {
       T uo[K], vo[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) uo[j] = __ldg(prev + j * ld + i);
+      solve_right<K, T>(uo, sh.Rp, sh.rpi, vo);
 #pragma unroll
       for (int l = 0; l < K; ++l) {
         T x = T(0);
 #pragma unroll
-        for (int p = 0; p <= l; ++p) x += uo[p] * sh.Np[p][l];
-        vo[l] = x;
-      }
-#pragma unroll
-      for (int l = 0; l < K; ++l) {
-        T x = T(0);
-#pragma unroll
-        for (int p = l; p < K; ++p) x += vo[p] * sh.Bc[l][p];
+        for (int p = l; p < K; ++p) x += vo[p] * sh.Rc[l][p];
         w[l] -= x;
       }
     }
@@ -594,11 +615,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_lz_b(const Args 
   constexpr int NS = K * (K + 1) / 2;
   if (a.ctl->done != RUNNING) return;
   const int s = a.ctl->step + 1;
-  for (int t = threadIdx.x; t < K * K; t += NT) {
-    const int p = t / K, q = t % K;
-    sh.Nc[p][q] = T(a.co->Nc[p * KMAX + q]);
-    Hs[p][q] = T(a.co->H[p * KMAX + q]);
-  }
+  load_factors<K, T>(a.co, sh, false);
+  for (int t = threadIdx.x; t < K * K; t += NT) Hs[t / K][t % K] = T(a.co->H[(t / K) * KMAX + t % K]);
   __syncthreads();
   const int64_t ld = a.op.ld, n = a.op.n;
   const T* cur = (const T*)a.basis + (size_t)(s - 1) * a.bstride;
@@ -619,13 +637,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_lz_b(const Args 
       u[j] = __ldg(cur + j * ld + i);
       ww[j] = __ldg(W + j * ld + i);
     }
-#pragma unroll
-    for (int l = 0; l < K; ++l) {
-      T x = T(0);
-#pragma unroll
-      for (int p = 0; p <= l; ++p) x += u[p] * sh.Nc[p][l];
-      vv[l] = x;
-    }
+    solve_right<K, T>(u, sh.Rc, sh.rci, vv);
 #pragma unroll
     for (int l = 0; l < K; ++l) {
       T x = ww[l];
@@ -747,12 +759,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
   __shared__ __align__(8) Pipe<NST_A> ps;
   if (a.ctl->done != RUNNING) return;
   const int s = a.ctl->step + 1;
-  for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
-    const int p = t / K, q = t % K;
-    sh.Nc[p][q] = float(a.co->Nc[p * KMAX + q]);
-    sh.Np[p][q] = float(a.co->Np[p * KMAX + q]);
-    sh.Bc[p][q] = float(a.co->Bc[p * KMAX + q]);
-  }
+  load_factors<K, float>(a.co, sh, s > 1);
   if (threadIdx.x == 0) pipe_init(ps);
   __syncthreads();
   const OpData& op = a.op;
@@ -832,32 +839,21 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
 #pragma unroll
         for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
       const float ninv = stage[L::NUINV * TILE_PX + t], nu = stage[L::NU * TILE_PX + t];
-      float vv[K], w[K];
+      float vv[K], qv[K], w[K];
+      solve_right<K, float>(uu, sh.Rc, sh.rci, vv);
+      solve_right<K, float>(lap, sh.Rc, sh.rci, qv);
 #pragma unroll
-      for (int l = 0; l < K; ++l) {
-        float x = 0.f, q = 0.f;
-#pragma unroll
-        for (int p = 0; p <= l; ++p) {
-          x += uu[p] * sh.Nc[p][l];
-          q += lap[p] * sh.Nc[p][l];
-        }
-        vv[l] = x;
-        w[l] = q * ninv;
-      }
+      for (int l = 0; l < K; ++l) w[l] = qv[l] * ninv;
       if (s > 1) {
-        float vo[K];
+        float uo[K], vo[K];
+#pragma unroll
+        for (int p = 0; p < K; ++p) uo[p] = stage[(L::PREV + p) * TILE_PX + t];
+        solve_right<K, float>(uo, sh.Rp, sh.rpi, vo);
 #pragma unroll
         for (int l = 0; l < K; ++l) {
           float x = 0.f;
 #pragma unroll
-          for (int p = 0; p <= l; ++p) x += stage[(L::PREV + p) * TILE_PX + t] * sh.Np[p][l];
-          vo[l] = x;
-        }
-#pragma unroll
-        for (int l = 0; l < K; ++l) {
-          float x = 0.f;
-#pragma unroll
-          for (int p = l; p < K; ++p) x += vo[p] * sh.Bc[l][p];
+          for (int p = l; p < K; ++p) x += vo[p] * sh.Rc[l][p];
           w[l] -= x;
         }
       }
@@ -906,11 +902,9 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
   __shared__ __align__(8) Pipe<NST_B> ps;
   if (a.ctl->done != RUNNING) return;
   const int s = a.ctl->step + 1;
-  for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
-    const int p = t / K, q = t % K;
-    sh.Nc[p][q] = float(a.co->Nc[p * KMAX + q]);
-    Hs[p][q] = float(a.co->H[p * KMAX + q]);
-  }
+  load_factors<K, float>(a.co, sh, false);
+  for (int t = threadIdx.x; t < K * K; t += blockDim.x)
+    Hs[t / K][t % K] = float(a.co->H[(t / K) * KMAX + t % K]);
   if (threadIdx.x == 0) pipe_init(ps);
   __syncthreads();
   const int64_t ld = a.op.ld, n = a.op.n;
@@ -962,13 +956,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
       __syncwarp();
       if (lane == 0) tma::mbar_arrive(&ps.empty[st]);
       consumed = u + 1;
-#pragma unroll
-      for (int l = 0; l < K; ++l) {
-        float x = 0.f;
-#pragma unroll
-        for (int p = 0; p <= l; ++p) x += uu[p] * sh.Nc[p][l];
-        vv[l] = x;
-      }
+      solve_right<K, float>(uu, sh.Rc, sh.rci, vv);
 #pragma unroll
       for (int l = 0; l < K; ++l) {
         float x = ww[l];
@@ -1828,7 +1816,7 @@ int run(sylv_handle h, const OpData& op, Cache& C, const double* B, double* X, i
       }
       if (outer >= o.max_outer || total >= o.maxit) break;
       // start block: Gram matrix of C = Yhat U, column scaling, Cholesky QR
-      double Gm[KMAX * KMAX], Sh[KMAX * KMAX], Rb[KMAX * KMAX], Rbi[KMAX * KMAX], sc[KMAX];
+      double Gm[KMAX * KMAX], Sh[KMAX * KMAX], Rb[KMAX * KMAX], sc[KMAX];
       int t = 0;
       for (int p = 0; p < k; ++p)
         for (int q = p; q < k; ++q, ++t) Gm[p * k + q] = Gm[q * k + p] = w.h_tot[t];
@@ -1846,16 +1834,18 @@ int run(sylv_handle h, const OpData& op, Cache& C, const double* B, double* X, i
         status = SYLV_E_BREAKDOWN;
         break;
       }
-      hinv_upper(k, Rb, Rbi);
+      // the start block C = Yhat U is raw block 1: C = V_1 B_1 with B_1 = Rb Sigma, which is
+      // also B_0 U (Yhat = V_1 Rb Sigma U^{-1})
       Coef init;
       std::memset(&init, 0, sizeof(init));
-      double N1[KMAX * KMAX], cU[KMAX * KMAX];
-      for (int p = 0; p < k; ++p)
+      double cU[KMAX * KMAX];
+      for (int p = 0; p < k; ++p) {
         for (int q = 0; q < k; ++q) {
-          N1[p * k + q] = Rbi[p * k + q] / sc[p];           // Sigma^{-1} Rb^{-1}
-          init.Nc[p * KMAX + q] = N1[p * k + q];
-          cU[p * k + q] = Rb[p * k + q] * sc[q];            // B_0 U = Rb Sigma
+          cU[p * k + q] = Rb[p * k + q] * sc[q];
+          init.Rc[p * KMAX + q] = cU[p * k + q];
         }
+        init.rci[p] = 1.0 / cU[p * k + p];
+      }
       double nB0 = 0.0;   // ||B_0||_F^2, B_0 = (B_0 U) U^{-1}
       for (int p = 0; p < k; ++p)
         for (int q = 0; q < k; ++q) {
@@ -1872,7 +1862,6 @@ int run(sylv_handle h, const OpData& op, Cache& C, const double* B, double* X, i
       std::memset(&c0, 0, sizeof(c0));
       c0.cap = std::min(w.cap_blocks - 1, o.maxit - total);
       LK(cudaMemcpyAsync(w.co, &init, sizeof(Coef) - sizeof(init.tot), cudaMemcpyHostToDevice, s));
-      LK(cudaMemcpyAsync(a.histN, N1, kk * sizeof(double), cudaMemcpyHostToDevice, s));
       *w.h_ctl = c0;
       LK(cudaMemcpyAsync(w.ctl, w.h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
       ++outer;
@@ -1957,10 +1946,12 @@ int run(sylv_handle h, const OpData& op, Cache& C, const double* B, double* X, i
         LK(cudaMemcpyAsync(w.h_hist + seen * kk, a.histH + seen * kk,
                            (size_t)(j - seen) * kk * sizeof(double), cudaMemcpyDeviceToHost, s));
       // coefficients on the host, then X += sum_s Vt_s G'_s
-      LK(cudaMemcpyAsync(w.h_hist + 2 * cb, a.histN, (size_t)j * kk * sizeof(double),
-                         cudaMemcpyDeviceToHost, s));
       LK(cudaStreamSynchronize(s));
-      coefficients(k, j, C, cU, w.h_hist, w.h_hist + cb, w.h_hist + 2 * cb, w.h_G);
+      // normalizers N_s = B_s^{-1} of the raw blocks (B_1 = Rb Sigma, B_s = recorded B for s > 1)
+      double* hN = w.h_hist + 2 * cb;
+      for (int t = 0; t < j; ++t)
+        hinv_upper(k, t == 0 ? cU : w.h_hist + cb + (size_t)(t - 1) * kk, hN + (size_t)t * kk);
+      coefficients(k, j, C, cU, w.h_hist, w.h_hist + cb, hN, w.h_G);
       LK(cudaMemcpyAsync((void*)a.G, w.h_G, (size_t)j * kk * sizeof(double), cudaMemcpyHostToDevice, s));
       a.nsteps = j;
       if (prof) LK(cudaEventRecord(w.evs0, s));
