@@ -5,7 +5,7 @@ They pin ``model``/``solve`` and, at full sizes, the GPU solver, because each re
 eq. mu* by a different route:
 
 * ``lattice_homogeneous``: periodic lattice, noise constant per channel.  A 2-D DFT
-  diagonalises L (eigenvalues 4 - 2cos(2 pi p/H) - 2cos(2 pi q/W)) and hence every Q_j at
+  diagonalises L (eigenvalues 4 - 2cos(2 pi p/H) - 2cos(2 pi q/W)), hence L^2 and every Q_j at
   once; each Fourier mode leaves a k x k system.
 * ``sphere_latitude_noise``: latitude-longitude sphere, noise depending on the row only.  A DFT
   in longitude decouples the modes; each is a symmetric block-tridiagonal system in latitude
@@ -23,14 +23,16 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 
-def lattice_homogeneous(H, W, tau, kappa, A, d, Y):
-    """X (k, H*W) for the periodic lattice with d_ci = d[c]; Y is (m, H*W)."""
+def lattice_homogeneous(H, W, tau, kappa, A, d, Y, power=1):
+    """X (k, H*W) for the periodic lattice with d_ci = d[c]; Y is (m, H*W).  ``power`` = 2
+    takes the prior shape L^2 (the intrinsic GMRF of App. C), whose modes are the squares of
+    the Laplacian's."""
     m, k = A.shape
     Yh = np.fft.fft2(np.asarray(Y, np.float64).reshape(m, H, W), axes=(1, 2))
     # right-hand side in Fourier space: b_j = sum_c a_cj d_c y_c
     bh = np.einsum("cj,c,chw->jhw", A, np.asarray(d, np.float64), Yh)
     lam = (4.0 - 2.0 * np.cos(2 * np.pi * np.arange(H) / H)[:, None]
-           - 2.0 * np.cos(2 * np.pi * np.arange(W) / W)[None, :])
+           - 2.0 * np.cos(2 * np.pi * np.arange(W) / W)[None, :]) ** power
     data = np.einsum("c,cj,cl->jl", np.asarray(d, np.float64), A, A)
     M = np.broadcast_to(data, (H, W, k, k)).copy()
     for j in range(k):

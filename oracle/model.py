@@ -101,6 +101,28 @@ def laplacian_bruteforce(H, W, kind):
     return L
 
 
+def igmrf_base(L):
+    """Precision shape of the intrinsic GMRF of App. C, Q = phi D^T D with D the Laplacian
+    (reading of Sec. 3 / App. C: the rank N - 1 stated there holds for the Laplacian): L^T L = L^2
+    as a sparse product."""
+    L = sp.csr_matrix(L)
+    return (L.T @ L).tocsr()
+
+
+def igmrf_bruteforce(Ld):
+    """(L^T L)_ij = sum_k L_ki L_kj by explicit loops over a dense L (tiny inputs only)."""
+    Ld = np.asarray(Ld, np.float64)
+    n = Ld.shape[0]
+    Q = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            acc = 0.0
+            for k in range(n):
+                acc += Ld[k, i] * Ld[k, j]
+            Q[i, j] = acc
+    return Q
+
+
 def laplacian_from_csr(rowptr, col, val, n):
     return sp.csr_matrix((np.asarray(val, np.float64), np.asarray(col), np.asarray(rowptr)),
                          shape=(n, n))

@@ -3,8 +3,9 @@
 This module is shared by the CPU oracle (``oracle/``), the tests and ``bench.py``.  It holds
 input synthesis only: pixel graphs and their Laplacian in CSR form (the neighbour structure a
 user of the solver supplies, Sec. 2.2 / App. C), noise-precision maps, spectral parameters and
-simulated observations.  It computes no part of the solve: no mixing matrix used by a solver,
-no right-hand side, no operator application.
+simulated observations, and the mixing matrix and channel weights App. B prints (input data as
+printed).  It computes no part of the solve: no mixing matrix derived from a model, no
+right-hand side, no operator application.
 """
 
 from .grids import (  # noqa: F401
@@ -13,6 +14,7 @@ from .grids import (  # noqa: F401
     latlong_sphere,
     laplacian_csr_from_edges,
 )
+from .physical import PLANCK_A_PRINTED, PLANCK_T_PRINTED  # noqa: F401
 from .problems import (  # noqa: F401
     PLANCK_NU,
     Problem,
@@ -20,5 +22,6 @@ from .problems import (  # noqa: F401
     config_problem,
     batch_problems,
     separable_problem,
+    igmrf_problem,
     CONFIG_SEED_BASE,
 )

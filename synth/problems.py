@@ -42,6 +42,8 @@ class Problem:
     X_true: np.ndarray       # (k, n) float64 simulated source maps
     tol: float = 1e-8
     meta: dict = field(default_factory=dict)
+    A: Optional[np.ndarray] = None   # (m, k) explicit mixing matrix (else the power law)
+    prior: str = "gmrf"              # "gmrf": Q_j = tau_j (kappa_j^2 W + L); "igmrf": L^2 for L
 
     @property
     def n(self) -> int:
@@ -176,6 +178,39 @@ def separable_problem(config_id: int = 2, *, scale: Optional[int] = None, kappa0
                         beta_draw=(-3.0, 2.0), noise="separable",
                         nrhs=nrhs or (8 if config_id == 5 else 1), tol=1e-8,
                         meta={"config": config_id, "separable": True})
+
+
+def igmrf_problem(config_id: int = 2, *, scale: Optional[int] = None, phi: float = 1e6,
+                  kappa0: float = 0.0, nrhs: Optional[int] = None) -> Problem:
+    """The paper's own model on the grid of workload ``config_id`` (2 or 4): the four physical
+    sources (CMB, synchrotron, dust, free-free) with the mixing matrix and channel weights T
+    printed in App. B over the nine Planck channels, noise precision d_ci = t_c nu_i with a
+    log-normal per-pixel map nu (C = T kron N), and the intrinsic GMRF prior of App. C,
+    Q_j = phi_j L^2 (kappa0 = 0; kappa0 > 0 adds kappa0^2 W).  The sky is the physical mixing of
+    smooth source maps with amplitudes of order 1e-3 (the scale where T's weights and the prior
+    phi ~ 1e6 are comparable), plus white noise of precision d_ci."""
+    from .physical import PLANCK_A_PRINTED, PLANCK_T_PRINTED
+    sides = {2: (1024, 2048), 4: (512, 1024)}
+    if config_id not in sides:
+        raise ValueError(f"no IGMRF variant of config {config_id}")
+    H, W = sides[config_id]
+    s = 1 if scale is None else int(scale)
+    g = _grid("sphere", H // s, W // s)
+    A = PLANCK_A_PRINTED.copy()
+    m, k = A.shape
+    R = nrhs or 1
+    rng = np.random.Generator(np.random.PCG64(CONFIG_SEED_BASE + 40 + config_id))
+    nu_pix = np.exp(0.3 * rng.standard_normal(g.n))
+    D = PLANCK_T_PRINTED[:, None] * nu_pix[None, :]
+    corr = max(2.0, min(g.H, g.W) / 16.0)
+    S = 1e-3 * _smooth_fields(rng, k, g.H, g.W, corr)
+    sky = A @ S
+    Yobs = np.empty((R, m, g.n))
+    for r in range(R):
+        Yobs[r] = sky + rng.standard_normal((m, g.n)) / np.sqrt(D)
+    return Problem(f"sphere{g.H}x{g.W}_k{k}_m{m}_igmrf_physical", g, k, m,
+                   np.full(k, float(phi)), np.full(k, float(kappa0)), _nu_for(m), np.zeros(k),
+                   D, Yobs, S, 1e-8, {"config": config_id, "igmrf": True}, A=A, prior="igmrf")
 
 
 def batch_problems(count=64, side_range=(128, 1024), *, seed=None) -> List[Problem]:
