@@ -463,8 +463,11 @@ def run_ours(args, rank, world, local_rank):
 
 def make_operator(p, device=None):
     from paper_2204_08057_gb300.operator import Operator
+    A = getattr(p, "A", None)
     return Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
-                    kappa=p.kappa, nu=p.nu, beta=p.beta)
+                    kappa=p.kappa, nu=None if A is not None else p.nu,
+                    beta=None if A is not None else p.beta, A=A,
+                    prior=getattr(p, "prior", "gmrf"))
 
 
 def run_profile_case(args):

@@ -63,6 +63,10 @@ enum { SYLV_PRECOND_NONE = 0, SYLV_PRECOND_BLOCK_JACOBI = 1 };
 #define SYLV_MAX_M 16     /* channels                                  */
 #define SYLV_MAX_DEGREE 8 /* off-diagonal entries per Laplacian row    */
 #define SYLV_MAX_RHS 16   /* right-hand sides per system in one solve  */
+#define SYLV_MAX_PRIOR_DEGREE 24 /* off-diagonals per row of the prior shape L^2 */
+
+#define SYLV_PRIOR_GMRF 0
+#define SYLV_PRIOR_IGMRF 1
 
 /* Problem definition (Sec. 2.1-2.2). */
 typedef struct {
@@ -83,6 +87,13 @@ typedef struct {
   const double* A;         /* host, m x k row-major: explicit mixing matrix, or NULL to  */
                            /* use a_cj = (nu_c / nu0)^beta_j                             */
   double nu0;              /* reference frequency of the power law; 0 means 100 GHz     */
+  int32_t prior;           /* SYLV_PRIOR_GMRF: Q_j = tau_j (kappa_j^2 W + L);            */
+                           /* SYLV_PRIOR_IGMRF: Q_j = tau_j (kappa_j^2 W + L^2), the      */
+                           /* intrinsic GMRF phi_j D^T D of App. C with D = L when        */
+                           /* kappa_j = 0 (then G is SPD iff A has full column rank);    */
+                           /* the library forms L^2 on the device (at most                */
+                           /* SYLV_MAX_PRIOR_DEGREE off-diagonals per row)                */
+  int32_t reserved;        /* 0                                                          */
 } sylv_problem;
 
 /* Solver options.  sylv_opts_default() fills the defaults given in brackets. */

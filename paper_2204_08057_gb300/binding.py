@@ -28,6 +28,8 @@ SYLV_PREC_F64 = 0
 SYLV_PREC_MIXED = 1
 SYLV_PRECOND_NONE = 0
 SYLV_PRECOND_BLOCK_JACOBI = 1
+SYLV_PRIOR_GMRF = 0
+SYLV_PRIOR_IGMRF = 1
 MAX_K, MAX_M, MAX_DEGREE, MAX_RHS = 8, 16, 8, 16
 
 EXPORTED = ["sylv_opts_default", "sylv_create", "sylv_rhs", "sylv_apply", "sylv_solve",
@@ -41,7 +43,8 @@ class sylv_problem(ctypes.Structure):
                 ("nnz", c_int64), ("w", c_void_p), ("D", c_void_p),
                 ("tau", POINTER(c_double)), ("kappa", POINTER(c_double)),
                 ("nu", POINTER(c_double)), ("beta", POINTER(c_double)),
-                ("A", POINTER(c_double)), ("nu0", c_double)]
+                ("A", POINTER(c_double)), ("nu0", c_double), ("prior", c_int32),
+                ("reserved", c_int32)]
 
 
 class sylv_opts(ctypes.Structure):
@@ -177,14 +180,15 @@ def make_opts(**kw):
 
 
 def sylv_create(*, n, k, m, ld, L_rowptr, L_col, L_val, D, tau, kappa, nu=None, beta=None,
-                A=None, w=None, nu0=0.0, stream=None):
+                A=None, w=None, nu0=0.0, prior=0, stream=None):
     """Returns an opaque handle (int).  Device tensors: L_rowptr (int32, n+1), L_col (int32),
     L_val (float64), D (float64, m x ld), w (float64, n) or None.  Host: tau, kappa (k),
-    nu (m), beta (k), A (m x k) or None."""
+    nu (m), beta (k), A (m x k) or None.  prior: SYLV_PRIOR_GMRF or SYLV_PRIOR_IGMRF."""
     import torch
     nnz = int(L_col.numel())
     p = sylv_problem()
     p.n, p.k, p.m, p.ld, p.nnz, p.nu0 = int(n), int(k), int(m), int(ld), nnz, float(nu0)
+    p.prior = int(prior)
     p.L_rowptr = _dev_ptr(L_rowptr, torch.int32, n + 1, "L_rowptr")
     p.L_col = _dev_ptr(L_col, torch.int32, nnz, "L_col")
     p.L_val = _dev_ptr(L_val, torch.float64, nnz, "L_val")

@@ -1006,6 +1006,65 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return bail(cuda_fail(e, "operator set-up"));
   if (hflags[0]) return bail(fail(SYLV_E_INVALID, "D (>= 0) or w (> 0) has invalid entries"));
+  if (p->prior == SYLV_PRIOR_IGMRF) {
+    // intrinsic GMRF prior shape: replace L by L^2 (formed from the ELL copy of L)
+    unsigned int width = 0;
+    if ((e = cudaMemsetAsync(dflags, 0, sizeof(unsigned int), s)) != cudaSuccess ||
+        (e = launch_square_count(op, dflags, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&width, dflags, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return bail(cuda_fail(e, "prior L^2 (width)"));
+    if (width > (unsigned)SYLV_MAX_PRIOR_DEGREE)
+      return bail(fail(SYLV_E_UNSUPPORTED, "L^2 has more than SYLV_MAX_PRIOR_DEGREE "
+                                           "off-diagonals in a row"));
+    const int E2 = (int)width;
+    int32_t* sq_col = nullptr;
+    float *sq_val32 = nullptr, *sq_diag32 = nullptr;
+    double *sq_val64 = nullptr, *sq_diag64 = nullptr;
+    auto drop = [&]() {
+      cudaFree(sq_col);
+      cudaFree(sq_val32);
+      cudaFree(sq_val64);
+      cudaFree(sq_diag32);
+      cudaFree(sq_diag64);
+    };
+    const size_t w2 = std::max<size_t>(E2, 1);
+    if ((e = dalloc(&sq_col, w2 * ld * sizeof(int32_t))) != cudaSuccess ||
+        (e = dalloc(&sq_val32, w2 * ld * sizeof(float))) != cudaSuccess ||
+        (e = dalloc(&sq_val64, w2 * ld * sizeof(double))) != cudaSuccess ||
+        (e = dalloc(&sq_diag32, ld * sizeof(float))) != cudaSuccess ||
+        (e = dalloc(&sq_diag64, ld * sizeof(double))) != cudaSuccess ||
+        (e = cudaMemsetAsync(sq_col, 0, w2 * ld * sizeof(int32_t), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(sq_val32, 0, w2 * ld * sizeof(float), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(sq_val64, 0, w2 * ld * sizeof(double), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(sq_diag32, 0, ld * sizeof(float), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(sq_diag64, 0, ld * sizeof(double), s)) != cudaSuccess ||
+        (e = launch_square_fill(op, E2, sq_col, sq_val32, sq_val64, sq_diag32, sq_diag64, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      drop();
+      return bail(cuda_fail(e, "prior L^2"));
+    }
+    cudaFree(h->ell_col);
+    cudaFree(h->ell_val32);
+    cudaFree(h->ell_val64);
+    cudaFree(h->diag32);
+    cudaFree(h->diag64);
+    h->ell_col = sq_col;
+    h->ell_val32 = sq_val32;
+    h->ell_val64 = sq_val64;
+    h->diag32 = sq_diag32;
+    h->diag64 = sq_diag64;
+    op.E = E2;
+    op.ell_col = sq_col;
+    op.ell_val32 = sq_val32;
+    op.ell_val64 = sq_val64;
+    op.diag32 = sq_diag32;
+    op.diag64 = sq_diag64;
+  } else if (p->prior != SYLV_PRIOR_GMRF) {
+    return bail(fail(SYLV_E_INVALID, "prior must be SYLV_PRIOR_GMRF or SYLV_PRIOR_IGMRF"));
+  }
   // FP64 pixel blocks and their factors (FP64 operator and preconditioner)
   const size_t nb = (size_t)p->k * (p->k + 1) / 2;
   if ((e = dalloc(&h->blk64, nb * ld * sizeof(double))) != cudaSuccess ||

@@ -73,6 +73,89 @@ __global__ void k_ell_build(int64_t n, int64_t ld, const int32_t* __restrict__ r
   diag64[i] = dg;
 }
 
+// Row i of L L for a symmetric L held as diagonal + sliced ELL (padding slots point at the row
+// itself): the prior shape L^T L = L^2 of the intrinsic GMRF (App. C).  Row i collects
+// L_ii row_i(L) + sum_e L_{i c_e} row_{c_e}(L); the off-diagonal entries are merged by column
+// and sorted ascending, the diagonal is returned apart.  Returns the number of off-diagonals.
+constexpr int SQ_MAX = 1 + EMAX + EMAX * EMAX;
+
+__device__ int square_row(int64_t ld, int E, const int32_t* __restrict__ ell_col,
+                          const double* __restrict__ ell_val, const double* __restrict__ diag,
+                          int64_t i, int32_t* cols, double* vals, double* dg_out) {
+  int cnt = 0;
+  auto add = [&](int32_t c, double v) {
+    for (int t = 0; t < cnt; ++t)
+      if (cols[t] == c) {
+        vals[t] += v;
+        return;
+      }
+    cols[cnt] = c;
+    vals[cnt] = v;
+    ++cnt;
+  };
+  const double di = diag[i];
+  double dg = di * di;
+  for (int e = 0; e < E; ++e) {
+    const int32_t c = ell_col[e * ld + i];
+    if ((int64_t)c == i) continue;
+    const double v = ell_val[e * ld + i];
+    add(c, di * v);                       // L_ii L_ic
+    add(c, v * diag[c]);                  // L_ic L_cc
+    for (int f = 0; f < E; ++f) {         // L_ic L_{c c2}
+      const int32_t c2 = ell_col[f * ld + c];
+      if (c2 == c) continue;
+      const double v2 = ell_val[f * ld + c];
+      if ((int64_t)c2 == i) dg += v * v2;
+      else add(c2, v * v2);
+    }
+  }
+  // insertion sort by column: a fixed order for the sums that use the row
+  for (int a = 1; a < cnt; ++a) {
+    const int32_t c = cols[a];
+    const double v = vals[a];
+    int b = a - 1;
+    while (b >= 0 && cols[b] > c) {
+      cols[b + 1] = cols[b];
+      vals[b + 1] = vals[b];
+      --b;
+    }
+    cols[b + 1] = c;
+    vals[b + 1] = v;
+  }
+  *dg_out = dg;
+  return cnt;
+}
+
+__global__ void k_square_count(int64_t n, int64_t ld, int E, const int32_t* __restrict__ ell_col,
+                               const double* __restrict__ ell_val,
+                               const double* __restrict__ diag, unsigned int* width) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t cols[SQ_MAX];
+  double vals[SQ_MAX], dg;
+  const int cnt = square_row(ld, E, ell_col, ell_val, diag, i, cols, vals, &dg);
+  atomicMax(width, (unsigned int)cnt);
+}
+
+__global__ void k_square_fill(int64_t n, int64_t ld, int E, const int32_t* __restrict__ ell_col,
+                              const double* __restrict__ ell_val, const double* __restrict__ diag,
+                              int E2, int32_t* sq_col, float* sq_val32, double* sq_val64,
+                              float* sq_diag32, double* sq_diag64) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t cols[SQ_MAX];
+  double vals[SQ_MAX], dg;
+  const int cnt = square_row(ld, E, ell_col, ell_val, diag, i, cols, vals, &dg);
+  for (int e = 0; e < E2; ++e) {
+    const bool real = e < cnt;
+    sq_col[e * ld + i] = real ? cols[e] : (int32_t)i;
+    sq_val64[e * ld + i] = real ? vals[e] : 0.0;
+    sq_val32[e * ld + i] = real ? (float)vals[e] : 0.0f;
+  }
+  sq_diag64[i] = dg;
+  sq_diag32[i] = (float)dg;
+}
+
 // Copies rows x n values (pitch ld) into FP32 and FP64 buffers and checks them (>= 0, or > 0
 // if positive, and finite).
 __global__ void k_convert_check(const double* __restrict__ src, int64_t rows, int64_t n,
@@ -295,6 +378,21 @@ cudaError_t launch_ell_build(const OpData& op, const int32_t* rowptr, const int3
                              cudaStream_t s) {
   k_ell_build<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(
       op.n, op.ld, rowptr, col, val, E, ell_col, ell_val32, ell_val64, diag32, diag64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_square_count(const OpData& op, unsigned int* width, cudaStream_t s) {
+  k_square_count<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(
+      op.n, op.ld, op.E, op.ell_col, op.ell_val64, op.diag64, width);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_square_fill(const OpData& op, int E2, int32_t* sq_col, float* sq_val32,
+                               double* sq_val64, float* sq_diag32, double* sq_diag64,
+                               cudaStream_t s) {
+  k_square_fill<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(
+      op.n, op.ld, op.E, op.ell_col, op.ell_val64, op.diag64, E2, sq_col, sq_val32, sq_val64,
+      sq_diag32, sq_diag64);
   return cudaGetLastError();
 }
 

@@ -161,6 +161,12 @@ cudaError_t launch_ell_build(const OpData& op, const int32_t* rowptr, const int3
                              const double* val, int32_t* ell_col, float* ell_val32,
                              double* ell_val64, float* diag32, double* diag64, int E,
                              cudaStream_t s);
+// Intrinsic GMRF prior shape: the ELL width of L^2 (atomic max into *width), then L^2 itself
+// into new ELL arrays of that width and a new diagonal.
+cudaError_t launch_square_count(const OpData& op, unsigned int* width, cudaStream_t s);
+cudaError_t launch_square_fill(const OpData& op, int E2, int32_t* sq_col, float* sq_val32,
+                               double* sq_val64, float* sq_diag32, double* sq_diag64,
+                               cudaStream_t s);
 cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int64_t ld_src,
                                  int64_t ld_dst, float* dst32, double* dst64, int positive,
                                  unsigned int* flags, cudaStream_t s);

@@ -17,12 +17,13 @@ def _to_device(x, dtype, device):
 
 
 class Operator:
-    """G = sum_j (e_j e_j^T) kron tau_j (kappa_j^2 W + L) + sum_c (a_c a_c^T) kron D_c.
+    """G = sum_j (e_j e_j^T) kron tau_j (kappa_j^2 W + L) + sum_c (a_c a_c^T) kron D_c
+    (prior="igmrf": L^2 in place of L, the intrinsic GMRF of App. C).
 
     Vectors are torch tensors of shape (R, k, ld) or (k, ld) (float64 unless noted)."""
 
     def __init__(self, *, rowptr, col, val, D, tau, kappa, nu=None, beta=None, A=None, w=None,
-                 ld=None, nu0=0.0, device="cuda", stream=None):
+                 ld=None, nu0=0.0, prior="gmrf", device="cuda", stream=None):
         import torch
         self.device = torch.device(device)
         D = _to_device(D, torch.float64, self.device)
@@ -52,6 +53,8 @@ class Operator:
                                     L_rowptr=self._rowptr, L_col=self._col, L_val=self._val,
                                     D=self._D, tau=self.tau, kappa=self.kappa, nu=self.nu,
                                     beta=self.beta, A=self.A, w=self._w, nu0=nu0,
+                                    prior={"gmrf": B.SYLV_PRIOR_GMRF,
+                                           "igmrf": B.SYLV_PRIOR_IGMRF}[prior],
                                     stream=stream)
 
     # -- helpers ---------------------------------------------------------------------------

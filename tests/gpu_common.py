@@ -19,18 +19,25 @@ def device_batch(arr, ld, device="cuda"):
 
 def operator_for(p, ld=None, A=None, use_powerlaw=True):
     from paper_2204_08057_gb300.operator import Operator
+    A = p.A if A is None else A
     return Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, tau=p.tau,
                     kappa=p.kappa, nu=p.nu if A is None else None,
-                    beta=p.beta if A is None else None, A=A, ld=ld)
+                    beta=p.beta if A is None else None, A=A, ld=ld, prior=p.prior)
 
 
 def oracle_L(p):
-    return model.laplacian_from_csr(p.graph.rowptr, p.graph.col, p.graph.val, p.n)
+    """The prior shape the problem's operator uses: L, or L^T L for the intrinsic GMRF."""
+    L = model.laplacian_from_csr(p.graph.rowptr, p.graph.col, p.graph.val, p.n)
+    return model.igmrf_base(L) if p.prior == "igmrf" else L
+
+
+def oracle_A(p):
+    return model.powerlaw_mixing(p.nu, p.beta) if p.A is None else p.A
 
 
 def oracle_solution(p, A=None):
     L = oracle_L(p)
-    A = model.powerlaw_mixing(p.nu, p.beta) if A is None else A
+    A = oracle_A(p) if A is None else A
     G = model.assemble_G(L, p.D, p.tau, p.kappa, A)
     b = np.stack([model.rhs(p.D, y, A) for y in p.Yobs])
     return solve.solve_direct(G, b), b
