@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_lz_b(const Args 
 // Ctl::err, waits (bounded) for its copies in flight and leaves without its partial sums.
 using tma::NCONS;
 using tma::WS_THREADS;
-constexpr int NST_A = 3;   // stages of the pass-A ring (3 x 23 KB for k = 6)
+constexpr int NST_A = 3;   // stages of the pass-A ring (3 x 23 KB for k = 6, E = 4)
 constexpr int NST_B = 4;   // stages of the pass-B ring (4 x 13 KB for k = 6)
 
 template <int NST>
@@ -724,6 +724,7 @@ __device__ __forceinline__ void producer(Pipe<NST>& ps, int nunits, Issue&& issu
 
 template <int K, int E>
 struct LayoutA {
+  static constexpr int NST = E > 8 ? 2 : NST_A;   // wide stencils: two stages of ~35 KB
   static constexpr int CUR = 0, PREV = K, VAL = 2 * K, COL = 2 * K + E, DIAG = 2 * K + 2 * E,
                        NU = DIAG + 1, NUINV = DIAG + 2;
   static constexpr int ROWS = 2 * K + 2 * E + 3;
@@ -756,7 +757,7 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
   constexpr int NS = K * (K + 1) / 2;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ Smem<float, WS_THREADS / 32> sh;
-  __shared__ __align__(8) Pipe<NST_A> ps;
+  __shared__ __align__(8) Pipe<L::NST> ps;
   if (a.ctl->done != RUNNING) return;
   const int s = a.ctl->step + 1;
   load_factors<K, float>(a.co, sh, s > 1);
@@ -801,8 +802,8 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
   } else {
     const int t = threadIdx.x;
     for (int u = 0; u < nunits; ++u) {
-      const int st = u % NST_A;
-      if (!tma::mbar_wait_bounded(&ps.full[st], (u / NST_A) & 1) || ps.bad) {
+      const int st = u % L::NST;
+      if (!tma::mbar_wait_bounded(&ps.full[st], (u / L::NST) & 1) || ps.bad) {
         ps.bad = 1;
         break;
       }
@@ -1125,33 +1126,43 @@ cudaError_t launch_b(const Args& a, int ncta, cudaStream_t s) {
 
 // Staged FP32 passes: compiled for E = 4 (lattices and latitude-longitude spheres), no mass
 // diagonal; other problems use the plain kernels.
-bool staged_available(const OpData& op) { return op.E == 4 && !op.has_w && op.ld % TILE_PX == 0; }
+bool staged_available(const OpData& op) {
+  return (op.E == 4 || op.E == 12) && !op.has_w && op.ld % TILE_PX == 0;
+}
 
-template <int K>
+template <int K, int E>
 cudaError_t set_smem_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_lz_a_tma<K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       NST_A * LayoutA<K, 4>::STAGE_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_lz_a_tma<K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       LayoutA<K, E>::NST * LayoutA<K, E>::STAGE_BYTES);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_lz_b_tma<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               NST_B * LayoutB<K>::STAGE_BYTES);
 }
 
 cudaError_t launch_a_tma(const Args& a, int ncta, cudaStream_t s) {
-#define CALL(K)                                                                              \
+#define CALL_E(K, E)                                                                         \
   do {                                                                                       \
-    static const cudaError_t attr = set_smem_attrs<K>();                                     \
+    static const cudaError_t attr = set_smem_attrs<K, E>();                                  \
     if (attr != cudaSuccess) return attr;                                                    \
-    k_lz_a_tma<K, 4><<<ncta, WS_THREADS, NST_A * LayoutA<K, 4>::STAGE_BYTES, s>>>(a);        \
+    k_lz_a_tma<K, E><<<ncta, WS_THREADS, LayoutA<K, E>::NST * LayoutA<K, E>::STAGE_BYTES, s>>>(a); \
   } while (0)
-  LZ_DISPATCH_K(a.op.k, CALL)
+  if (a.op.E == 12) {
+#define CALL(K) CALL_E(K, 12)
+    LZ_DISPATCH_K(a.op.k, CALL)
 #undef CALL
+  } else {
+#define CALL(K) CALL_E(K, 4)
+    LZ_DISPATCH_K(a.op.k, CALL)
+#undef CALL
+  }
+#undef CALL_E
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_tma(const Args& a, int ncta, cudaStream_t s) {
 #define CALL(K)                                                                              \
   do {                                                                                       \
-    static const cudaError_t attr = set_smem_attrs<K>();                                     \
+    static const cudaError_t attr = set_smem_attrs<K, 4>();                                  \
     if (attr != cudaSuccess) return attr;                                                    \
     k_lz_b_tma<K><<<ncta, WS_THREADS, NST_B * LayoutB<K>::STAGE_BYTES, s>>>(a);             \
   } while (0)
@@ -1186,12 +1197,17 @@ int occupancy(int kind, int k, int E) {
     else if (kind == 2) take((const void*)k_lz_assemble<K, T>);                   \
     else if (kind == 3)                                                           \
       take(E == 4 ? (const void*)k_lz_start<K, 4, T> : (const void*)k_lz_start<K, 0, T>); \
-    else if (kind == 4) {                                                         \
-      if (set_smem_attrs<K>() != cudaSuccess) nb = 1;                             \
-      else take_ws((const void*)k_lz_a_tma<K, 4>, NST_A * LayoutA<K, 4>::STAGE_BYTES); \
+    else if (kind == 4 && E == 12) {                                              \
+      if (set_smem_attrs<K, 12>() != cudaSuccess) nb = 1;                         \
+      else take_ws((const void*)k_lz_a_tma<K, 12>,                                \
+                   LayoutA<K, 12>::NST * LayoutA<K, 12>::STAGE_BYTES);            \
+    } else if (kind == 4) {                                                       \
+      if (set_smem_attrs<K, 4>() != cudaSuccess) nb = 1;                          \
+      else take_ws((const void*)k_lz_a_tma<K, 4>,                                 \
+                   LayoutA<K, 4>::NST * LayoutA<K, 4>::STAGE_BYTES);              \
     } else {                                                                      \
-      if (set_smem_attrs<K>() != cudaSuccess) nb = 1;                             \
-      else take_ws((const void*)k_lz_b_tma<K>, NST_B * LayoutB<K>::STAGE_BYTES); \
+      if (set_smem_attrs<K, 4>() != cudaSuccess) nb = 1;                          \
+      else take_ws((const void*)k_lz_b_tma<K>, NST_B * LayoutB<K>::STAGE_BYTES);  \
     }                                                                             \
   } while (0)
     LZ_DISPATCH_K(k, CALL)

@@ -763,7 +763,8 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
 // launchers
 // ---------------------------------------------------------------------------------------------
 // Shapes with compile-time (k, m, E) kernels; every other shape uses the (k, 0, 0) kernels.
-#define SYLV_SPECIAL_SHAPES(X) X(3, 5, 4) X(4, 6, 4) X(4, 7, 4) X(5, 7, 4) X(6, 8, 4) X(6, 9, 4)
+#define SYLV_SPECIAL_SHAPES(X) \
+  X(3, 5, 4) X(4, 6, 4) X(4, 7, 4) X(5, 7, 4) X(6, 8, 4) X(6, 9, 4) X(4, 9, 12)
 
 #define SYLV_IS_SPECIAL_(K_, M_, E_) || (k == K_ && m == M_ && e == E_)
 inline bool special_shape(int k, int m, int e) {
