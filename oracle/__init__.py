@@ -22,6 +22,8 @@ What it computes (all in float64, unknowns stored as X with shape (k, n), so tha
 * ``gradient``: derivatives of a loss on the posterior mean with respect to tau_j, kappa_j and
   beta_j through one adjoint solve, and central finite differences of the direct solve.
 * ``physical_mixing``: the physical mixing matrix of App. B (CMB, synchrotron, dust, free-free).
+* ``variance``: the posterior variances diag(G^{-1}) (exact, and the probe estimator of Bekas,
+  Kokiopoulou and Saad), with the lattice closed form.
 * ``sylvester``: the block-Lanczos solver of the Sylvester form eq. Axb-Sylv for separable noise
   and a common prior shape (Algorithms 4 and 5, Sec. 3.3).
 """

@@ -23,5 +23,6 @@ from .problems import (  # noqa: F401
     batch_problems,
     separable_problem,
     igmrf_problem,
+    rademacher_probes,
     CONFIG_SEED_BASE,
 )

@@ -213,6 +213,12 @@ def igmrf_problem(config_id: int = 2, *, scale: Optional[int] = None, phi: float
                    D, Yobs, S, 1e-8, {"config": config_id, "igmrf": True}, A=A, prior="igmrf")
 
 
+def rademacher_probes(count: int, k: int, n: int, seed: int) -> np.ndarray:
+    """(count, k, n) probe vectors with independent +-1 entries (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(0, 2, size=(count, k, n)).astype(np.float64) * 2.0 - 1.0
+
+
 def batch_problems(count=64, side_range=(128, 1024), *, seed=None) -> List[Problem]:
     """Batched workload: ``count`` independent periodic lattices of log-uniform side, k in
     {3,4,5,6} uniform, m = k + 2, own kappa (log-spaced 0.01..1, permuted), beta and noise."""
