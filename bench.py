@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's own model on the workload grid: printed physical mixing "
                          "and channel weights (App. B), intrinsic GMRF prior (App. C)")
+    ap.add_argument("--variance", type=int, default=0, metavar="S",
+                    help="posterior variances of the workload from S Rademacher probes")
     ap.add_argument("--separable", action="store_true",
                     help="separable special case of the workload: block-Lanczos Sylvester "
                          "solver (Algorithms 4 and 5) against the preconditioned CG")
@@ -828,6 +830,42 @@ def run_paper_model(args):
     op.close()
 
 
+def run_variance(args):
+    """Posterior variances diag(G^{-1}) of the 1024 x 2048 workload from S Rademacher probes
+    (sylv_variance: probe solves 16 at a time by the multi-right-hand-side mixed PCG)."""
+    import torch
+    import synth
+    from paper_2204_08057_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(0)
+    p = synth.config_problem(args.config, scale=args.scale if args.scale > 1 else None)
+    op = make_operator(p)
+    S = int(args.variance)
+    Z = torch.from_numpy(synth.rademacher_probes(S, p.k, p.n, seed=2204)).cuda()
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=1e-8, precision=1)
+    for _ in range(max(1, args.warmup // 2)):
+        op.variance(Z, **kw)
+    clocks = ClockSampler(0) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    ms, (var, info) = _timed(stream, lambda: op.variance(Z, **kw), max(1, args.steps // 2))
+    clk = clocks.stop() if clocks else None
+    assert info["code"] == 0, info
+    v = var[:, :p.n]
+    line = _base_line(args, "posterior variances diag(G^-1) from %d probes (probe solves to "
+                            "relres 1e-8, 16 at a time)" % S, ms, "ms",
+                      {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "probes": S,
+                       "tol": 1e-8, "precision": "mixed", "l2": "inputs larger than L2"})
+    line.update({"ms_per_probe": ms / S, "iterations_max": info["iterations"],
+                 "outer_max": info["outer"],
+                 "variance_range": [float(v.min()), float(v.max())],
+                 "gpu_launches": info["launches"], "clocks": clk})
+    print(json.dumps(line), flush=True)
+    op.close()
+
+
 def op_degree(p):
     """Off-diagonals per row of the prior shape the operator uses (L, or L^2 for the IGMRF)."""
     import numpy as _np
@@ -839,6 +877,9 @@ def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.impl == "ours" and args.variance > 0:
+        run_variance(args)
         return
     if args.impl == "ours" and args.paper_model:
         run_paper_model(args)

@@ -192,6 +192,20 @@ int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const d
                   int nrhs, double* lambda, double* g_tau, double* g_kappa, double* g_beta,
                   const sylv_opts* o, sylv_info* info, sylv_stream s);
 
+/* Posterior variances: the diagonal of the posterior covariance Qhat^{-1} = G^{-1} (eq. Q*:
+ * its main diagonal holds the variance of each source at each pixel), by the stochastic
+ * diagonal estimator of Bekas, Kokiopoulou and Saad (2007):
+ *     var ~ (sum_s z_s o G^{-1} z_s) / (sum_s z_s o z_s)   (element-wise),
+ * with the probe solves run SYLV_MAX_RHS at a time by the multi-right-hand-side solve (mixed
+ * or FP64 per o->precision; o->use_x0 is ignored).  Z: device, nprobe x k x ld FP64 probe
+ * vectors (caller-drawn, e.g. independent +-1 entries; unit vectors give the exact
+ * diagonal).  var: device, k x ld FP64 output (entries whose probes are all zero get 0).
+ * info: iterations and refinements are the maxima over the chunks, times their sums.
+ * Returns SYLV_OK, SYLV_E_NOT_CONVERGED (estimate written from the last iterates) or a solve
+ * error.  Synchronises s. */
+int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const sylv_opts* o,
+                  sylv_info* info, sylv_stream s);
+
 /* Solves the same system through its Sylvester form (Sec. 3.3, eq. Axb-Sylv) with the block
  * Lanczos method of Algorithms 4 and 5.  Applies when the noise precision is separable,
  * d_ci = t_c nu_i (C = T kron N, nu_i > 0), and every source shares one prior shape

@@ -34,7 +34,7 @@ MAX_K, MAX_M, MAX_DEGREE, MAX_RHS = 8, 16, 8, 16
 
 EXPORTED = ["sylv_opts_default", "sylv_create", "sylv_rhs", "sylv_apply", "sylv_solve",
             "sylv_solve_batched", "sylv_backward", "sylv_destroy", "sylv_strerror",
-            "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester"]
+            "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester", "sylv_variance"]
 
 
 class sylv_problem(ctypes.Structure):
@@ -104,6 +104,8 @@ def load(path=None):
                                        POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
     lib.sylv_solve_sylvester.argtypes = [c_void_p, c_void_p, c_void_p, c_int,
                                          POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
+    lib.sylv_variance.argtypes = [c_void_p, c_void_p, c_int, c_void_p, POINTER(sylv_opts),
+                                  POINTER(sylv_info), c_void_p]
     lib.sylv_destroy.argtypes = [c_void_p]
     lib.sylv_destroy.restype = None
     lib.sylv_strerror.argtypes = [c_int]
@@ -312,4 +314,17 @@ def sylv_solve_sylvester(h, B, X, nrhs, opts=None, *, k, ld, n, stream=None, all
                                        ctypes.byref(opts) if opts is not None else None,
                                        ctypes.byref(info), _stream(stream))
     _check(code, "sylv_solve_sylvester", ok=(SYLV_OK,) + tuple(allow))
+    return code, info
+
+
+def sylv_variance(h, Z, nprobe, var, opts=None, *, k, ld, n, stream=None, allow=()):
+    """Probe estimate of the posterior variances (see sylv.h).  Returns (status, info)."""
+    import torch
+    need = ((nprobe - 1) * k + k - 1) * ld + n
+    info = sylv_info()
+    code = load().sylv_variance(c_void_p(h), _dev_ptr(Z, torch.float64, need, "Z"), int(nprobe),
+                                _dev_ptr(var, torch.float64, (k - 1) * ld + n, "var"),
+                                ctypes.byref(opts) if opts is not None else None,
+                                ctypes.byref(info), _stream(stream))
+    _check(code, "sylv_variance", ok=(SYLV_OK,) + tuple(allow))
     return code, info

@@ -144,6 +144,8 @@ struct sylv_ctx {
   size_t lam_bytes = 0;
   double* grad_ws = nullptr;
   size_t grad_bytes = 0;
+  double* var_ws = nullptr;   // sylv_variance: solves of one chunk of probes, num, den
+  size_t var_bytes = 0;
 };
 
 Plan::~Plan() {
@@ -861,6 +863,7 @@ static void free_handle(sylv_ctx* h) {
   cudaFree(h->apply_err);
   cudaFree(h->lam);
   cudaFree(h->grad_ws);
+  cudaFree(h->var_ws);
   delete h;
 }
 
@@ -1202,6 +1205,65 @@ int sylv_solve_batched(int nsys, const sylv_handle* hs, const double* const* B,
                        double* const* X, const int* nrhs, const sylv_opts* o,
                        sylv_info* infos, sylv_stream s) {
   return solve_impl(nsys, hs, B, X, nrhs, o, infos, (cudaStream_t)s, false);
+}
+
+int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const sylv_opts* o_in,
+                  sylv_info* info, sylv_stream stream) {
+  if (!h || !Z || !var) return fail(SYLV_E_INVALID, "NULL argument");
+  if (nprobe < 1) return fail(SYLV_E_INVALID, "nprobe must be >= 1");
+  sylv_opts o;
+  if (o_in) o = *o_in;
+  else sylv_opts_default(&o);
+  o.use_x0 = 0;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const OpData& op = h->op;
+  const int chunk = std::min(nprobe, RMAX);
+  const size_t xelems = (size_t)chunk * op.k * op.ldu, kelems = (size_t)op.k * op.ld;
+  const size_t bytes = (xelems + 2 * kelems) * sizeof(double);
+  if (h->var_bytes < bytes) {
+    cudaFree(h->var_ws);
+    h->var_ws = nullptr;
+    h->var_bytes = 0;
+    CK(dalloc(&h->var_ws, bytes));
+    h->var_bytes = bytes;
+  }
+  double* X = h->var_ws;
+  double* num = X + xelems;
+  double* den = num + kelems;
+  CK(cudaMemsetAsync(num, 0, 2 * kelems * sizeof(double), s));
+  sylv_info tot;
+  std::memset(&tot, 0, sizeof(tot));
+  int worst = SYLV_OK;
+  for (int s0 = 0; s0 < nprobe; s0 += chunk) {
+    const int r = std::min(chunk, nprobe - s0);
+    const double* Zc = Z + (size_t)s0 * op.k * op.ldu;
+    sylv_info inf;
+    int rc = sylv_solve(h, Zc, X, r, &o, &inf, stream);
+    if (rc != SYLV_OK && rc != SYLV_E_NOT_CONVERGED) return rc;
+    if (rc != SYLV_OK) worst = rc;
+    CK(launch_var_accum(op, Zc, X, r, num, den, s));
+    tot.iterations = std::max(tot.iterations, inf.iterations);
+    tot.outer = std::max(tot.outer, inf.outer);
+    tot.polls += inf.polls;
+    tot.relres = std::max(tot.relres, inf.relres);
+    tot.ms_total += inf.ms_total;
+    tot.ms_apply += inf.ms_apply;
+    tot.ms_update += inf.ms_update;
+    tot.ms_residual += inf.ms_residual;
+    tot.launches += inf.launches + 1;
+    tot.tile = inf.tile;
+    tot.slots_mult = inf.slots_mult;
+    tot.apply_staged = inf.apply_staged;
+    tot.update_staged = inf.update_staged;
+  }
+  CK(launch_var_finish(op, num, den, var, s));
+  CK(cudaStreamSynchronize(s));
+  tot.launches += 1;
+  tot.status = worst;
+  if (info) *info = tot;
+  if (worst != SYLV_OK) g_last_error = "a probe solve did not reach the tolerance";
+  return worst;
 }
 
 int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const double* Yobs,

@@ -156,6 +156,33 @@ __global__ void k_square_fill(int64_t n, int64_t ld, int E, const int32_t* __res
   sq_diag32[i] = (float)dg;
 }
 
+// Probe estimator of the posterior variances: num += z o x and den += z o z over R probes z
+// (caller layout, pitch ldu) and their solves x = G^{-1} z; then var = num / den.
+__global__ void k_var_accum(int64_t n, int k, int64_t ldu, int64_t ld, const double* __restrict__ Z,
+                            const double* __restrict__ X, int R, double* num, double* den) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)k * n) return;
+  const int64_t j = t / n, i = t - j * n;
+  double a = num[j * ld + i], b = den[j * ld + i];
+  for (int r = 0; r < R; ++r) {
+    const double z = Z[((int64_t)r * k + j) * ldu + i];
+    a += z * X[((int64_t)r * k + j) * ldu + i];
+    b += z * z;
+  }
+  num[j * ld + i] = a;
+  den[j * ld + i] = b;
+}
+
+__global__ void k_var_finish(int64_t n, int k, int64_t ldu, int64_t ld,
+                             const double* __restrict__ num, const double* __restrict__ den,
+                             double* var) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)k * n) return;
+  const int64_t j = t / n, i = t - j * n;
+  const double b = den[j * ld + i];
+  var[j * ldu + i] = b > 0.0 ? num[j * ld + i] / b : 0.0;
+}
+
 // Copies rows x n values (pitch ld) into FP32 and FP64 buffers and checks them (>= 0, or > 0
 // if positive, and finite).
 __global__ void k_convert_check(const double* __restrict__ src, int64_t rows, int64_t n,
@@ -393,6 +420,22 @@ cudaError_t launch_square_fill(const OpData& op, int E2, int32_t* sq_col, float*
   k_square_fill<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(
       op.n, op.ld, op.E, op.ell_col, op.ell_val64, op.diag64, E2, sq_col, sq_val32, sq_val64,
       sq_diag32, sq_diag64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_accum(const OpData& op, const double* Z, const double* X, int R,
+                             double* num, double* den, cudaStream_t s) {
+  const int64_t tot = (int64_t)op.k * op.n;
+  k_var_accum<<<blocks_for(tot, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(op.n, op.k, op.ldu, op.ld, Z, X,
+                                                                   R, num, den);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_var_finish(const OpData& op, const double* num, const double* den,
+                              double* var, cudaStream_t s) {
+  const int64_t tot = (int64_t)op.k * op.n;
+  k_var_finish<<<blocks_for(tot, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(op.n, op.k, op.ldu, op.ld, num,
+                                                                    den, var);
   return cudaGetLastError();
 }
 

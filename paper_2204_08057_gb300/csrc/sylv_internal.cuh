@@ -161,6 +161,11 @@ cudaError_t launch_ell_build(const OpData& op, const int32_t* rowptr, const int3
                              const double* val, int32_t* ell_col, float* ell_val32,
                              double* ell_val64, float* diag32, double* diag64, int E,
                              cudaStream_t s);
+// Probe estimator of the posterior variances (sylv_variance).
+cudaError_t launch_var_accum(const OpData& op, const double* Z, const double* X, int R,
+                             double* num, double* den, cudaStream_t s);
+cudaError_t launch_var_finish(const OpData& op, const double* num, const double* den,
+                              double* var, cudaStream_t s);
 // Intrinsic GMRF prior shape: the ELL width of L^2 (atomic max into *width), then L^2 itself
 // into new ELL arrays of that width and a new diagonal.
 cudaError_t launch_square_count(const OpData& op, unsigned int* width, cudaStream_t s);

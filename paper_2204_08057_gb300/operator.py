@@ -132,6 +132,19 @@ class Operator:
         d["code"] = code
         return X, d
 
+    def variance(self, Z, *, opts=None, stream=None, allow_not_converged=False, **kw):
+        """Posterior variances diag(G^{-1}) (k, ld) estimated from the probes Z (S, k, ld)."""
+        Zb = self._batch(Z, self.k)
+        if opts is None:
+            opts = B.make_opts(**kw)
+        var = Zb.new_zeros((self.k, self.ld))
+        allow = (B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ()
+        code, info = B.sylv_variance(self.handle, Zb, Zb.shape[0], var, opts, k=self.k,
+                                     ld=self.ld, n=self.n, stream=stream, allow=allow)
+        d = info.as_dict()
+        d["code"] = code
+        return var, d
+
     def backward(self, Xhat, dLdX, Yobs=None, *, opts=None, want=("tau", "kappa", "beta"),
                  stream=None, **kw):
         """Gradients (g_tau, g_kappa, g_beta) of a loss with dl/dX = dLdX at X = Xhat."""
