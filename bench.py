@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's own model on the workload grid: printed physical mixing "
                          "and channel weights (App. B), intrinsic GMRF prior (App. C)")
+    ap.add_argument("--learn", type=int, default=0, metavar="N",
+                    help="N steps of parameter learning on the 512 x 1024 workload, warm and cold")
     ap.add_argument("--variance", type=int, default=0, metavar="S",
                     help="posterior variances of the workload from S Rademacher probes")
     ap.add_argument("--separable", action="store_true",
@@ -866,6 +868,50 @@ def run_variance(args):
     op.close()
 
 
+def run_learn(args):
+    """Parameter learning on the 512 x 1024 sphere (k = 4, m = 7): N gradient steps over
+    (log tau, log kappa, beta) on ||X - X_true||^2, each a parameter update in place, the
+    right-hand side, a forward solve, an adjoint solve and the gradient reduction; with warm
+    starts (the previous step's X and lambda) against cold starts."""
+    import torch
+    import synth
+    from paper_2204_08057_gb300 import build as _build
+    from paper_2204_08057_gb300.learn import HyperLearner
+    _build.build()
+    torch.cuda.set_device(0)
+    p = synth.config_problem(4, scale=args.scale if args.scale > 1 else None)
+    op = make_operator(p)
+    Y = torch.from_numpy(p.Yobs).cuda()
+    Xt = torch.from_numpy(p.X_true).cuda()[None]
+
+    def loss_grad(X):
+        d = X - Xt
+        return float(torch.sum(d * d)), 2.0 * d
+
+    stream = torch.cuda.current_stream()
+    tau0, kappa0, beta0 = p.tau * 1.5, p.kappa * 0.7, p.beta + 0.05
+    N = int(args.learn)
+    out = {}
+    for warm in (True, False):
+        hl = HyperLearner(op, Y, loss_grad, tau0, kappa0, beta0, lr=1e-7, warm=warm, tol=1e-8)
+        hl.step()                                  # warm-up (first step is cold either way)
+        hl = HyperLearner(op, Y, loss_grad, tau0, kappa0, beta0, lr=1e-7, warm=warm, tol=1e-8)
+        ms, _ = _timed(stream, lambda: [hl.step() for _ in range(N)], 1)
+        recs = hl.history
+        out[warm] = {"ms_per_step": ms / N,
+                     "forward_iterations": [r["forward_iterations"] for r in recs],
+                     "adjoint_iterations": [r["adjoint_iterations"] for r in recs],
+                     "loss": [r["loss"] for r in recs]}
+    line = _base_line(args, "parameter-learning step (set params, rhs, forward + adjoint solve "
+                            "to relres 1e-8, gradient), warm-started", out[True]["ms_per_step"],
+                      "ms", {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "steps": N,
+                             "tol": 1e-8, "precision": "mixed"})
+    line.update({"warm": out[True], "cold": out[False],
+                 "speedup_warm_vs_cold": out[False]["ms_per_step"] / out[True]["ms_per_step"]})
+    print(json.dumps(line), flush=True)
+    op.close()
+
+
 def op_degree(p):
     """Off-diagonals per row of the prior shape the operator uses (L, or L^2 for the IGMRF)."""
     import numpy as _np
@@ -877,6 +923,9 @@ def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.impl == "ours" and args.learn > 0:
+        run_learn(args)
         return
     if args.impl == "ours" and args.variance > 0:
         run_variance(args)

@@ -192,6 +192,17 @@ int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const d
                   int nrhs, double* lambda, double* g_tau, double* g_kappa, double* g_beta,
                   const sylv_opts* o, sylv_info* info, sylv_stream s);
 
+/* Replaces the prior scalars tau_j, kappa_j and the mixing matrix (explicit A, or nu and beta
+ * for the power law with the handle's nu0) of a handle in place, as repeated solves across the
+ * model parameters need (Sec. 5: learning the parameters by solving the system for many of
+ * their values).  The graph, noise maps and the ELL copy are kept; the FP64 pixel blocks and
+ * their factors are recomputed on the device.  Host arrays as in sylv_problem.  Solves and
+ * gradients that follow use the new values; an earlier solution passed as X with
+ * o->use_x0 = 1 is a warm start for the new system.  Returns SYLV_OK or SYLV_E_INVALID
+ * (nothing changed).  Synchronises s. */
+int sylv_set_params(sylv_handle h, const double* tau, const double* kappa, const double* nu,
+                    const double* beta, const double* A, sylv_stream s);
+
 /* Posterior variances: the diagonal of the posterior covariance Qhat^{-1} = G^{-1} (eq. Q*:
  * its main diagonal holds the variance of each source at each pixel), by the stochastic
  * diagonal estimator of Bekas, Kokiopoulou and Saad (2007):

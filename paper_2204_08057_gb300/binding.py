@@ -34,7 +34,7 @@ MAX_K, MAX_M, MAX_DEGREE, MAX_RHS = 8, 16, 8, 16
 
 EXPORTED = ["sylv_opts_default", "sylv_create", "sylv_rhs", "sylv_apply", "sylv_solve",
             "sylv_solve_batched", "sylv_backward", "sylv_destroy", "sylv_strerror",
-            "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester", "sylv_variance"]
+            "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester", "sylv_variance", "sylv_set_params"]
 
 
 class sylv_problem(ctypes.Structure):
@@ -106,6 +106,9 @@ def load(path=None):
                                          POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
     lib.sylv_variance.argtypes = [c_void_p, c_void_p, c_int, c_void_p, POINTER(sylv_opts),
                                   POINTER(sylv_info), c_void_p]
+    lib.sylv_set_params.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double),
+                                    POINTER(c_double), POINTER(c_double), POINTER(c_double),
+                                    c_void_p]
     lib.sylv_destroy.argtypes = [c_void_p]
     lib.sylv_destroy.restype = None
     lib.sylv_strerror.argtypes = [c_int]
@@ -328,3 +331,15 @@ def sylv_variance(h, Z, nprobe, var, opts=None, *, k, ld, n, stream=None, allow=
                                 ctypes.byref(info), _stream(stream))
     _check(code, "sylv_variance", ok=(SYLV_OK,) + tuple(allow))
     return code, info
+
+
+def sylv_set_params(h, *, k, m, tau, kappa, nu=None, beta=None, A=None, stream=None):
+    """New tau, kappa and mixing for an existing handle (see sylv.h)."""
+    keep = []
+    ptrs = []
+    for name, val, cnt in (("tau", tau, k), ("kappa", kappa, k), ("nu", nu, m),
+                           ("beta", beta, k), ("A", A, m * k)):
+        arr, ptr = _host_doubles(val, cnt, name)
+        keep.append(arr)
+        ptrs.append(ptr)
+    _check(load().sylv_set_params(c_void_p(h), *ptrs, _stream(stream)), "sylv_set_params")

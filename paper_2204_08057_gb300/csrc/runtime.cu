@@ -125,6 +125,7 @@ struct sylv_ctx {
   int device = 0;
   OpData op{};
   int explicit_A = 0;
+  double nu0 = 100.0;
   int32_t* ell_col = nullptr;
   float* ell_val32 = nullptr;
   double* ell_val64 = nullptr;
@@ -867,6 +868,43 @@ static void free_handle(sylv_ctx* h) {
   delete h;
 }
 
+// Mixing matrix (explicit, or a_cj = (nu_c / nu0)^beta_j) and prior scalars into op.
+static int set_scalars(OpData& op, const double* tau, const double* kappa, const double* nu,
+                       const double* beta, const double* A, double nu0) {
+  const int k = op.k, m = op.m;
+  for (int j = 0; j < k; ++j) {
+    if (!(tau[j] > 0.0) || !std::isfinite(tau[j]))
+      return fail(SYLV_E_INVALID, "tau_j must be finite and > 0");
+    if (!(kappa[j] >= 0.0) || !std::isfinite(kappa[j]))
+      return fail(SYLV_E_INVALID, "kappa_j must be finite and >= 0");
+  }
+  double A64[MMAX * KMAX], logf[MMAX];
+  for (int c = 0; c < m; ++c) {
+    if (!A && !(nu[c] > 0.0)) return fail(SYLV_E_INVALID, "nu_c must be > 0");
+    for (int j = 0; j < k; ++j) {
+      const double a = A ? A[c * k + j] : std::pow(nu[c] / nu0, beta[j]);
+      if (!std::isfinite(a)) return fail(SYLV_E_INVALID, "mixing matrix entry is not finite");
+      A64[c * k + j] = a;
+    }
+    logf[c] = A ? 0.0 : std::log(nu[c] / nu0);
+  }
+  for (int c = 0; c < m; ++c) {
+    for (int j = 0; j < k; ++j) {
+      op.A64[c * k + j] = A64[c * k + j];
+      op.A32[c * k + j] = (float)A64[c * k + j];
+    }
+    op.logf64[c] = logf[c];
+  }
+  for (int j = 0; j < k; ++j) {
+    op.tau64[j] = tau[j];
+    op.kappa64[j] = kappa[j];
+    op.tk2_64[j] = tau[j] * kappa[j] * kappa[j];
+    op.tau32[j] = (float)op.tau64[j];
+    op.tk2_32[j] = (float)op.tk2_64[j];
+  }
+  return SYLV_OK;
+}
+
 int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   if (!out) return fail(SYLV_E_INVALID, "handle pointer is NULL");
   *out = nullptr;
@@ -883,12 +921,6 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   if (!p->A && (!p->nu || !p->beta))
     return fail(SYLV_E_INVALID, "give A, or nu and beta for the power-law mixing");
   const double nu0 = p->nu0 > 0.0 ? p->nu0 : 100.0;
-  for (int j = 0; j < p->k; ++j) {
-    if (!(p->tau[j] > 0.0) || !std::isfinite(p->tau[j]))
-      return fail(SYLV_E_INVALID, "tau_j must be finite and > 0");
-    if (!(p->kappa[j] >= 0.0) || !std::isfinite(p->kappa[j]))
-      return fail(SYLV_E_INVALID, "kappa_j must be finite and >= 0");
-  }
   cudaStream_t s = (cudaStream_t)stream;
   sylv_ctx* h = new sylv_ctx();
   cudaGetDevice(&h->device);
@@ -899,35 +931,15 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   op.k = p->k;
   op.m = p->m;
   op.has_w = p->w != nullptr;
-  for (int c = 0; c < p->m; ++c) {
-    for (int j = 0; j < p->k; ++j) {
-      double a;
-      if (p->A) {
-        a = p->A[c * p->k + j];
-      } else {
-        if (!(p->nu[c] > 0.0)) {
-          free_handle(h);
-          return fail(SYLV_E_INVALID, "nu_c must be > 0");
-        }
-        a = std::pow(p->nu[c] / nu0, p->beta[j]);
-      }
-      if (!std::isfinite(a)) {
-        free_handle(h);
-        return fail(SYLV_E_INVALID, "mixing matrix entry is not finite");
-      }
-      op.A64[c * p->k + j] = a;
-      op.A32[c * p->k + j] = (float)a;
+  h->nu0 = nu0;
+  {
+    const int rc0 = set_scalars(op, p->tau, p->kappa, p->nu, p->beta, p->A, nu0);
+    if (rc0 != SYLV_OK) {
+      free_handle(h);
+      return rc0;
     }
-    op.logf64[c] = (!p->A) ? std::log(p->nu[c] / nu0) : 0.0;
   }
   h->explicit_A = p->A != nullptr;
-  for (int j = 0; j < p->k; ++j) {
-    op.tau64[j] = p->tau[j];
-    op.kappa64[j] = p->kappa[j];
-    op.tk2_64[j] = p->tau[j] * p->kappa[j] * p->kappa[j];
-    op.tau32[j] = (float)op.tau64[j];
-    op.tk2_32[j] = (float)op.tk2_64[j];
-  }
   // validate the CSR and find the ELL width
   unsigned int* dflags = nullptr;
   int rc = SYLV_OK;
@@ -1090,6 +1102,24 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   cudaFree(dflags);
   *out = h;
   (void)rc;
+  return SYLV_OK;
+}
+
+int sylv_set_params(sylv_handle h, const double* tau, const double* kappa, const double* nu,
+                    const double* beta, const double* A, sylv_stream stream) {
+  if (!h || !tau || !kappa) return fail(SYLV_E_INVALID, "NULL argument");
+  if (!A && (!nu || !beta)) return fail(SYLV_E_INVALID, "give A, or nu and beta");
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  OpData op = h->op;
+  int rc = set_scalars(op, tau, kappa, nu, beta, A, h->nu0);
+  if (rc != SYLV_OK) return rc;
+  // the pixel blocks and their factors depend on tau, kappa and A
+  CK(launch_block_setup(op, h->blk64, h->fac64, h->fs32, h->fl16, s));
+  CK(cudaStreamSynchronize(s));
+  h->op = op;
+  h->explicit_A = A != nullptr;
+  lanczos_release(h);   // separability and Lhat were derived from the old scalars
   return SYLV_OK;
 }
 

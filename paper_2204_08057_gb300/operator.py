@@ -145,15 +145,35 @@ class Operator:
         d["code"] = code
         return var, d
 
+    def set_params(self, tau, kappa, *, nu=None, beta=None, A=None, stream=None):
+        """New prior scalars and mixing for this handle (sylv_set_params)."""
+        tau = np.asarray(tau, dtype=np.float64).reshape(-1)
+        kappa = np.asarray(kappa, dtype=np.float64).reshape(-1)
+        if A is None:
+            nu = self.nu if nu is None else np.asarray(nu, dtype=np.float64).reshape(-1)
+            beta = self.beta if beta is None else np.asarray(beta, dtype=np.float64).reshape(-1)
+        B.sylv_set_params(self.handle, k=self.k, m=self.m, tau=tau, kappa=kappa, nu=nu,
+                          beta=None if A is not None else beta, A=A, stream=stream)
+        self.tau, self.kappa = tau, kappa
+        if A is None:
+            self.nu, self.beta, self.A = nu, beta, None
+        else:
+            self.A = np.asarray(A, dtype=np.float64).reshape(self.m, self.k)
+
     def backward(self, Xhat, dLdX, Yobs=None, *, opts=None, want=("tau", "kappa", "beta"),
-                 stream=None, **kw):
-        """Gradients (g_tau, g_kappa, g_beta) of a loss with dl/dX = dLdX at X = Xhat."""
+                 stream=None, lam0=None, **kw):
+        """Gradients (g_tau, g_kappa, g_beta) of a loss with dl/dX = dLdX at X = Xhat.  lam0: an
+        earlier adjoint solution to start the adjoint solve from (warm start)."""
         Xb = self._batch(Xhat, self.k)
         Gb = self._batch(dLdX, self.k)
         Yb = self._batch(Yobs, self.m) if Yobs is not None else None
         if opts is None:
             opts = B.make_opts(**kw)
-        lam = Xb.new_zeros(Xb.shape)
+        if lam0 is not None:
+            lam = self._batch(lam0, self.k).clone()
+            opts.use_x0 = 1
+        else:
+            lam = Xb.new_zeros(Xb.shape)
         gt, gk, gb, info = B.sylv_backward(self.handle, Xb, Gb, Yb, Xb.shape[0], lam, opts,
                                            k=self.k, m=self.m, ld=self.ld, n=self.n,
                                            want=want, stream=stream)
