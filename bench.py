@@ -893,9 +893,11 @@ def run_learn(args):
     N = int(args.learn)
     out = {}
     for warm in (True, False):
-        hl = HyperLearner(op, Y, loss_grad, tau0, kappa0, beta0, lr=1e-7, warm=warm, tol=1e-8)
+        # steps of length 0.02 in (log tau, log kappa, beta) along the negative gradient
+        kwl = dict(lr=0.02, normalize=True, warm=warm, tol=1e-8)
+        hl = HyperLearner(op, Y, loss_grad, tau0, kappa0, beta0, **kwl)
         hl.step()                                  # warm-up (first step is cold either way)
-        hl = HyperLearner(op, Y, loss_grad, tau0, kappa0, beta0, lr=1e-7, warm=warm, tol=1e-8)
+        hl = HyperLearner(op, Y, loss_grad, tau0, kappa0, beta0, **kwl)
         ms, _ = _timed(stream, lambda: [hl.step() for _ in range(N)], 1)
         recs = hl.history
         out[warm] = {"ms_per_step": ms / N,

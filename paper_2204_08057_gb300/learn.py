@@ -16,8 +16,8 @@ import numpy as np
 class HyperLearner:
     """loss_grad(X) -> (loss, dl/dX) for the (R, k, ld) posterior mean X, as float, tensor."""
 
-    def __init__(self, op, Yobs, loss_grad, tau, kappa, beta, *, lr=0.05, learn=("tau", "kappa", "beta"),
-                 warm=True, **solve_kw):
+    def __init__(self, op, Yobs, loss_grad, tau, kappa, beta, *, lr=0.05,
+                 learn=("tau", "kappa", "beta"), warm=True, normalize=False, **solve_kw):
         self.op = op
         self.Y = Yobs
         self.loss_grad = loss_grad
@@ -27,6 +27,7 @@ class HyperLearner:
         self.lr = float(lr)
         self.learn = tuple(learn)
         self.warm = bool(warm)
+        self.normalize = bool(normalize)   # steps of length lr along -gradient
         self.solve_kw = dict(solve_kw)
         self.X = None
         self.lam = None
@@ -46,12 +47,16 @@ class HyperLearner:
         lam0 = self.lam if (self.warm and self.lam is not None) else None
         gt, gk, gb, lam, info_b = self.op.backward(X, g, self.Y, lam0=lam0, **self.solve_kw)
         # chain rule to log tau, log kappa: dl/dlog(t) = t dl/dt
-        if "tau" in self.learn:
-            self.log_tau -= self.lr * tau * gt
-        if "kappa" in self.learn:
-            self.log_kappa -= self.lr * kappa * gk
-        if "beta" in self.learn:
-            self.beta -= self.lr * gb
+        d_tau = tau * gt if "tau" in self.learn else 0.0 * gt
+        d_kappa = kappa * gk if "kappa" in self.learn else 0.0 * gk
+        d_beta = gb if "beta" in self.learn else 0.0 * gb
+        scale = self.lr
+        if self.normalize:
+            norm = np.sqrt(np.sum(d_tau ** 2) + np.sum(d_kappa ** 2) + np.sum(d_beta ** 2))
+            scale = self.lr / norm if norm > 0 else 0.0
+        self.log_tau -= scale * d_tau
+        self.log_kappa -= scale * d_kappa
+        self.beta -= scale * d_beta
         self.X, self.lam = X, lam
         rec = {"loss": float(loss), "forward_iterations": info["iterations"],
                "adjoint_iterations": info_b["iterations"], "tau": tau.tolist(),
