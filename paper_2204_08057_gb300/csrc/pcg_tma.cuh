@@ -547,53 +547,89 @@ struct ApplyXLayout {
 template <int K, int M, int E>
 __global__ void __launch_bounds__(WS_THREADS, 3)
 k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R,
-            unsigned int* error) {
+            unsigned int* ctr) {
+  // ctr[0]: timeout flag; ctr[1]: next tile; ctr[2]: CTAs done (both zero between launches).
+  // Tiles are taken from ctr[1] one ahead, so CTAs on faster SMs take more of them; there are
+  // no partial sums here, so how the tiles are split changes nothing in the result.  A tile
+  // index >= ntiles stops the consumers.  A tile's columns run back to back.
   using L = ApplyXLayout<K, M, E>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 1> sh;
   __shared__ __align__(8) PipeShared ps;
+  __shared__ int utile[NSTAGE], ucol[NSTAGE];
   stage_operator<float, 1>(op, K, sh);
   if (threadIdx.x == 0) pipe_init(ps);
   __syncthreads();
   const int64_t ldu = op.ldu;
   const int ntiles = (int)(op.n / TILE_PX);
-  const int ntl = (int)blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const int nunits = ntl * R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int consumed = 0;
   if (warp == NCONS) {
-    producer_loop(ps, nunits, [&](int u, int st) {
-      const int tile = blockIdx.x + (u / R) * gridDim.x;   // a tile's columns back to back
-      const int r = u % R;
-      const int64_t base = (int64_t)tile * TILE_PX;
-      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
-      const uint32_t rowb = TILE_PX * 4;
-      if (lane == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(&ps.full[st], (uint32_t)L::ROWS * rowb);
+    int next = 0, u = 0;
+    if (lane == 0) next = (int)atomicAdd(ctr + 1, 1u);
+    bool stop = false;
+    while (!stop) {
+      const int tile = __shfl_sync(0xffffffffu, next, 0);
+      const bool end = tile >= ntiles;
+      if (!end && lane == 0) next = (int)atomicAdd(ctr + 1, 1u);
+      const int nu = end ? 1 : R;
+      for (int r = 0; r < nu; ++r, ++u) {
+        const int st = u % NSTAGE;
+        if (u >= NSTAGE) {
+          bool ok = true;
+          if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NSTAGE) - 1) & 1);
+          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+          if (!ok || ps.bad) {
+            if (lane == 0) ps.bad = 1;
+            stop = true;
+            break;
+          }
+        }
+        if (lane == 0) {
+          utile[st] = end ? -1 : tile;
+          ucol[st] = r;
+        }
+        __syncwarp();
+        if (end) {
+          if (lane == 0) mbar_arrive(&ps.full[st]);
+        } else {
+          const int64_t base = (int64_t)tile * TILE_PX;
+          float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+          const uint32_t rowb = TILE_PX * 4;
+          if (lane == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(&ps.full[st], (uint32_t)L::ROWS * rowb);
+          }
+          __syncwarp();
+          const size_t xoff = (size_t)r * K * ldu;
+          for (int q = lane; q < L::ROWS; q += 32) {
+            const void* src;
+            if (q < K) src = X + xoff + (size_t)q * ldu + base;
+            else if (q < L::VAL) src = op.D32 + (size_t)(q - L::D) * op.ld + base;
+            else if (q < L::DIAG) src = op.ell_val32 + (size_t)(q - L::VAL) * op.ld + base;
+            else if (q == L::DIAG) src = op.diag32 + base;
+            else src = op.ell_col + (size_t)(q - L::COL) * op.ld + base;
+            bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
+          }
+        }
+        if (lane == 0) ps.issued = u + 1;
       }
-      __syncwarp();
-      const size_t xoff = (size_t)r * K * ldu;
-      for (int q = lane; q < L::ROWS; q += 32) {
-        const void* src;
-        if (q < K) src = X + xoff + (size_t)q * ldu + base;
-        else if (q < L::VAL) src = op.D32 + (size_t)(q - L::D) * op.ld + base;
-        else if (q < L::DIAG) src = op.ell_val32 + (size_t)(q - L::VAL) * op.ld + base;
-        else if (q == L::DIAG) src = op.diag32 + base;
-        else src = op.ell_col + (size_t)(q - L::COL) * op.ld + base;
-        bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
-      }
-    });
+      if (end) stop = true;
+    }
   } else {
     const int t = threadIdx.x;
-    for (int u = 0; u < nunits; ++u) {
+    for (int u = 0;; ++u) {
       const int st = u % NSTAGE;
       if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
         ps.bad = 1;
         break;
       }
-      const int tile = blockIdx.x + (u / R) * gridDim.x;   // a tile's columns back to back
-      const int r = u % R;
+      const int tile = utile[st];
+      if (tile < 0) {
+        consumed = u + 1;
+        break;
+      }
+      const int r = ucol[st];
       const int64_t base = (int64_t)tile * TILE_PX;
       const int64_t i = base + t;
       const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
@@ -649,10 +685,20 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
     }
   }
   __syncthreads();
-  if (ps.bad && threadIdx.x == 0) {
-    atomicOr(error, 1u);
-    for (int u = consumed; u < ps.issued; ++u)
-      mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+  if (threadIdx.x == 0) {
+    if (ps.bad) {
+      atomicOr(ctr, 1u);
+      for (int u = consumed; u < ps.issued; ++u)
+        mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+    }
+    // every CTA's producer has finished taking tiles when its CTA gets here; the last CTA
+    // resets the counters for the next launch
+    __threadfence();
+    if (atomicAdd(ctr + 2, 1u) == gridDim.x - 1u) {
+      ctr[1] = 0u;
+      ctr[2] = 0u;
+      __threadfence();
+    }
   }
 }
 

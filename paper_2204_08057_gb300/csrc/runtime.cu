@@ -137,7 +137,8 @@ struct sylv_ctx {
   double* w64 = nullptr;
   double* blk64 = nullptr;
   double* fac64 = nullptr;
-  unsigned int* apply_err = nullptr;  // timeout flag of the staged stand-alone apply
+  unsigned int* apply_err = nullptr;  // staged stand-alone apply: timeout flag, tile counter,
+                                      // CTAs done
   float* fs32 = nullptr;
   __half2* fl16 = nullptr;
   std::unique_ptr<Plan> plan[2];  // single-system plans, [inner_double]
@@ -1151,8 +1152,8 @@ int sylv_apply(sylv_handle h, const void* X, void* Y, int nrhs, int dtype, sylv_
   DeviceGuard g(h->device);
   if (dtype == SYLV_F32) {
     if (!h->apply_err) {
-      CK(dalloc(&h->apply_err, sizeof(unsigned int)));
-      CK(cudaMemset(h->apply_err, 0, sizeof(unsigned int)));
+      CK(dalloc(&h->apply_err, 3 * sizeof(unsigned int)));
+      CK(cudaMemset(h->apply_err, 0, 3 * sizeof(unsigned int)));
     }
     cudaError_t e = g_staged_apply ? launch_apply_staged(h->op, (const float*)X, (float*)Y, nrhs,
                                                          h->apply_err, (cudaStream_t)s)
