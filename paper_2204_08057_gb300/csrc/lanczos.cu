@@ -12,17 +12,17 @@
 // (N^{-1} Q_0 + rho_l) m_l = Yhat u_l at once (Lhat = U diag(rho) U^{-1}).
 //
 // GPU design (one inner run = Algorithm 5's first pass):
-//   * The basis is kept in HBM as raw blocks Vt_s with V_s = Vt_s N_s (N_s upper triangular,
-//     the inverse Cholesky factor of the block's N-Gram matrix, applied on the fly), so a block
-//     is written once and read back by the next two passes and by the final assembly
-//     M = sum_s V_s G_s (eq. soln-darstellung).  The paper regenerates the blocks in a second
+//   * The basis is kept in HBM as raw blocks Vt_s = V_s B_s (B_s upper triangular, the Cholesky
+//     factor of the block's N-Gram matrix; the passes form V_s = Vt_s B_s^{-1} per pixel by
+//     forward substitution), so a block is written once and read back by the next two passes
+//     and by the final assembly M = sum_s V_s G_s (eq. soln-darstellung).  The paper regenerates the blocks in a second
 //     Lanczos pass instead; on GB300 the basis fits in memory, and the second pass diverges
 //     when B_0 is ill conditioned (as it is for power-law mixing over the Planck channels).
 //   * Per Lanczos step two kernels: pass A (W = N^{-1} Q_0 V_s - V_{s-1} B_s^T with the
 //     stencil of Algorithm 1 on Vt_s, partial sums of H_s = V_s^T N W), pass B
 //     (Vt_{s+1} = W - V_s H_s, partial sums of its N-Gram matrix S).  The last CTA of pass B
 //     (atomic counter, fixed-order sums, no waiting) forms B_{s+1} = chol(S) (the N-orthonormal
-//     QR of Algorithm 4 as a Cholesky QR) and its inverse, and records H_s, B_{s+1}.
+//     QR of Algorithm 4 as a Cholesky QR) and records H_s, B_{s+1}.
 //   * The residual estimate of Algorithm 5 is evaluated on the host at every poll from the
 //     recorded blocks, by one block-LDL^T step per shift and step: the last block z_l of
 //     (T_s + rho_l I)^{-1} E_1 B_0 u_l gives gamma = sum_l ||B_{s+1} z_l||^2, the same number
@@ -33,9 +33,10 @@
 //     N-norm before its Cholesky QR (Yhat U Sigma^{-1}; same span, so the same Krylov space),
 //     which keeps the Gram matrix well conditioned when Lhat is.
 //   * After the run the host solves the k shifted block-tridiagonal systems for Z (eq.
-//     soln-constr, Z = Zhat U^{-1}), and one kernel adds M = sum_s Vt_s (N_s G_s) to X.
-//   * Mixed precision: the basis, the operator and the per-thread partial sums in FP32, the
-//     block reductions, the small k x k algebra and X in FP64; an outer loop forms the true
+//     soln-constr, Z = Zhat U^{-1}), and one kernel adds M = sum_s Vt_s (B_s^{-1} G_s) to X.
+//   * Mixed precision: the basis, the operator, the partial sums within a CTA and the k x k
+//     Cholesky in FP32, the sums across CTAs in two-float arithmetic, the residual estimate,
+//     the coefficients and X in FP64; an outer loop forms the true
 //     residual B - G X in FP64 (the FP64 pixel-block operator) and restarts the Lanczos run on
 //     it until ||B - G X|| / ||B|| <= tol.  In FP64 mode the same loop runs with an FP64 basis.
 #include <algorithm>
@@ -59,7 +60,7 @@ constexpr int NSMAX = KMAX * (KMAX + 1) / 2;   // packed symmetric k x k
 constexpr int NVMAX = NSMAX + 2;               // partial sums per CTA (start kernel: + 2)
 constexpr int GCHUNK = 32;                     // assembly coefficient blocks staged at a time
 
-enum Done : int { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, CAPPED = 3, NONFINITE = 4 };
+enum Done : int { RUNNING = 0, BREAKDOWN = 2, CAPPED = 3 };
 
 struct Ctl {
   int step;           // Lanczos steps completed in the current inner run
@@ -95,7 +96,6 @@ struct Args {
   Coef* co;
   double* histH;           // cap x k*k: H_s
   double* histB;           // cap x k*k: B_{s+1}
-  double* histN;           // cap x k*k: unused by the kernels (host-side N_s = B_s^{-1})
   const double* G;         // nsteps x k*k: assembly coefficients N_s G_s
   const double* B;         // caller right-hand side, k x ldu
   double* X;               // caller solution, k x ldu
@@ -188,43 +188,6 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   r.lo = r.lo - (s - r.hi);
   r.hi = s;
   return r;
-}
-
-// Dekker's exact product with a fused multiply-add, and the products, sums, reciprocal square
-// root (FP32 seed, one Newton step in two-float arithmetic) used by the small k x k algebra
-__device__ __forceinline__ FF ff_fast(float a, float b) {   // |a| >= |b|
-  const float s = a + b;
-  return FF{s, b - (s - a)};
-}
-
-__device__ __forceinline__ FF ff_sum(FF x, FF y) {
-  const float s = x.hi + y.hi;
-  const float bb = s - x.hi;
-  const float e = (x.hi - (s - bb)) + (y.hi - bb);
-  return ff_fast(s, e + x.lo + y.lo);
-}
-
-__device__ __forceinline__ FF ff_mul(FF x, FF y) {
-  const float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  return ff_fast(p, e);
-}
-
-__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
-
-__device__ __forceinline__ FF ff_of(double d) {
-  const float hi = float(d);
-  return FF{hi, float(d - double(hi))};
-}
-
-__device__ __forceinline__ double ff_dbl(FF x) { return double(x.hi) + double(x.lo); }
-
-__device__ __forceinline__ FF ff_rsqrt(FF x) {
-  const FF r{rsqrtf(x.hi), 0.f};
-  const FF e = ff_sum(FF{1.f, 0.f}, ff_neg(ff_mul(x, ff_mul(r, r))));   // 1 - x r^2
-  return ff_sum(r, ff_mul(r, FF{0.5f * e.hi, 0.5f * e.lo}));
 }
 
 __device__ __forceinline__ FF warp_sum_ff(FF v) {
@@ -1254,7 +1217,7 @@ struct Work {   // per inner type
   double* partial = nullptr;
   Ctl* ctl = nullptr;
   Coef* co = nullptr;
-  double* hist = nullptr;      // histH | histB | histN | G, each cap x k*k
+  double* hist = nullptr;      // histH | histB | (spare) | G, each cap x k*k
   Ctl* h_ctl = nullptr;        // pinned
   double* h_hist = nullptr;    // pinned, 3 x cap x k*k
   double* h_tot = nullptr;     // pinned, NVMAX
@@ -1554,7 +1517,6 @@ Args make_args(const OpData& op, const Cache& C, Work& w) {
   const size_t kk = (size_t)op.k * op.k;
   a.histH = w.hist;
   a.histB = w.hist + (size_t)w.cap_blocks * kk;
-  a.histN = w.hist + (size_t)2 * w.cap_blocks * kk;
   a.G = w.hist + (size_t)3 * w.cap_blocks * kk;
   a.kap2 = C.kappa0 * C.kappa0;
   for (int j = 0; j < op.k; ++j) a.phinv[j] = 1.0 / C.phi[j];
