@@ -268,6 +268,65 @@ __device__ __forceinline__ bool reduce_last(const float (&v)[NV], S& sh, double*
   return true;
 }
 
+// The same with a scratch area in shared memory (the staged kernels' free stage buffers,
+// blockDim.x * NV * 2 floats): instead of NV warp trees in every warp, the per-thread values are
+// transposed through shared memory and SEG threads per value add blockDim.x / SEG rows each,
+// then SEG-lane shuffles finish; likewise for the two-float sums of the last CTA.
+template <int NV, typename S>
+__device__ __forceinline__ bool reduce_last_t(const float (&v)[NV], S& sh, double* partial,
+                                              unsigned* counter, float* scratch) {
+  constexpr int SEG = 8;
+  // blockDim.x is a multiple of SEG and at least SEG * NV
+  const int nt = (int)blockDim.x, rows = nt / SEG;
+  float* pf = reinterpret_cast<float*>(partial);
+  const int x = threadIdx.x, val = x / SEG, part = x % SEG;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) scratch[t * nt + x] = v[t];
+  __syncthreads();
+  if (x < ((SEG * NV + 31) / 32) * 32) {   // whole warps, so the shuffles are full-warp
+    float s = 0.f;
+    if (val < NV)
+      for (int r = part * rows; r < (part + 1) * rows; ++r) s += scratch[val * nt + r];
+#pragma unroll
+    for (int off = SEG / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, SEG);
+    if (val < NV && part == 0) pf[(size_t)val * gridDim.x + blockIdx.x] = s;
+  }
+  if (!arrive_last(sh, counter)) return false;
+  FF acc[NV];
+#pragma unroll
+  for (int t = 0; t < NV; ++t) acc[t] = FF{0.f, 0.f};
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    float y[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) y[t] = __ldcg(pf + (size_t)t * gridDim.x + b);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] = ff_add(acc[t], y[t]);
+  }
+  __syncthreads();   // scratch is reused
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    scratch[(t * nt + x) * 2] = acc[t].hi;
+    scratch[(t * nt + x) * 2 + 1] = acc[t].lo;
+  }
+  __syncthreads();
+  if (x < ((SEG * NV + 31) / 32) * 32) {
+    FF s{0.f, 0.f};
+    if (val < NV)
+      for (int r = part * rows; r < (part + 1) * rows; ++r)
+        s = ff_add(s, FF{scratch[(val * nt + r) * 2], scratch[(val * nt + r) * 2 + 1]});
+#pragma unroll
+    for (int off = SEG / 2; off > 0; off >>= 1) {
+      FF o;
+      o.hi = __shfl_down_sync(0xffffffffu, s.hi, off, SEG);
+      o.lo = __shfl_down_sync(0xffffffffu, s.lo, off, SEG);
+      s = ff_add(s, o);
+    }
+    if (val < NV && part == 0) sh.tot[val] = double(s.hi) + double(s.lo);
+  }
+  __syncthreads();
+  return true;
+}
+
 // FP64 per-thread values (FP64 kernels and the start kernel).
 template <int NV, typename S>
 __device__ __forceinline__ bool reduce_last(const double (&v)[NV], S& sh, double* partial,
@@ -359,9 +418,9 @@ __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
   using AR = Arith<T>;
   using V = typename AR::V;
   const int lane = threadIdx.x & 31;
-  double tr = 0.0;
+  float tr = 0.f;
 #pragma unroll
-  for (int p = 0; p < K; ++p) tr += sh.tot[p * K - p * (p - 1) / 2];
+  for (int p = 0; p < K; ++p) tr += float(sh.tot[p * K - p * (p - 1) / 2]);
   V col[K], Rc[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -370,7 +429,7 @@ __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
     col[i] = lane < K ? AR::of(sh.tot[p0 * K - p0 * (p0 - 1) / 2 + (q0 - p0)]) : AR::of(0.0);
     Rc[i] = AR::of(0.0);
   }
-  const float thr = float((sizeof(T) == 4 ? 1e-12 : 1e-26) * tr);
+  const float thr = (sizeof(T) == 4 ? 1e-12f : 1e-26f) * tr;
   V rinv[K];
   bool bad = false;
 #pragma unroll
@@ -393,10 +452,11 @@ __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
   if (lane < K) {
     double* hb = a.histB + (size_t)(s - 1) * K * K;
     Coef* co = a.co;
+    // the factor this kernel used (staged in shared memory at its start) becomes the previous
     double prev[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i) prev[i] = co->Rc[i * KMAX + lane];
-    const double prevri = co->rci[lane];
+    for (int i = 0; i < K; ++i) prev[i] = double(sh.Rc[i][lane]);
+    const double prevri = double(sh.rci[lane]);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const double rb = AR::dbl(Rc[i]);
@@ -840,7 +900,14 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
     }
   }
   if (staged_failed(ps, consumed, a.ctl)) return;
-  if (!reduce_last<NS>(acc, sh, a.partial, &a.ctl->counter)) return;
+  // the transposed reduction needs 8 threads per value and the stage ring as scratch
+  if constexpr (8 * NS <= WS_THREADS &&
+                (size_t)WS_THREADS * NS * 8 <= (size_t)L::NST * L::STAGE_BYTES) {
+    if (!reduce_last_t<NS>(acc, sh, a.partial, &a.ctl->counter, reinterpret_cast<float*>(dsm)))
+      return;
+  } else {
+    if (!reduce_last<NS>(acc, sh, a.partial, &a.ctl->counter)) return;
+  }
   if (threadIdx.x == 0) {
     int t = 0;
     double* hh = a.histH + (size_t)(s - 1) * K * K;
@@ -942,7 +1009,13 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
     }
   }
   if (staged_failed(ps, consumed, a.ctl)) return;
-  if (!reduce_last<NS>(acc, sh, a.partial, &a.ctl->counter)) return;
+  if constexpr (8 * NS <= WS_THREADS &&
+                (size_t)WS_THREADS * NS * 8 <= (size_t)NST_B * L::STAGE_BYTES) {
+    if (!reduce_last_t<NS>(acc, sh, a.partial, &a.ctl->counter, reinterpret_cast<float*>(dsm)))
+      return;
+  } else {
+    if (!reduce_last<NS>(acc, sh, a.partial, &a.ctl->counter)) return;
+  }
   if (threadIdx.x < 32) {
     const bool ok = qr_coefficients<K, float>(a, s, sh);
     if (threadIdx.x == 0) {
