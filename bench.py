@@ -687,7 +687,9 @@ def bytes_lanczos_b(k, s=4):
 def run_sylvester(args):
     """Separable special case of the workload (noise d_ci = t_c nu_i, one prior shape): time
     to relres 1e-8 of the block-Lanczos Sylvester solver (mixed and FP64) against the
-    preconditioned CG (mixed and FP64) on the same system."""
+    preconditioned CG (mixed and FP64) on the same system, and against CG with no
+    preconditioner on the Kronecker-structured system, the comparison of Sec. 4 (one solve
+    each; thousands of iterations)."""
     import torch
     import synth
     from paper_2204_08057_gb300 import build as _build
@@ -708,6 +710,10 @@ def run_sylvester(args):
     def cg(prec):
         return op.solve(B, precision=prec, **kw)
 
+    def cg_plain(prec):
+        from paper_2204_08057_gb300 import binding as _B
+        return op.solve(B, precision=prec, precond=_B.SYLV_PRECOND_NONE, maxit=100000, **kw)
+
     for _ in range(args.warmup):
         lz(1)
         cg(1)
@@ -721,7 +727,9 @@ def run_sylvester(args):
     lz(0)
     ms_lz64, (X_lz64, info_lz64) = _timed(stream, lambda: lz(0), args.fp64_steps)
     ms_cg64, (_, info_cg64) = _timed(stream, lambda: cg(0), args.fp64_steps)
-    for inf in (info_lz, info_cg, info_lz64, info_cg64):
+    ms_cgp, (_, info_cgp) = _timed(stream, lambda: cg_plain(1), 1)
+    ms_cgp64, (_, info_cgp64) = _timed(stream, lambda: cg_plain(0), 1)
+    for inf in (info_lz, info_cg, info_lz64, info_cg64, info_cgp, info_cgp64):
         assert inf["code"] == 0, inf
     # kernel breakdown from one more solve with CUDA events around every launch
     _, info_prof = lz(1, profile=1)
@@ -747,6 +755,11 @@ def run_sylvester(args):
         "lanczos_fp64": summary(ms_lz64, info_lz64),
         "pcg_mixed": summary(ms_cg, info_cg),
         "pcg_fp64": summary(ms_cg64, info_cg64),
+        "cg_mixed_no_preconditioner": summary(ms_cgp, info_cgp),
+        "cg_fp64_no_preconditioner": summary(ms_cgp64, info_cgp64),
+        "lanczos_time_share_of_cg": {"mixed": ms_lz / ms_cgp, "fp64": ms_lz64 / ms_cgp64,
+                                     "note": "Sec. 4 compares the Sylvester method with CG "
+                                             "applied directly to the Kronecker system"},
         "speedup_vs_pcg_mixed": ms_cg / ms_lz, "speedup_vs_pcg_fp64": ms_cg64 / ms_lz,
         "relerr_lanczos_vs_pcg": rel,
         "kernel_ms_per_solve": {"pass_a": info_prof["ms_apply"], "pass_b": info_prof["ms_update"],
@@ -766,7 +779,8 @@ def run_sylvester(args):
 def run_paper_model(args):
     """The paper's model (App. B mixing and weights, App. C intrinsic GMRF prior phi L^2) on the
     1024 x 2048 sphere: time to relres 1e-8 by mixed PCG, FP64 PCG and mixed Lanczos-Sylvester
-    (the model is separable: C = T kron N, one prior shape)."""
+    (the model is separable: C = T kron N, one prior shape), and by CG with no preconditioner
+    on the Kronecker-structured system, the method Sec. 4 compares the Sylvester solver with."""
     import torch
     import synth
     from paper_2204_08057_gb300 import build as _build
@@ -799,7 +813,11 @@ def run_paper_model(args):
     ms_lz, (X_lz, info_lz) = _timed(stream, lambda: lz(1), args.steps)
     cg(0)
     ms64, (X64, info64) = _timed(stream, lambda: cg(0), args.fp64_steps)
-    for inf in (info, info_lz, info64):
+    from paper_2204_08057_gb300 import binding as _B
+    plain = dict(precond=_B.SYLV_PRECOND_NONE, maxit=100000)
+    ms_p, (_, info_p) = _timed(stream, lambda: cg(1, **plain), 1)
+    ms_p64, (_, info_p64) = _timed(stream, lambda: cg(0, **plain), 1)
+    for inf in (info, info_lz, info64, info_p, info_p64):
         assert inf["code"] == 0, inf
     _, info_prof = cg(1, profile=1)
     E = int(op_degree(p))
@@ -818,6 +836,11 @@ def run_paper_model(args):
         "setup_ms": setup_ms,
         "pcg_mixed": summary(ms, info), "pcg_fp64": summary(ms64, info64),
         "lanczos_mixed": summary(ms_lz, info_lz),
+        "cg_mixed_no_preconditioner": summary(ms_p, info_p),
+        "cg_fp64_no_preconditioner": summary(ms_p64, info_p64),
+        "lanczos_time_share_of_cg": {"mixed": ms_lz / ms_p,
+                                     "note": "Sec. 4 compares the Sylvester method with CG "
+                                             "applied directly to the Kronecker system"},
         "speedup_mixed_vs_fp64": ms64 / ms,
         "relerr_mixed_vs_fp64": float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64)),
         "relerr_lanczos_vs_fp64": float(torch.linalg.norm(X_lz - X64) / torch.linalg.norm(X64)),

@@ -68,6 +68,8 @@ struct Ctl {
   int cap;            // steps allowed in this run (basis capacity and iteration budget)
   unsigned counter;   // last-CTA detection, zero between kernels
   unsigned err;       // nonzero: a bounded wait of a staged kernel expired (SYLV_E_TIMEOUT)
+  int sa;             // staged passes: the last step whose pass B ran (pass A runs sa + 1)
+  int sb;             // staged passes: the step whose pass A ran last (pass B runs it)
   int pad;
 };
 
@@ -79,6 +81,8 @@ struct Coef {
   double rci[KMAX];               // 1 / diagonal of B_s
   double rpi[KMAX];               // 1 / diagonal of B_{s-1}
   double H[KMAX * KMAX];          // H_s
+  double R2[2][KMAX * KMAX];      // staged passes: B_s in slot s & 1 (slot 1 starts as B_1)
+  double ri2[2][KMAX];            // and the reciprocals of its diagonal
   double tot[NVMAX];              // start kernel: Gram matrix of the start block, ||r||^2, ||B||^2
 };
 
@@ -92,6 +96,9 @@ struct Args {
   int64_t bstride;         // elements per block
   void* wbuf;              // k x ld
   double* partial;         // gridDim.x x NVMAX
+  float* partA;            // staged pass A partial sums, value-major, stride gpA
+  float* partB;            // staged pass B partial sums, value-major, stride gpB
+  int gpA, gpB;            // the producing grid rounded up to 32 (padding stays zero)
   Ctl* ctl;
   Coef* co;
   double* histH;           // cap x k*k: H_s
@@ -268,17 +275,21 @@ __device__ __forceinline__ bool reduce_last(const float (&v)[NV], S& sh, double*
   return true;
 }
 
-// The same with a scratch area in shared memory (the staged kernels' free stage buffers,
-// blockDim.x * NV * 2 floats): instead of NV warp trees in every warp, the per-thread values are
-// transposed through shared memory and SEG threads per value add blockDim.x / SEG rows each,
-// then SEG-lane shuffles finish; likewise for the two-float sums of the last CTA.
-template <int NV, typename S>
-__device__ __forceinline__ bool reduce_last_t(const float (&v)[NV], S& sh, double* partial,
-                                              unsigned* counter, float* scratch) {
+// Staged passes elect no last CTA.  At its end every CTA writes its FP32 partial sums
+// (value-major with stride gp, the producing grid rounded up to 32 and zero padded), and every
+// CTA of the next pass forms the totals itself at its start while its producer warp is already
+// filling the stage ring.  All CTAs add in the same order, so they hold identical totals (and
+// identical k x k factors); no CTA of a pass waits for the others at its end.
+//
+// Per-CTA sums, with the free stage ring as scratch (blockDim.x * NV floats): the per-thread
+// values are transposed through shared memory, SEG threads per value add blockDim.x / SEG rows
+// each and SEG-lane shuffles finish.
+template <int NV>
+__device__ __forceinline__ void write_partials_t(const float (&v)[NV], float* pf, int gp,
+                                                 float* scratch) {
   constexpr int SEG = 8;
   // blockDim.x is a multiple of SEG and at least SEG * NV
   const int nt = (int)blockDim.x, rows = nt / SEG;
-  float* pf = reinterpret_cast<float*>(partial);
   const int x = threadIdx.x, val = x / SEG, part = x % SEG;
 #pragma unroll
   for (int t = 0; t < NV; ++t) scratch[t * nt + x] = v[t];
@@ -289,42 +300,59 @@ __device__ __forceinline__ bool reduce_last_t(const float (&v)[NV], S& sh, doubl
       for (int r = part * rows; r < (part + 1) * rows; ++r) s += scratch[val * nt + r];
 #pragma unroll
     for (int off = SEG / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, SEG);
-    if (val < NV && part == 0) pf[(size_t)val * gridDim.x + blockIdx.x] = s;
+    if (val < NV && part == 0) pf[(size_t)val * gp + blockIdx.x] = s;
   }
-  if (!arrive_last(sh, counter)) return false;
-  FF acc[NV];
+}
+
+// Named barrier of the NCS consumer threads (the producer warp is not part of it).
+template <int NCS>
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(NCS) : "memory");
+}
+
+// Totals of NV values over the partials of one grid (stride gp, a multiple of 32, zero
+// padded), as doubles in tot[0 .. NV); run by threads 0 .. NCS - 1, which meet at the named
+// barrier afterwards.  SEG lanes per value; lane p adds the 4-vectors p, p + SEG, ... in
+// two-float arithmetic (one accumulator per vector component), then SEG-lane shuffles.
+template <int NV, int NCS>
+__device__ __forceinline__ void sum_partials(const float* pf, int gp, double* tot) {
+  constexpr int SEG = 8, NGRP = NCS / SEG, BATCH = 8;
+  const int x = threadIdx.x, grp = x / SEG, part = x % SEG;
+  const int nq = gp / 4;
+#pragma unroll 1
+  for (int v0 = 0; v0 < NV; v0 += NGRP) {
+    const int v = v0 + grp;
+    FF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (v < NV) {
+      const float4* p4 = reinterpret_cast<const float4*>(pf + (size_t)v * gp);
+#pragma unroll 1
+      for (int q0 = part; q0 < nq; q0 += SEG * BATCH) {
+        float4 y[BATCH];
 #pragma unroll
-  for (int t = 0; t < NV; ++t) acc[t] = FF{0.f, 0.f};
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-    float y[NV];
+        for (int b = 0; b < BATCH; ++b) {   // every load of the batch before any add
+          const int q = q0 + b * SEG;
+          y[b] = q < nq ? __ldcg(p4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
-    for (int t = 0; t < NV; ++t) y[t] = __ldcg(pf + (size_t)t * gridDim.x + b);
-#pragma unroll
-    for (int t = 0; t < NV; ++t) acc[t] = ff_add(acc[t], y[t]);
-  }
-  __syncthreads();   // scratch is reused
-#pragma unroll
-  for (int t = 0; t < NV; ++t) {
-    scratch[(t * nt + x) * 2] = acc[t].hi;
-    scratch[(t * nt + x) * 2 + 1] = acc[t].lo;
-  }
-  __syncthreads();
-  if (x < ((SEG * NV + 31) / 32) * 32) {
-    FF s{0.f, 0.f};
-    if (val < NV)
-      for (int r = part * rows; r < (part + 1) * rows; ++r)
-        s = ff_add(s, FF{scratch[(val * nt + r) * 2], scratch[(val * nt + r) * 2 + 1]});
+        for (int b = 0; b < BATCH; ++b) {
+          acc[0] = ff_add(acc[0], y[b].x);
+          acc[1] = ff_add(acc[1], y[b].y);
+          acc[2] = ff_add(acc[2], y[b].z);
+          acc[3] = ff_add(acc[3], y[b].w);
+        }
+      }
+    }
+    FF t = ff_add(ff_add(acc[0], acc[1]), ff_add(acc[2], acc[3]));
 #pragma unroll
     for (int off = SEG / 2; off > 0; off >>= 1) {
       FF o;
-      o.hi = __shfl_down_sync(0xffffffffu, s.hi, off, SEG);
-      o.lo = __shfl_down_sync(0xffffffffu, s.lo, off, SEG);
-      s = ff_add(s, o);
+      o.hi = __shfl_down_sync(0xffffffffu, t.hi, off, SEG);
+      o.lo = __shfl_down_sync(0xffffffffu, t.lo, off, SEG);
+      t = ff_add(t, o);
     }
-    if (val < NV && part == 0) sh.tot[val] = double(s.hi) + double(s.lo);
+    if (v < NV && part == 0) tot[v] = double(t.hi) + double(t.lo);
   }
-  __syncthreads();
-  return true;
+  consumers_sync<NCS>();
 }
 
 // FP64 per-thread values (FP64 kernels and the start kernel).
@@ -413,24 +441,24 @@ __device__ __forceinline__ FF shfl_v<FF>(FF x, int src) {
 
 // Lane l of warp 0 holds column l of S, R and R^{-1} in registers; rows move between lanes by
 // shuffles.  Called by all 32 lanes of warp 0 (lanes >= K carry zero columns).
-template <int K, typename T, typename SM>
-__device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
+template <int K, typename T>
+__device__ __forceinline__ bool chol_lanes(const double* tot, typename Arith<T>::V (&Rc)[K],
+                                           typename Arith<T>::V (&rinv)[K]) {
   using AR = Arith<T>;
   using V = typename AR::V;
   const int lane = threadIdx.x & 31;
   float tr = 0.f;
 #pragma unroll
-  for (int p = 0; p < K; ++p) tr += float(sh.tot[p * K - p * (p - 1) / 2]);
-  V col[K], Rc[K];
+  for (int p = 0; p < K; ++p) tr += float(tot[p * K - p * (p - 1) / 2]);
+  V col[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     // packed upper triangle, row by row: entry (p, q), q >= p, at p K - p (p - 1) / 2 + q - p
     const int p0 = i < lane ? i : lane, q0 = i < lane ? lane : i;
-    col[i] = lane < K ? AR::of(sh.tot[p0 * K - p0 * (p0 - 1) / 2 + (q0 - p0)]) : AR::of(0.0);
+    col[i] = lane < K ? AR::of(tot[p0 * K - p0 * (p0 - 1) / 2 + (q0 - p0)]) : AR::of(0.0);
     Rc[i] = AR::of(0.0);
   }
   const float thr = (sizeof(T) == 4 ? 1e-12f : 1e-26f) * tr;
-  V rinv[K];
   bool bad = false;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -448,7 +476,16 @@ __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
       col[i] = AR::add(col[i], AR::neg(AR::mul(rji, Rc[j])));
     }
   }
-  if (bad) return false;
+  return !bad;
+}
+
+template <int K, typename T, typename SM>
+__device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
+  using AR = Arith<T>;
+  using V = typename AR::V;
+  const int lane = threadIdx.x & 31;
+  V Rc[K], rinv[K];
+  if (!chol_lanes<K, T>(sh.tot, Rc, rinv)) return false;
   if (lane < K) {
     double* hb = a.histB + (size_t)(s - 1) * K * K;
     Coef* co = a.co;
@@ -473,6 +510,43 @@ __device__ __noinline__ bool qr_coefficients(const Args& a, int s, SM& sh) {
     co->rci[lane] = own;
   }
   return true;
+}
+
+// Staged passes, warp 0: B = chol(S) of this CTA's totals into shared memory (FP32 Rc, rci).
+// With `rec` (one CTA) also its record: histB row `hrow` and, for slot >= 0, coefficient slot
+// `slot` for the passes that follow.
+template <int K, typename SM>
+__device__ __noinline__ bool factor_staged(const Args& a, SM& sh, bool rec, int hrow, int slot) {
+  const int lane = threadIdx.x & 31;
+  float Rc[K], rinv[K];
+  const bool ok = chol_lanes<K, float>(sh.tot, Rc, rinv);
+  if (ok && lane < K) {
+    float own = 0.f;   // rinv[j] is uniform over the lanes: lane j keeps its own
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j == lane) own = rinv[j];
+#pragma unroll
+    for (int i = 0; i < K; ++i) sh.Rc[i][lane] = Rc[i];
+    sh.rci[lane] = own;
+    if (rec) {
+      double* hb = a.histB + (size_t)hrow * K * K;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        hb[i * K + lane] = double(Rc[i]);
+        if (slot >= 0) a.co->R2[slot][i * KMAX + lane] = double(Rc[i]);
+      }
+      if (slot >= 0) a.co->ri2[slot][lane] = double(own);
+    }
+  }
+  return ok;
+}
+
+template <int K>
+__device__ __forceinline__ void load_slot(const Coef* co, int slot, float (&R)[KMAX][KMAX],
+                                          float (&ri)[KMAX]) {
+  for (int t = threadIdx.x; t < K * K; t += blockDim.x)
+    R[t / K][t % K] = float(co->R2[slot][(t / K) * KMAX + t % K]);
+  if (threadIdx.x < K) ri[threadIdx.x] = float(co->ri2[slot][threadIdx.x]);
 }
 
 // ---- start: r = B - G X (FP64), rotated and weighted start block, its N-Gram matrix ----------
@@ -725,11 +799,12 @@ __device__ __forceinline__ void pipe_init(Pipe<NST>& ps) {
   tma::fence_mbar_init();
 }
 
-// Producer warp: waits until the consumers released stage u % NST, then issues unit u.
+// Producer warp, units u0 .. u1 - 1: waits until the consumers released stage u % NST (from
+// the second round of the ring on), then issues unit u.
 template <int NST, typename Issue>
-__device__ __forceinline__ void producer(Pipe<NST>& ps, int nunits, Issue&& issue) {
+__device__ __forceinline__ void producer_range(Pipe<NST>& ps, int u0, int u1, Issue&& issue) {
   const int lane = threadIdx.x & 31;
-  for (int u = 0; u < nunits; ++u) {
+  for (int u = u0; u < u1; ++u) {
     const int st = u % NST;
     if (u >= NST) {
       bool ok = true;
@@ -774,16 +849,29 @@ __device__ __forceinline__ bool staged_failed(Pipe<NST>& ps, int consumed, Ctl* 
   return true;
 }
 
+// Copies issued before a run ends at the start of a pass: wait (bounded) until they landed.
+template <int NST>
+__device__ __forceinline__ void drain_issued(Pipe<NST>& ps) {
+  for (int u = 0; u < ps.issued; ++u) tma::mbar_wait_bounded(&ps.full[u % NST], (u / NST) & 1);
+}
+
+// Pass A, step s = Ctl::sa + 1.  The producer warp issues the first ring of stages at once;
+// meanwhile the consumers sum pass B's partials (the N-Gram matrix of Vt_s) and warp 0 factors
+// it, B_s = chol(S) (CTA 0 records it).  A breakdown, or a run that reached its cap, ends here.
 template <int K, int E>
 __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
   using L = LayoutA<K, E>;
   constexpr int NS = K * (K + 1) / 2;
+  static_assert(8 * NS <= WS_THREADS && (size_t)WS_THREADS * NS * 4 <= (size_t)L::NST * L::STAGE_BYTES,
+                "per-CTA sums need 8 threads per value and the stage ring as scratch");
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ Smem<float, WS_THREADS / 32> sh;
   __shared__ __align__(8) Pipe<L::NST> ps;
   if (a.ctl->done != RUNNING) return;
-  const int s = a.ctl->step + 1;
-  load_factors<K, float>(a.co, sh, s > 1);
+  const int s = a.ctl->sa + 1;
+  // B_{s-1} from its slot (s = 1: B_1 from the host, into the current factor)
+  if (s > 1) load_slot<K>(a.co, (s - 1) & 1, sh.Rp, sh.rpi);
+  else load_slot<K>(a.co, 1, sh.Rc, sh.rci);
   if (threadIdx.x == 0) pipe_init(ps);
   __syncthreads();
   const OpData& op = a.op;
@@ -794,34 +882,62 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
   const float kap2 = float(a.kap2);
   const int ntiles = (int)((n + TILE_PX - 1) / TILE_PX);
   const int nunits = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const int head = nunits < L::NST ? nunits : L::NST;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto issue = [&](int u, int st) {
+    const int64_t base = ((int64_t)blockIdx.x + (int64_t)u * gridDim.x) * TILE_PX;
+    float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+    const uint32_t rowb = TILE_PX * 4;
+    const int nrows = s > 1 ? L::ROWS : L::ROWS - K;
+    if (lane == 0) {
+      tma::fence_proxy_async();
+      tma::mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
+    }
+    __syncwarp();
+    for (int q = lane; q < L::ROWS; q += 32) {
+      const void* src = nullptr;
+      if (q < K) src = cur + (size_t)q * ld + base;
+      else if (q < 2 * K) src = s > 1 ? prev + (size_t)(q - K) * ld + base : nullptr;
+      else if (q < L::COL) src = op.ell_val32 + (size_t)(q - L::VAL) * ld + base;
+      else if (q < L::DIAG) src = op.ell_col + (size_t)(q - L::COL) * ld + base;
+      else if (q == L::DIAG) src = op.diag32 + base;
+      else if (q == L::NU) src = a.nu32 + base;
+      else src = a.nuinv32 + base;
+      if (src) tma::bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
+    }
+  };
+  if (warp == NCONS) {
+    producer_range(ps, 0, head, issue);
+  } else if (s > 1) {
+    sum_partials<NS, TILE_PX>(a.partB, a.gpB, sh.tot);
+    if (warp == 0) {
+      const bool rec = blockIdx.x == 0;
+      const bool ok = factor_staged<K>(a, sh, rec, s - 2, s & 1);
+      if (lane == 0) {
+        const int stop = !ok ? BREAKDOWN : (s - 1 >= a.ctl->cap ? CAPPED : RUNNING);
+        sh.flag = stop;
+        if (rec) {
+          a.ctl->step = s - 1;
+          if (stop != RUNNING) a.ctl->done = stop;
+          else a.ctl->sb = s;
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    sh.flag = RUNNING;
+    if (blockIdx.x == 0) a.ctl->sb = 1;
+  }
+  __syncthreads();
+  if (sh.flag != RUNNING) {
+    if (threadIdx.x == 0) drain_issued(ps);
+    return;
+  }
   int consumed = 0;
   float acc[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) acc[t] = 0.f;
   if (warp == NCONS) {
-    producer(ps, nunits, [&](int u, int st) {
-      const int64_t base = ((int64_t)blockIdx.x + (int64_t)u * gridDim.x) * TILE_PX;
-      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
-      const uint32_t rowb = TILE_PX * 4;
-      const int nrows = s > 1 ? L::ROWS : L::ROWS - K;
-      if (lane == 0) {
-        tma::fence_proxy_async();
-        tma::mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
-      }
-      __syncwarp();
-      for (int q = lane; q < L::ROWS; q += 32) {
-        const void* src = nullptr;
-        if (q < K) src = cur + (size_t)q * ld + base;
-        else if (q < 2 * K) src = s > 1 ? prev + (size_t)(q - K) * ld + base : nullptr;
-        else if (q < L::COL) src = op.ell_val32 + (size_t)(q - L::VAL) * ld + base;
-        else if (q < L::DIAG) src = op.ell_col + (size_t)(q - L::COL) * ld + base;
-        else if (q == L::DIAG) src = op.diag32 + base;
-        else if (q == L::NU) src = a.nu32 + base;
-        else src = a.nuinv32 + base;
-        if (src) tma::bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
-      }
-    });
+    producer_range(ps, head, nunits, issue);
   } else {
     const int t = threadIdx.x;
     for (int u = 0; u < nunits; ++u) {
@@ -900,42 +1016,24 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
     }
   }
   if (staged_failed(ps, consumed, a.ctl)) return;
-  // the transposed reduction needs 8 threads per value and the stage ring as scratch
-  if constexpr (8 * NS <= WS_THREADS &&
-                (size_t)WS_THREADS * NS * 8 <= (size_t)L::NST * L::STAGE_BYTES) {
-    if (!reduce_last_t<NS>(acc, sh, a.partial, &a.ctl->counter, reinterpret_cast<float*>(dsm)))
-      return;
-  } else {
-    if (!reduce_last<NS>(acc, sh, a.partial, &a.ctl->counter)) return;
-  }
-  if (threadIdx.x == 0) {
-    int t = 0;
-    double* hh = a.histH + (size_t)(s - 1) * K * K;
-    for (int p = 0; p < K; ++p)
-      for (int q = p; q < K; ++q, ++t) {
-        const double h = 0.5 * sh.tot[t];
-        a.co->H[p * KMAX + q] = h;
-        a.co->H[q * KMAX + p] = h;
-        hh[p * K + q] = h;
-        hh[q * K + p] = h;
-      }
-    a.ctl->counter = 0u;
-  }
+  write_partials_t<NS>(acc, a.partA, a.gpA, reinterpret_cast<float*>(dsm));
 }
 
+// Pass B, step s = Ctl::sb: the consumers first sum pass A's partials into H_s (CTA 0 records
+// it) while the producer fills the ring.
 template <int K>
 __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
   using L = LayoutB<K>;
   constexpr int NS = K * (K + 1) / 2;
+  static_assert(8 * NS <= WS_THREADS && (size_t)WS_THREADS * NS * 4 <= (size_t)NST_B * L::STAGE_BYTES,
+                "per-CTA sums need 8 threads per value and the stage ring as scratch");
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ Smem<float, WS_THREADS / 32> sh;
   __shared__ float Hs[KMAX][KMAX];
   __shared__ __align__(8) Pipe<NST_B> ps;
   if (a.ctl->done != RUNNING) return;
-  const int s = a.ctl->step + 1;
-  load_factors<K, float>(a.co, sh, false);
-  for (int t = threadIdx.x; t < K * K; t += blockDim.x)
-    Hs[t / K][t % K] = float(a.co->H[(t / K) * KMAX + t % K]);
+  const int s = a.ctl->sb;
+  load_slot<K>(a.co, s & 1, sh.Rc, sh.rci);
   if (threadIdx.x == 0) pipe_init(ps);
   __syncthreads();
   const int64_t ld = a.op.ld, n = a.op.n;
@@ -944,29 +1042,44 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
   const float* W = (const float*)a.wbuf;
   const int ntiles = (int)((n + TILE_PX - 1) / TILE_PX);
   const int nunits = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const int head = nunits < NST_B ? nunits : NST_B;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto issue = [&](int u, int st) {
+    const int64_t base = ((int64_t)blockIdx.x + (int64_t)u * gridDim.x) * TILE_PX;
+    float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+    const uint32_t rowb = TILE_PX * 4;
+    if (lane == 0) {
+      tma::fence_proxy_async();
+      tma::mbar_expect_tx(&ps.full[st], (uint32_t)L::ROWS * rowb);
+    }
+    __syncwarp();
+    for (int q = lane; q < L::ROWS; q += 32) {
+      const void* src;
+      if (q < K) src = W + (size_t)q * ld + base;
+      else if (q < 2 * K) src = cur + (size_t)(q - K) * ld + base;
+      else src = a.nu32 + base;
+      tma::bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
+    }
+  };
+  if (warp == NCONS) {
+    producer_range(ps, 0, head, issue);
+  } else {
+    sum_partials<NS, TILE_PX>(a.partA, a.gpA, sh.tot);
+    for (int t = threadIdx.x; t < K * K; t += TILE_PX) {
+      const int p = t / K, q = t % K, lo = p < q ? p : q, hi = p < q ? q : p;
+      const double h = 0.5 * sh.tot[lo * K - lo * (lo - 1) / 2 + (hi - lo)];
+      Hs[p][q] = float(h);
+      if (blockIdx.x == 0) a.histH[(size_t)(s - 1) * K * K + t] = h;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->sa = s;
+  }
+  __syncthreads();
   int consumed = 0;
   float acc[NS];
 #pragma unroll
   for (int t = 0; t < NS; ++t) acc[t] = 0.f;
   if (warp == NCONS) {
-    producer(ps, nunits, [&](int u, int st) {
-      const int64_t base = ((int64_t)blockIdx.x + (int64_t)u * gridDim.x) * TILE_PX;
-      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
-      const uint32_t rowb = TILE_PX * 4;
-      if (lane == 0) {
-        tma::fence_proxy_async();
-        tma::mbar_expect_tx(&ps.full[st], (uint32_t)L::ROWS * rowb);
-      }
-      __syncwarp();
-      for (int q = lane; q < L::ROWS; q += 32) {
-        const void* src;
-        if (q < K) src = W + (size_t)q * ld + base;
-        else if (q < 2 * K) src = cur + (size_t)(q - K) * ld + base;
-        else src = a.nu32 + base;
-        tma::bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
-      }
-    });
+    producer_range(ps, head, nunits, issue);
   } else {
     const int t = threadIdx.x;
     for (int u = 0; u < nunits; ++u) {
@@ -1009,21 +1122,26 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_b_tma(const Args a) {
     }
   }
   if (staged_failed(ps, consumed, a.ctl)) return;
-  if constexpr (8 * NS <= WS_THREADS &&
-                (size_t)WS_THREADS * NS * 8 <= (size_t)NST_B * L::STAGE_BYTES) {
-    if (!reduce_last_t<NS>(acc, sh, a.partial, &a.ctl->counter, reinterpret_cast<float*>(dsm)))
-      return;
-  } else {
-    if (!reduce_last<NS>(acc, sh, a.partial, &a.ctl->counter)) return;
-  }
+  write_partials_t<NS>(acc, a.partB, a.gpB, reinterpret_cast<float*>(dsm));
+}
+
+// End of a chunk of staged steps (one CTA of TILE_PX threads): B_{s+1} of the last step s from
+// pass B's sums, recorded so that the host sees it at the poll, and the stopping state; the next
+// pass A forms the same factor again.
+template <int K>
+__global__ void __launch_bounds__(TILE_PX, 1) k_lz_fin(const Args a) {
+  constexpr int NS = K * (K + 1) / 2;
+  __shared__ Smem<float, TILE_PX / 32> sh;
+  if (a.ctl->done != RUNNING) return;
+  const int s = a.ctl->sa;
+  if (s < 1) return;
+  sum_partials<NS, TILE_PX>(a.partB, a.gpB, sh.tot);
   if (threadIdx.x < 32) {
-    const bool ok = qr_coefficients<K, float>(a, s, sh);
+    const bool ok = factor_staged<K>(a, sh, true, s - 1, -1);
     if (threadIdx.x == 0) {
-      Ctl* ctl = a.ctl;
-      ctl->step = s;
-      if (!ok) ctl->done = BREAKDOWN;
-      else if (s >= ctl->cap) ctl->done = CAPPED;
-      ctl->counter = 0u;
+      a.ctl->step = s;
+      if (!ok) a.ctl->done = BREAKDOWN;
+      else if (s >= a.ctl->cap) a.ctl->done = CAPPED;
     }
   }
 }
@@ -1207,6 +1325,13 @@ cudaError_t launch_b_tma(const Args& a, int ncta, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_fin(const Args& a, cudaStream_t s) {
+#define CALL(K) k_lz_fin<K><<<1, TILE_PX, 0, s>>>(a)
+  LZ_DISPATCH_K(a.op.k, CALL)
+#undef CALL
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_assemble(const Args& a, int ncta, cudaStream_t s) {
 #define CALL(K) k_lz_assemble<K, T><<<ncta, NT, 0, s>>>(a)
@@ -1288,6 +1413,8 @@ struct Work {   // per inner type
   void* basis = nullptr;
   void* wbuf = nullptr;
   double* partial = nullptr;
+  float* partAB = nullptr;     // staged passes: pass A | pass B partial sums
+  int gpA = 0, gpB = 0;
   Ctl* ctl = nullptr;
   Coef* co = nullptr;
   double* hist = nullptr;      // histH | histB | (spare) | G, each cap x k*k
@@ -1306,6 +1433,7 @@ struct Work {   // per inner type
     cudaFree(basis);
     cudaFree(wbuf);
     cudaFree(partial);
+    cudaFree(partAB);
     cudaFree(ctl);
     cudaFree(co);
     cudaFree(hist);
@@ -1554,6 +1682,13 @@ int ensure_work(const OpData& op, Cache& C, int maxit, std::unique_ptr<Work>& sl
   }
   const int maxcta = *std::max_element(w->ncta, w->ncta + 6);
   LK(cudaMalloc(&w->partial, (size_t)maxcta * NVMAX * sizeof(double)));
+  if (w->staged) {   // value-major, stride rounded up to 32 CTAs; the padding stays zero
+    w->gpA = (w->ncta[4] + 31) / 32 * 32;
+    w->gpB = (w->ncta[5] + 31) / 32 * 32;
+    const size_t nf = (size_t)(w->gpA + w->gpB) * NSMAX;
+    LK(cudaMalloc(&w->partAB, nf * sizeof(float)));
+    LK(cudaMemset(w->partAB, 0, nf * sizeof(float)));
+  }
   LK(cudaMalloc(&w->ctl, sizeof(Ctl)));
   LK(cudaMemset(w->ctl, 0, sizeof(Ctl)));
   LK(cudaMalloc(&w->co, sizeof(Coef)));
@@ -1585,6 +1720,10 @@ Args make_args(const OpData& op, const Cache& C, Work& w) {
   a.bstride = (int64_t)op.k * op.ld;
   a.wbuf = w.wbuf;
   a.partial = w.partial;
+  a.partA = w.partAB;
+  a.partB = w.partAB ? w.partAB + (size_t)w.gpA * NSMAX : nullptr;
+  a.gpA = w.gpA;
+  a.gpB = w.gpB;
   a.ctl = w.ctl;
   a.co = w.co;
   const size_t kk = (size_t)op.k * op.k;
@@ -1608,6 +1747,8 @@ int launch_steps(Work& w, const Args& a, int iters, cudaStream_t s, bool capture
                  : cudaEventRecord(w.events[2 * it + 1], s));
     if (w.staged) LK(launch_b_tma(a, w.ncta[5], s));
     else LK(launch_b<T>(a, w.ncta[1], s));
+    // staged passes: the factor of the chunk's last step, for the poll
+    if (w.staged && it == iters - 1) LK(launch_fin(a, s));
     if (prof)
       LK(capture ? cudaEventRecordWithFlags(w.events[2 * it + 2], s, cudaEventRecordExternal)
                  : cudaEventRecord(w.events[2 * it + 2], s));
@@ -1897,6 +2038,8 @@ int run(sylv_handle h, const OpData& op, Cache& C, const double* B, double* X, i
         }
         init.rci[p] = 1.0 / cU[p * k + p];
       }
+      std::memcpy(init.R2[1], init.Rc, sizeof(init.Rc));   // staged passes read slot 1 at s = 1
+      std::memcpy(init.ri2[1], init.rci, sizeof(init.rci));
       double nB0 = 0.0;   // ||B_0||_F^2, B_0 = (B_0 U) U^{-1}
       for (int p = 0; p < k; ++p)
         for (int q = 0; q < k; ++q) {
@@ -1933,7 +2076,7 @@ int run(sylv_handle h, const OpData& op, Cache& C, const double* B, double* X, i
           rc = launch_steps<T>(w, a, iters, s, false, prof);
           if (rc != SYLV_OK) return rc;
         }
-        launches += 2L * iters;
+        launches += 2L * iters + (w.staged ? 1 : 0);
         const int cnt = std::min(iters, c0.cap - seen);
         LK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
         if (cnt > 0) {
