@@ -5,6 +5,41 @@ namespace sylv {
 
 bool tma_available(int k, int m, int e) { return special_shape(k, m, e); }
 
+namespace tma {
+
+// Chunk-closing kernel of the staged pair in modes 1 and 2 (launched over the update kernel's
+// CTA list; the slot-0 CTA of each system works): the state change of the last update of a
+// chunk, so that the host's poll and the next chunk see it.
+__global__ void __launch_bounds__(TILE_PX)
+k_inner_close(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, Control* ctl) {
+  __shared__ ColState cst[CS_RMAX];
+  __shared__ int want[RMAX];
+  __shared__ double red[32 * 2];
+  __shared__ double tot[CS_RMAX][NPART];
+  const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0 || cr.slot != 0) return;
+  const SysDesc& sd = descs[cr.sys];
+  const int R = sd.R;
+  if (R > CS_RMAX) return;
+  if (threadIdx.x < RMAX) {
+    const int r = threadIdx.x;
+    want[r] = 0;
+    if (r < R) {
+      cst[r] = sd.st[r];
+      want[r] = cst[r].phase == PH_INNER;
+    }
+  }
+  __syncthreads();
+  sum_slots<2>(sd.partial2, sd.nslots[1], R, want, red, tot);
+  if (threadIdx.x < R && want[threadIdx.x]) {
+    const int r = threadIdx.x;
+    after_update(cst[r], tot[r][0], tot[r][1], ctl, true);
+    sd.st[r] = cst[r];
+  }
+}
+
+}  // namespace tma
+
 namespace {
 
 template <int K, int M, int E>
@@ -17,7 +52,8 @@ size_t update_tma_smem() {
 }
 
 template <int K, int M, int E>
-cudaError_t apply_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl, cudaStream_t s) {
+cudaError_t apply_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl, int mode,
+                      cudaStream_t s) {
   static bool attr = false;
   const size_t smem = apply_tma_smem<K, M, E>();
   if (!attr) {
@@ -26,12 +62,12 @@ cudaError_t apply_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tma::k_inner_apply_tma<K, M, E><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
+  tma::k_inner_apply_tma<K, M, E><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl, mode);
   return cudaGetLastError();
 }
 
 template <int K, int M>
-cudaError_t update_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
+cudaError_t update_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl, int mode,
                        cudaStream_t s) {
   static bool attr = false;
   const size_t smem = update_tma_smem<K, M>();
@@ -41,7 +77,7 @@ cudaError_t update_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tma::k_inner_update_tma<K, M><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
+  tma::k_inner_update_tma<K, M><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl, mode);
   return cudaGetLastError();
 }
 
@@ -107,9 +143,9 @@ cudaError_t launch_apply_staged(const OpData& op, const float* X, float* Y, int 
 }
 
 #define SYLV_TMA_APPLY_(K_, M_, E_) \
-  if (k == K_ && m == M_ && e == E_) return apply_tma<K_, M_, E_>(ncta, d, c, ctl, s);
+  if (k == K_ && m == M_ && e == E_) return apply_tma<K_, M_, E_>(ncta, d, c, ctl, variant - 1, s);
 #define SYLV_TMA_UPDATE_(K_, M_, E_) \
-  if (k == K_ && m == M_ && e == E_) return update_tma<K_, M_>(ncta, d, c, ctl, s);
+  if (k == K_ && m == M_ && e == E_) return update_tma<K_, M_>(ncta, d, c, ctl, variant - 1, s);
 #define SYLV_TMA_OCC_(K_, M_, E_) \
   if (k == K_ && m == M_ && e == E_) return tma_occupancy<K_, M_, E_>(kind);
 
@@ -118,7 +154,7 @@ cudaError_t launch_inner_apply<float>(int k, int m, int e, int variant, int ncta
                                       const SysDesc* d, const CtaRef* c, Control* ctl,
                                       cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  if (variant == 1) {
+  if (variant >= 1 && variant <= 3) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_APPLY_)
   }
   return launch_inner_apply_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
@@ -128,7 +164,7 @@ cudaError_t launch_inner_update<float>(int k, int m, int e, int variant, int nct
                                        const SysDesc* d, const CtaRef* c, Control* ctl,
                                        cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  if (variant == 1) {
+  if (variant >= 1 && variant <= 3) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_UPDATE_)
   }
   return launch_inner_update_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
@@ -143,9 +179,16 @@ cudaError_t launch_update_x<float>(int k, int ncta, int block, const SysDesc* d,
                                    cudaStream_t s) {
   return launch_update_x_impl<float>(k, ncta, block, d, c, s);
 }
+cudaError_t launch_inner_close(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
+                               cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+  tma::k_inner_close<<<ncta, TILE_PX, 0, s>>>(d, c, ctl);
+  return cudaGetLastError();
+}
+
 template <>
 int occupancy<float>(int kind, int k, int m, int e, int variant, int block) {
-  if (variant == 1 && kind < 2) {
+  if (variant >= 1 && kind < 2) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_OCC_)
   }
   return occupancy_impl<float>(kind, k, m, e, block);

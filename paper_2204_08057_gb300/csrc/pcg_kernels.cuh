@@ -348,6 +348,72 @@ __device__ __forceinline__ void warp_accumulate(CtaShared<T, NV>& sh, int r,
   }
 }
 
+// Column state after an inner operator kernel with total p . q: alpha, or the end of the inner
+// solve (exact solution reached, or breakdown).  `count` keeps the active/unfinished counters.
+__device__ __forceinline__ void after_apply(ColState& cs, double pq, Control* ctl, bool count) {
+  if (pq > 0.0 && isfinite(pq)) {
+    cs.alpha = cs.gamma / pq;
+    cs.first = 0;
+  } else if (cs.rr_in == 0.0) {
+    cs.phase = PH_INNER_DONE;  // exact solution: nothing left to do
+    if (count) atomicSub(&ctl->n_active, 1u);
+  } else {
+    cs.phase = PH_FAILED;
+    cs.status = SYLV_E_BREAKDOWN;
+    if (count) {
+      atomicSub(&ctl->n_active, 1u);
+      atomicSub(&ctl->n_unfinished, 1u);
+    }
+  }
+}
+
+// Column state after an inner update with totals r . z and r . r: beta and gamma, or the end of
+// the inner solve (target reached, iteration cap, breakdown).
+__device__ __forceinline__ void after_update(ColState& cs, double rz, double rr, Control* ctl,
+                                             bool count) {
+  cs.it += 1;
+  cs.rr_in = rr;
+  if (!isfinite(rz) || !isfinite(rr)) {
+    cs.phase = PH_FAILED;
+    cs.status = SYLV_E_BREAKDOWN;
+    if (count) {
+      atomicSub(&ctl->n_active, 1u);
+      atomicSub(&ctl->n_unfinished, 1u);
+    }
+  } else if (rr <= cs.thr_in || rr == 0.0) {
+    cs.phase = PH_INNER_DONE;
+    if (count) atomicSub(&ctl->n_active, 1u);
+  } else if (!(rz > 0.0)) {
+    cs.phase = PH_FAILED;
+    cs.status = SYLV_E_BREAKDOWN;
+    if (count) {
+      atomicSub(&ctl->n_active, 1u);
+      atomicSub(&ctl->n_unfinished, 1u);
+    }
+  } else if (cs.it >= ctl->maxit) {
+    cs.phase = PH_INNER_DONE;
+    cs.stop_after = 1;
+    if (count) atomicSub(&ctl->n_active, 1u);
+  } else {
+    cs.beta = rz / cs.gamma;
+    cs.gamma = rz;
+  }
+}
+
+// This CTA's per-column partials (sum of the per-warp sums), no arrival.
+template <typename T, int NV>
+__device__ __forceinline__ void write_cta_partials(double* dst, int slot, CtaShared<T, NV>& sh,
+                                                   int R) {
+  const int nw = blockDim.x >> 5;
+  __syncthreads();
+  for (int t = threadIdx.x; t < R * NV; t += blockDim.x) {
+    const int r = t / NV, v = t - r * NV;
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh.wacc[r][w][v];
+    dst[((size_t)slot * R + r) * NPART + v] = s;
+  }
+}
+
 // Writes this CTA's partials, then returns true in the last CTA of the system to arrive, which
 // then holds the fixed-order totals of every active column in sh.red[r * NV + t] (thread 0).
 template <typename T, int NV>
@@ -461,23 +527,8 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
   double tot[RMAX][1];
   if (!finish_partials<T, 1>(sd, cr.slot, sd.nslots[0], sh, R, tot)) return;
   if (threadIdx.x == 0) {
-    for (int r = 0; r < R; ++r) {
-      if (!sh.act[r]) continue;
-      ColState& cs = sd.st[r];
-      const double pq = tot[r][0];
-      if (pq > 0.0 && isfinite(pq)) {
-        cs.alpha = cs.gamma / pq;
-        cs.first = 0;
-      } else if (cs.rr_in == 0.0) {
-        cs.phase = PH_INNER_DONE;  // exact solution: nothing left to do
-        atomicSub(&ctl->n_active, 1u);
-      } else {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_active, 1u);
-        atomicSub(&ctl->n_unfinished, 1u);
-      }
-    }
+    for (int r = 0; r < R; ++r)
+      if (sh.act[r]) after_apply(sd.st[r], tot[r][0], ctl, true);
     *sd.counter = 0u;
   }
 }
@@ -561,34 +612,8 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
   double tot[RMAX][2];
   if (!finish_partials<T, 2>(sd, cr.slot, sd.nslots[1], sh, R, tot)) return;
   if (threadIdx.x == 0) {
-    for (int r = 0; r < R; ++r) {
-      if (!sh.act[r]) continue;
-      ColState& cs = sd.st[r];
-      const double rz = tot[r][0], rr = tot[r][1];
-      cs.it += 1;
-      cs.rr_in = rr;
-      if (!isfinite(rz) || !isfinite(rr)) {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_active, 1u);
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else if (rr <= cs.thr_in || rr == 0.0) {
-        cs.phase = PH_INNER_DONE;
-        atomicSub(&ctl->n_active, 1u);
-      } else if (!(rz > 0.0)) {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_active, 1u);
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else if (cs.it >= ctl->maxit) {
-        cs.phase = PH_INNER_DONE;
-        cs.stop_after = 1;
-        atomicSub(&ctl->n_active, 1u);
-      } else {
-        cs.beta = rz / cs.gamma;
-        cs.gamma = rz;
-      }
-    }
+    for (int r = 0; r < R; ++r)
+      if (sh.act[r]) after_update(sd.st[r], tot[r][0], tot[r][1], ctl, true);
     *sd.counter = 0u;
   }
 }

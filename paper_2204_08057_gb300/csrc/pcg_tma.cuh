@@ -125,11 +125,12 @@ __device__ __forceinline__ void pipe_init(PipeShared& ps) {
   fence_mbar_init();
 }
 
-// Producer loop: waits for stage release, then issues unit u with issue(u, stage).
+// Producer loop over units u0 .. u1 - 1: waits for stage release (from the second round of the
+// ring on), then issues unit u with issue(u, stage).
 template <typename Issue>
-__device__ __forceinline__ void producer_loop(PipeShared& ps, int nunits, Issue&& issue) {
+__device__ __forceinline__ void producer_loop_range(PipeShared& ps, int u0, int u1, Issue&& issue) {
   const int lane = threadIdx.x & 31;
-  for (int u = 0; u < nunits; ++u) {
+  for (int u = u0; u < u1; ++u) {
     const int st = u % NSTAGE;
     if (u >= NSTAGE) {
       bool ok = true;
@@ -159,6 +160,70 @@ __device__ __forceinline__ bool pipe_failed(PipeShared& ps, int consumed, Contro
   return true;
 }
 
+// ---- consumer-side sums (modes 1 and 2 of the staged kernels) -------------------------------
+// In mode 0 the last CTA of a system to finish (atomic counter) sums the CTAs' partials and
+// updates the column states.  In modes 1 and 2 no CTA waits for the others at its end: every
+// CTA writes its partials, and every CTA of the NEXT kernel sums them itself at its start while
+// its producer warp already fills the stage ring (mode 2), then applies the state change to its
+// own copy of the column states.  All CTAs add in the same order, so the copies agree.  The
+// states are double-buffered: operator kernels read ColState st (written by the update kernel,
+// the residual kernel and the chunk-closing kernel) and their slot-0 CTA writes st2; update
+// kernels read st2 and their slot-0 CTA writes st.  So no kernel reads a state it writes, and
+// the counters of active and unfinished columns are kept by slot 0 alone.
+
+// Columns a system may have for the consumer-side protocol (the host uses it up to this many;
+// the copies live in shared memory next to the stage ring, which leaves little room).
+constexpr int CS_RMAX = 2;
+
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(TILE_PX) : "memory");
+}
+
+// tot[r][v] = sum over the system's slots of src[(slot R + r) NPART + v] for the columns with
+// want[r], in a fixed order: thread t adds slots t, t + TILE_PX, ..., then FP64 warp trees and
+// a tree over the warps.  Run by the TILE_PX consumer threads.
+template <int NV>
+__device__ __forceinline__ void sum_slots(const double* src, int nslots, int R, const int* want,
+                                          double* red, double (*tot)[NPART]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < R; ++r) {
+    if (!want[r]) continue;
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int sl = threadIdx.x; sl < nslots; sl += TILE_PX) {
+      const double* p = src + ((size_t)sl * R + r) * NPART;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += __ldcg(p + v);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double w = warp_sum(acc[v]);
+      if (lane == 0) red[warp * NV + v] = w;
+    }
+    consumers_sync();
+    if (warp == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double w = warp_sum(lane < NCONS ? red[lane * NV + v] : 0.0);
+        if (lane == 0) tot[r][v] = w;
+      }
+    }
+    consumers_sync();
+  }
+}
+
+// Copies issued ahead for a column list that the state change altered: wait (bounded) until
+// they landed, then start the ring afresh (thread 0; the caller synchronises).
+__device__ __forceinline__ void pipe_restart(PipeShared& ps) {
+  for (int u = 0; u < ps.issued; ++u) mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+  for (int q = 0; q < NSTAGE; ++q) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(saddr(&ps.full[q])) : "memory");
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(saddr(&ps.empty[q])) : "memory");
+  }
+  pipe_init(ps);
+}
+
 // Stage layouts.  Rows hold TILE_PX entries of 4 bytes (FP16 factor rows hold half2 pairs).
 template <int K, int M, int E>
 struct ApplyLayout {
@@ -180,24 +245,30 @@ struct UpdateLayout {
 // ---------------------------------------------------------------------------------------------
 // inner_apply (staged): p = z + beta p, q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
+// mode 0: the last CTA sets alpha (last-CTA protocol); mode 1: column states as stored in st;
+// mode 2: first the state change of the previous update kernel, from its partials.
 template <int K, int M, int E>
 __global__ void __launch_bounds__(WS_THREADS, 3)
 k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
-                  Control* ctl) {
+                  Control* ctl, int mode) {
   using L = ApplyLayout<K, M, E>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 1> sh;
   __shared__ __align__(8) PipeShared ps;
+  __shared__ ColState cst[CS_RMAX];
+  __shared__ double tot2[CS_RMAX][NPART];
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
+  const bool newp = mode != 0 && R <= CS_RMAX;
   int act = 0;
   if (threadIdx.x < RMAX) {
     const int r = threadIdx.x;
     if (r < R) {
       const ColState& cs = sd.st[r];
+      if (newp) cst[r] = cs;
       act = cs.phase == PH_INNER;
       sh.sc[r] = float(cs.beta);
       sh.aux[r] = cs.first;
@@ -213,43 +284,88 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
     ps.nact = na;
     pipe_init(ps);
   }
-  if (!__syncthreads_or(act)) return;
+  if (!__syncthreads_or(act)) {
+    if (newp && cr.slot == 0 && threadIdx.x < R) sd.st2[threadIdx.x] = cst[threadIdx.x];
+    return;
+  }
 
   const int64_t ld = op.ld, n = op.n;
-  const Units U = count_units(sd, cr.slot, sd.nslots[0], ps.nact);
+  Units U = count_units(sd, cr.slot, sd.nslots[0], ps.nact);
   const float* zg = (const float*)sd.vz;
   float* pg = (float*)sd.vp;
   float* qg = (float*)sd.vq;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int consumed = 0;
+  auto issue = [&](int u, int st) {
+    const int tile = cr.slot + (u / U.nact) * sd.nslots[0];
+    const int r = ps.cols[u % U.nact];
+    const bool first = sh.aux[r] != 0;
+    const int64_t base = (int64_t)tile * TILE_PX;
+    float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+    const uint32_t rowb = TILE_PX * 4;
+    const int nrows = first ? L::ROWS - 2 * K : L::ROWS;
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
+    }
+    __syncwarp();
+    const size_t voff = (size_t)r * K * ld;
+    for (int q = lane; q < L::ROWS; q += 32) {
+      const void* src = nullptr;
+      if (q < K) src = zg + voff + (size_t)q * ld + base;
+      else if (q < 2 * K) src = first ? nullptr : pg + voff + (size_t)(q - K) * ld + base;
+      else if (q < 3 * K) src = first ? nullptr : qg + voff + (size_t)(q - 2 * K) * ld + base;
+      else if (q < L::VAL) src = op.D32 + (size_t)(q - L::D) * ld + base;
+      else if (q < L::DIAG) src = op.ell_val32 + (size_t)(q - L::VAL) * ld + base;
+      else if (q == L::DIAG) src = op.diag32 + base;
+      else src = op.ell_col + (size_t)(q - L::COL) * ld + base;
+      if (src) bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
+    }
+  };
+  int head = 0;
+  if (newp) {
+    // the first ring of copies goes out for the columns active as stored; meanwhile the
+    // consumers apply the previous update's state change (which keeps p, q and first as they are)
+    head = U.n < NSTAGE ? U.n : NSTAGE;
+    if (warp == NCONS) {
+      producer_loop_range(ps, 0, head, issue);
+    } else if (mode == 2) {
+      sum_slots<2>(sd.partial2, sd.nslots[1], R, sh.act, sh.red, tot2);
+      if (threadIdx.x < R && sh.act[threadIdx.x]) {
+        const int r = threadIdx.x;
+        after_update(cst[r], tot2[r][0], tot2[r][1], ctl, cr.slot == 0);
+      }
+    }
+    __syncthreads();
+    if (cr.slot == 0 && threadIdx.x < R) sd.st2[threadIdx.x] = cst[threadIdx.x];
+    if (threadIdx.x == 0) {
+      int na = 0;
+      bool same = true;
+      for (int r = 0; r < R; ++r) {
+        const int a2 = cst[r].phase == PH_INNER;
+        if (a2 != sh.act[r]) same = false;
+        sh.act[r] = a2;
+        sh.sc[r] = float(cst[r].beta);
+        if (a2) ps.cols[na++] = r;
+      }
+      if (!same) {   // a column ended: restart the ring for the columns still running
+        pipe_restart(ps);
+        ps.nact = na;
+        sh.flag = 1;
+      } else {
+        sh.flag = 0;
+      }
+    }
+    __syncthreads();
+    if (sh.flag) {
+      if (ps.nact == 0) return;
+      U = count_units(sd, cr.slot, sd.nslots[0], ps.nact);
+      head = 0;
+    }
+  }
 
   if (warp == NCONS) {
-    producer_loop(ps, U.n, [&](int u, int st) {
-      const int tile = cr.slot + (u / U.nact) * sd.nslots[0];
-      const int r = ps.cols[u % U.nact];
-      const bool first = sh.aux[r] != 0;
-      const int64_t base = (int64_t)tile * TILE_PX;
-      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
-      const uint32_t rowb = TILE_PX * 4;
-      const int nrows = first ? L::ROWS - 2 * K : L::ROWS;
-      if (lane == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
-      }
-      __syncwarp();
-      const size_t voff = (size_t)r * K * ld;
-      for (int q = lane; q < L::ROWS; q += 32) {
-        const void* src = nullptr;
-        if (q < K) src = zg + voff + (size_t)q * ld + base;
-        else if (q < 2 * K) src = first ? nullptr : pg + voff + (size_t)(q - K) * ld + base;
-        else if (q < 3 * K) src = first ? nullptr : qg + voff + (size_t)(q - 2 * K) * ld + base;
-        else if (q < L::VAL) src = op.D32 + (size_t)(q - L::D) * ld + base;
-        else if (q < L::DIAG) src = op.ell_val32 + (size_t)(q - L::VAL) * ld + base;
-        else if (q == L::DIAG) src = op.diag32 + base;
-        else src = op.ell_col + (size_t)(q - L::COL) * ld + base;
-        if (src) bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
-      }
-    });
+    producer_loop_range(ps, head, U.n, issue);
   } else {
     const int t = threadIdx.x;
     double acc = 0.0;
@@ -338,26 +454,15 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
     }
   }
   if (pipe_failed(ps, consumed, ctl)) return;
+  if (newp) {
+    write_cta_partials<float, 1>(sd.partial, cr.slot, sh, R);
+    return;
+  }
   double tot[RMAX][1];
   if (!finish_partials<float, 1>(sd, cr.slot, sd.nslots[0], sh, R, tot)) return;
   if (threadIdx.x == 0) {
-    for (int r = 0; r < R; ++r) {
-      if (!sh.act[r]) continue;
-      ColState& cs = sd.st[r];
-      const double pq = tot[r][0];
-      if (pq > 0.0 && isfinite(pq)) {
-        cs.alpha = cs.gamma / pq;
-        cs.first = 0;
-      } else if (cs.rr_in == 0.0) {
-        cs.phase = PH_INNER_DONE;
-        atomicSub(&ctl->n_active, 1u);
-      } else {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_active, 1u);
-        atomicSub(&ctl->n_unfinished, 1u);
-      }
-    }
+    for (int r = 0; r < R; ++r)
+      if (sh.act[r]) after_apply(sd.st[r], tot[r][0], ctl, true);
     *sd.counter = 0u;
   }
 }
@@ -365,24 +470,31 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
 // ---------------------------------------------------------------------------------------------
 // inner_update (staged): d += alpha p, r -= alpha q, z = P^{-1} r, partial r . z and r . r
 // ---------------------------------------------------------------------------------------------
+// mode 0: the last CTA sets beta, gamma and the stopping state (last-CTA protocol); mode 1:
+// column states as stored in st2 (alpha included); mode 2: first alpha (the operator kernel's
+// state change) from its partials.
 template <int K, int M>
 __global__ void __launch_bounds__(WS_THREADS, 2)
 k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
-                   Control* ctl) {
+                   Control* ctl, int mode) {
   using L = UpdateLayout<K, M>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 2> sh;  // (mixing rows unused here: the factor is stored)
   __shared__ __align__(8) PipeShared ps;
+  __shared__ ColState cst[CS_RMAX];
+  __shared__ double tot1[CS_RMAX][NPART];
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
   const OpData& op = sd.op;
   const int R = sd.R;
+  const bool newp = mode != 0 && R <= CS_RMAX;
   int act = 0;
   if (threadIdx.x < RMAX) {
     const int r = threadIdx.x;
     if (r < R) {
-      const ColState& cs = sd.st[r];
+      const ColState& cs = newp ? sd.st2[r] : sd.st[r];
+      if (newp) cst[r] = cs;
       act = cs.phase == PH_INNER;
       sh.sc[r] = float(cs.alpha);
     }
@@ -396,11 +508,14 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
     ps.nact = na;
     pipe_init(ps);
   }
-  if (!__syncthreads_or(act)) return;
+  if (!__syncthreads_or(act)) {
+    if (newp && cr.slot == 0 && threadIdx.x < R) sd.st[threadIdx.x] = cst[threadIdx.x];
+    return;
+  }
 
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
-  const Units U = count_units(sd, cr.slot, sd.nslots[1], ps.nact);
+  Units U = count_units(sd, cr.slot, sd.nslots[1], ps.nact);
   float* dgl = (float*)sd.vd;
   float* rg = (float*)sd.vr;
   float* zg = (float*)sd.vz;
@@ -408,32 +523,74 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
   const float* qg = (const float*)sd.vq;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int consumed = 0;
+  auto issue = [&](int u, int st) {
+    const int tile = cr.slot + (u / U.nact) * sd.nslots[1];
+    const int r = ps.cols[u % U.nact];
+    const int64_t base = (int64_t)tile * TILE_PX;
+    float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
+    const uint32_t rowb = TILE_PX * 4;
+    const int nrows = prec ? L::ROWS : L::NOPREC_ROWS;
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
+    }
+    __syncwarp();
+    const size_t voff = (size_t)r * K * ld;
+    for (int q = lane; q < nrows; q += 32) {
+      const void* src;
+      if (q < K) src = dgl + voff + (size_t)q * ld + base;
+      else if (q < 2 * K) src = pg + voff + (size_t)(q - K) * ld + base;
+      else if (q < 3 * K) src = rg + voff + (size_t)(q - 2 * K) * ld + base;
+      else if (q < 4 * K) src = qg + voff + (size_t)(q - 3 * K) * ld + base;
+      else if (q < 5 * K) src = op.fs32 + (size_t)(q - 4 * K) * ld + base;
+      else src = op.fl16 + (size_t)(q - 5 * K) * ld + base;
+      bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
+    }
+  };
+  int head = 0;
+  if (newp) {
+    // the first ring of copies goes out for the columns active as stored; meanwhile the
+    // consumers form alpha from the operator kernel's partial sums
+    head = U.n < NSTAGE ? U.n : NSTAGE;
+    if (warp == NCONS) {
+      producer_loop_range(ps, 0, head, issue);
+    } else if (mode == 2) {
+      sum_slots<1>(sd.partial, sd.nslots[0], R, sh.act, sh.red, tot1);
+      if (threadIdx.x < R && sh.act[threadIdx.x]) {
+        const int r = threadIdx.x;
+        after_apply(cst[r], tot1[r][0], ctl, cr.slot == 0);
+      }
+    }
+    __syncthreads();
+    if (cr.slot == 0 && threadIdx.x < R) sd.st[threadIdx.x] = cst[threadIdx.x];
+    if (threadIdx.x == 0) {
+      int na = 0;
+      bool same = true;
+      for (int r = 0; r < R; ++r) {
+        const int a2 = cst[r].phase == PH_INNER;
+        if (a2 != sh.act[r]) same = false;
+        sh.act[r] = a2;
+        sh.sc[r] = float(cst[r].alpha);
+        if (a2) ps.cols[na++] = r;
+      }
+      if (!same) {   // a column ended: restart the ring for the columns still running
+        pipe_restart(ps);
+        ps.nact = na;
+        sh.flag = 1;
+      } else {
+        sh.flag = 0;
+      }
+    }
+    __syncthreads();
+    if (sh.flag) {
+      if (ps.nact == 0) return;
+      U = count_units(sd, cr.slot, sd.nslots[1], ps.nact);
+      head = 0;
+    }
+  }
 
   if (warp == NCONS) {
-    producer_loop(ps, U.n, [&](int u, int st) {
-      const int tile = cr.slot + (u / U.nact) * sd.nslots[1];
-      const int r = ps.cols[u % U.nact];
-      const int64_t base = (int64_t)tile * TILE_PX;
-      float* stage = reinterpret_cast<float*>(dsm + (size_t)st * L::STAGE_BYTES);
-      const uint32_t rowb = TILE_PX * 4;
-      const int nrows = prec ? L::ROWS : L::NOPREC_ROWS;
-      if (lane == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(&ps.full[st], (uint32_t)nrows * rowb);
-      }
-      __syncwarp();
-      const size_t voff = (size_t)r * K * ld;
-      for (int q = lane; q < nrows; q += 32) {
-        const void* src;
-        if (q < K) src = dgl + voff + (size_t)q * ld + base;
-        else if (q < 2 * K) src = pg + voff + (size_t)(q - K) * ld + base;
-        else if (q < 3 * K) src = rg + voff + (size_t)(q - 2 * K) * ld + base;
-        else if (q < 4 * K) src = qg + voff + (size_t)(q - 3 * K) * ld + base;
-        else if (q < 5 * K) src = op.fs32 + (size_t)(q - 4 * K) * ld + base;
-        else src = op.fl16 + (size_t)(q - 5 * K) * ld + base;
-        bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
-      }
-    });
+    producer_loop_range(ps, head, U.n, issue);
   } else {
     const int t = threadIdx.x;
     double acc_rz = 0.0, acc_rr = 0.0;
@@ -495,37 +652,15 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
     }
   }
   if (pipe_failed(ps, consumed, ctl)) return;
+  if (newp) {
+    write_cta_partials<float, 2>(sd.partial2, cr.slot, sh, R);
+    return;
+  }
   double tot[RMAX][2];
   if (!finish_partials<float, 2>(sd, cr.slot, sd.nslots[1], sh, R, tot)) return;
   if (threadIdx.x == 0) {
-    for (int r = 0; r < R; ++r) {
-      if (!sh.act[r]) continue;
-      ColState& cs = sd.st[r];
-      const double rz = tot[r][0], rr = tot[r][1];
-      cs.it += 1;
-      cs.rr_in = rr;
-      if (!isfinite(rz) || !isfinite(rr)) {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_active, 1u);
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else if (rr <= cs.thr_in || rr == 0.0) {
-        cs.phase = PH_INNER_DONE;
-        atomicSub(&ctl->n_active, 1u);
-      } else if (!(rz > 0.0)) {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_active, 1u);
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else if (cs.it >= ctl->maxit) {
-        cs.phase = PH_INNER_DONE;
-        cs.stop_after = 1;
-        atomicSub(&ctl->n_active, 1u);
-      } else {
-        cs.beta = rz / cs.gamma;
-        cs.gamma = rz;
-      }
-    }
+    for (int r = 0; r < R; ++r)
+      if (sh.act[r]) after_update(sd.st[r], tot[r][0], tot[r][1], ctl, true);
     *sd.counter = 0u;
   }
 }

@@ -75,6 +75,8 @@ struct Group {
   int block = TILE_PX;      // pixels per tile = threads per CTA
   int mult = 1;             // CTA slots = mult x resident CTAs
   int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (1: staged)
+  int csum = 0;             // staged pair with consumer-side sums (variants 2/3, chunks end
+                            // with launch_inner_close): both staged and at most 2 columns
   // Three CTA lists: [0] for operator (inner_apply) launches, [1] for update launches, [2] for
   // residual and update_x launches (their kernels keep different numbers of CTAs resident).
   int ncta[3] = {0, 0, 0};  // CTAs of every launch of that kind (fixed per configuration)
@@ -88,7 +90,9 @@ struct SysWork {
   int slot_cap = 0;          // partial-sum capacity in CTA slots
   void* vec = nullptr;       // 5 inner vectors
   ColState* st = nullptr;
+  ColState* st2 = nullptr;
   double* partial = nullptr;
+  double* partial2 = nullptr;
   unsigned int* counter = nullptr;
 };
 
@@ -161,6 +165,7 @@ Plan::~Plan() {
   for (auto& w : work) {
     cudaFree(w.vec);
     cudaFree(w.partial);
+    cudaFree(w.partial2);
     cudaFree(w.counter);
   }
   cudaFree(d_desc);
@@ -235,6 +240,9 @@ int configure_group(Plan& P, Group& g, int block, int mult, int va, int vu) {
   g.mult = mult;
   g.va = va;
   g.vu = vu;
+  int rmax = 0;
+  for (int s : g.sys) rmax = std::max(rmax, P.R[s]);
+  g.csum = (!P.inner_double && va == 1 && vu == 1 && rmax <= 2) ? 1 : 0;
   return SYLV_OK;
 }
 
@@ -349,14 +357,16 @@ int time_inner(Plan& P, Group& g, int kind, int reps, float* ms_out) {
     for (int sidx : g.sys) {
       CK(cudaMemcpyAsync(P.work[sidx].st, st.data(), P.R[sidx] * sizeof(ColState),
                          cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(P.work[sidx].st2, st.data(), P.R[sidx] * sizeof(ColState),
+                         cudaMemcpyHostToDevice, s));
     }
     CK(cudaEventRecord(P.evr0, s));
     if (kind == 0)
-      CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta[0], g.block, P.d_desc, g.d_ctas[0],
-                               P.d_ctl, s));
+      CK(launch_inner_apply<T>(g.k, g.m, g.e, g.csum ? 2 : g.va, g.ncta[0], g.block, P.d_desc,
+                               g.d_ctas[0], P.d_ctl, s));
     else
-      CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta[1], g.block, P.d_desc, g.d_ctas[1],
-                                P.d_ctl, s));
+      CK(launch_inner_update<T>(g.k, g.m, g.e, g.csum ? 2 : g.vu, g.ncta[1], g.block, P.d_desc,
+                                g.d_ctas[1], P.d_ctl, s));
     CK(cudaEventRecord(P.evr1, s));
     CK(cudaStreamSynchronize(s));
     float ms = 0;
@@ -500,6 +510,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     P.col_off.push_back(P.ncols);
     P.ncols += R[s];
     CK(dalloc(&w.partial, (size_t)w.slot_cap * R[s] * NPART * sizeof(double)));
+    CK(dalloc(&w.partial2, (size_t)w.slot_cap * R[s] * NPART * sizeof(double)));
     CK(dalloc(&w.counter, sizeof(unsigned int)));
     CK(cudaMemset(w.counter, 0, sizeof(unsigned int)));
     for (int r = 0; r < R[s]; ++r) {
@@ -507,8 +518,11 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
       P.col_rhs.push_back(r);
     }
   }
-  CK(dalloc(&P.d_states, (size_t)P.ncols * sizeof(ColState)));
-  for (int s = 0; s < nsys; ++s) P.work[s].st = P.d_states + P.col_off[s];
+  CK(dalloc(&P.d_states, (size_t)2 * P.ncols * sizeof(ColState)));
+  for (int s = 0; s < nsys; ++s) {
+    P.work[s].st = P.d_states + P.col_off[s];
+    P.work[s].st2 = P.d_states + P.ncols + P.col_off[s];
+  }
   CK(dalloc(&P.d_desc, nsys * sizeof(SysDesc)));
   CK(cudaMallocHost((void**)&P.h_desc, nsys * sizeof(SysDesc)));
   CK(dalloc(&P.d_ctl, sizeof(Control)));
@@ -535,7 +549,9 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     d.vp = base + 3 * vbytes;
     d.vq = base + 4 * vbytes;
     d.st = P.work[s].st;
+    d.st2 = P.work[s].st2;
     d.partial = P.work[s].partial;
+    d.partial2 = P.work[s].partial2;
     d.counter = P.work[s].counter;
   }
   CK(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
@@ -550,16 +566,25 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
   return SYLV_OK;
 }
 
+// Iteration `it` of a chunk of `iters`.  Groups with consumer-side sums: the chunk's first
+// operator kernel reads the stored states, every other kernel first sums its predecessor's
+// partials, and the chunk ends with the state change of its last update (launch_inner_close).
 template <typename T>
 int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
-                           bool capture_events) {
-  for (auto& g : P.groups)
-    CK(launch_inner_apply<T>(g.k, g.m, g.e, g.va, g.ncta[0], g.block, P.d_desc, g.d_ctas[0], P.d_ctl, s));
+                           bool capture_events, int it, int iters) {
+  for (auto& g : P.groups) {
+    const int va = g.csum ? (it == 0 ? 2 : 3) : g.va;
+    CK(launch_inner_apply<T>(g.k, g.m, g.e, va, g.ncta[0], g.block, P.d_desc, g.d_ctas[0], P.d_ctl, s));
+  }
   if (e_mid)
     CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_mid, s));
   for (auto& g : P.groups)
-    CK(launch_inner_update<T>(g.k, g.m, g.e, g.vu, g.ncta[1], g.block, P.d_desc, g.d_ctas[1], P.d_ctl, s));
+    CK(launch_inner_update<T>(g.k, g.m, g.e, g.csum ? 3 : g.vu, g.ncta[1], g.block, P.d_desc,
+                              g.d_ctas[1], P.d_ctl, s));
+  if (it == iters - 1)
+    for (auto& g : P.groups)
+      if (g.csum) CK(launch_inner_close(g.ncta[1], P.d_desc, g.d_ctas[1], P.d_ctl, s));
   if (e_end)
     CK(capture_events ? cudaEventRecordWithFlags(e_end, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_end, s));
@@ -590,7 +615,8 @@ int ensure_graph(Plan& P, int iters, int profile) {
   for (int it = 0; it < iters && rc == SYLV_OK; ++it)
     rc = launch_inner_iteration<T>(P, P.cap_stream,
                                    profile ? P.chunk_events[2 * it + 1] : nullptr,
-                                   profile ? P.chunk_events[2 * it + 2] : nullptr, true);
+                                   profile ? P.chunk_events[2 * it + 2] : nullptr, true, it,
+                                   iters);
   cudaError_t e = cudaStreamEndCapture(P.cap_stream, &graph);
   if (rc != SYLV_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -701,11 +727,13 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
         if (prof) CK(cudaEventRecord(direct_events[0], s));
         for (int it = 0; it < iters; ++it) {
           rc = launch_inner_iteration<T>(P, s, prof ? direct_events[2 * it + 1] : nullptr,
-                                         prof ? direct_events[2 * it + 2] : nullptr, false);
+                                         prof ? direct_events[2 * it + 2] : nullptr, false, it,
+                                         iters);
           if (rc != SYLV_OK) return rc;
         }
       }
       launches += 2L * iters * ng;
+      for (auto& g : P.groups) launches += g.csum;
       if ((rc = poll(P, s)) != SYLV_OK) return rc;
       ++polls;
       if (prof) {

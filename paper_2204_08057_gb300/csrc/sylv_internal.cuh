@@ -104,7 +104,9 @@ struct SysDesc {
   void* vp;
   void* vq;
   ColState* st;          // R
+  ColState* st2;         // R: the staged pair's second copy (written by its operator kernel)
   double* partial;       // nslots x R x NPART
+  double* partial2;      // nslots x R x NPART: the staged update kernel's partials
   unsigned int* counter; // one per system, zero between kernels
 };
 
@@ -131,8 +133,10 @@ struct CtaRef {
 // launchers (defined in the kernel translation units)
 // ------------------------------------------------------------------------------------------
 // Iteration kernels for a group of systems of one shape (k sources, m channels, ELL width e).
-// variant 1 selects the bulk-copy staged FP32 kernels (shapes with compile-time instances,
-// no mass diagonal); tma_available() says whether a shape has them.
+// variant 0: the direct kernels; 1-3: the bulk-copy staged FP32 kernels (shapes with
+// compile-time instances, no mass diagonal; tma_available() says whether a shape has them)
+// with 1 the last-CTA protocol, 2 and 3 the consumer-side protocol (3: the kernel first sums
+// the previous kernel's partials; a chunk of such iterations ends with launch_inner_close).
 template <typename T>
 cudaError_t launch_inner_apply(int k, int m, int e, int variant, int ncta, int block,
                                const SysDesc* d, const CtaRef* c, Control* ctl, cudaStream_t s);
@@ -141,6 +145,8 @@ cudaError_t launch_inner_update(int k, int m, int e, int variant, int ncta, int 
                                 const SysDesc* d, const CtaRef* c, Control* ctl,
                                 cudaStream_t s);
 bool tma_available(int k, int m, int e);
+cudaError_t launch_inner_close(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_residual(int k, int m, int e, int ncta, int block, const SysDesc* d,
                             const CtaRef* c, Control* ctl, cudaStream_t s);
