@@ -20,9 +20,12 @@
 //     when B_0 is ill conditioned (as it is for power-law mixing over the Planck channels).
 //   * Per Lanczos step two kernels: pass A (W = N^{-1} Q_0 V_s - V_{s-1} B_s^T with the
 //     stencil of Algorithm 1 on Vt_s, partial sums of H_s = V_s^T N W), pass B
-//     (Vt_{s+1} = W - V_s H_s, partial sums of its N-Gram matrix S).  The last CTA of pass B
-//     (atomic counter, fixed-order sums, no waiting) forms B_{s+1} = chol(S) (the N-orthonormal
-//     QR of Algorithm 4 as a Cholesky QR) and records H_s, B_{s+1}.
+//     (Vt_{s+1} = W - V_s H_s, partial sums of its N-Gram matrix S).  B_{s+1} = chol(S) is the
+//     N-orthonormal QR of Algorithm 4 as a Cholesky QR.  In the plain kernels the last CTA of
+//     a pass (atomic counter, fixed-order sums, no waiting) forms the totals, the factor and
+//     the records.  The staged kernels elect no last CTA: every CTA of the next pass sums the
+//     partials and factors S itself while its producer warp fills the stage ring (pass A of
+//     step s + 1 forms B_{s+1}, pass B forms H_s), and a one-CTA kernel closes each chunk.
 //   * The residual estimate of Algorithm 5 is evaluated on the host at every poll from the
 //     recorded blocks, by one block-LDL^T step per shift and step: the last block z_l of
 //     (T_s + rho_l I)^{-1} E_1 B_0 u_l gives gamma = sum_l ||B_{s+1} z_l||^2, the same number

@@ -22,7 +22,9 @@
 // Work split: each system owns `nslots` CTAs (all resident at once); CTA `slot` handles tiles
 // slot, slot + nslots, ... of blockDim.x consecutive pixels, keeps per-warp partial sums in
 // shared memory, writes one partial per column at the end, and the last of the system's CTAs
-// to finish (atomic counter, no waiting) reduces the nslots partials in a fixed order.
+// to finish (atomic counter, no waiting) reduces the nslots partials in a fixed order.  The
+// staged FP32 pair with one or two columns instead lets every CTA of the next kernel form the
+// sums (pcg_tma.cuh); the state changes are the same functions in both cases.
 #pragma once
 
 #include <cmath>
