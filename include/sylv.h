@@ -133,6 +133,9 @@ typedef struct {
   int32_t slots_mult;  /* CTA slots as a multiple of the resident CTAs                      */
   int32_t apply_staged;  /* 1: operator kernel stages its streams with bulk copies         */
   int32_t update_staged; /* 1: update kernel stages its streams with bulk copies           */
+  int32_t residual_staged; /* 1: the FP64 residual kernel stages its streams (mixed mode,
+                              whole tiles, even ldu, 16-byte aligned X and B)              */
+  int32_t reserved_info;   /* 0                                                          */
 } sylv_info;
 
 /* Fills *o with the defaults.  Returns SYLV_OK, or SYLV_E_INVALID if o is NULL. */

@@ -60,7 +60,8 @@ class sylv_info(ctypes.Structure):
                 ("ms_apply", c_double), ("ms_update", c_double), ("ms_residual", c_double),
                 ("n_apply", c_int32), ("n_update", c_int32), ("n_residual", c_int32),
                 ("launches", c_int32), ("tile", c_int32), ("slots_mult", c_int32),
-                ("apply_staged", c_int32), ("update_staged", c_int32)]
+                ("apply_staged", c_int32), ("update_staged", c_int32),
+                ("residual_staged", c_int32), ("reserved_info", c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -101,6 +101,36 @@ int tma_occupancy(int kind) {
 }
 
 template <int K, int M, int E>
+size_t residual_tma_smem() {
+  return (size_t)tma::NSTAGE * tma::ResidLayout<K, E>::STAGE_BYTES;
+}
+
+template <int K, int M, int E>
+cudaError_t residual_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
+                         cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = residual_tma_smem<K, M, E>();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tma::k_residual_tma<K, M, E>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  tma::k_residual_tma<K, M, E><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
+  return cudaGetLastError();
+}
+
+template <int K, int M, int E>
+int residual_tma_occupancy() {
+  int nb = 0;
+  cudaFuncSetAttribute(tma::k_residual_tma<K, M, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)residual_tma_smem<K, M, E>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_residual_tma<K, M, E>,
+                                                tma::WS_THREADS, residual_tma_smem<K, M, E>());
+  return nb < 1 ? 1 : nb;
+}
+
+template <int K, int M, int E>
 cudaError_t apply_x_tma(const OpData& op, const float* X, float* Y, int R, unsigned int* err,
                         cudaStream_t s) {
   static bool attr = false;
@@ -148,6 +178,17 @@ cudaError_t launch_apply_staged(const OpData& op, const float* X, float* Y, int 
   if (k == K_ && m == M_ && e == E_) return update_tma<K_, M_>(ncta, d, c, ctl, variant - 1, s);
 #define SYLV_TMA_OCC_(K_, M_, E_) \
   if (k == K_ && m == M_ && e == E_) return tma_occupancy<K_, M_, E_>(kind);
+#define SYLV_TMA_RESID_(K_, M_, E_) \
+  if (k == K_ && m == M_ && e == E_) return residual_tma<K_, M_, E_>(ncta, d, c, ctl, s);
+#define SYLV_TMA_RESID_OCC_(K_, M_, E_) \
+  if (k == K_ && m == M_ && e == E_) return residual_tma_occupancy<K_, M_, E_>();
+
+cudaError_t launch_residual_staged(int k, int m, int e, int ncta, const SysDesc* d,
+                                   const CtaRef* c, Control* ctl, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+  SYLV_SPECIAL_SHAPES(SYLV_TMA_RESID_)
+  return cudaErrorNotSupported;
+}
 
 template <>
 cudaError_t launch_inner_apply<float>(int k, int m, int e, int variant, int ncta, int block,
@@ -188,6 +229,10 @@ cudaError_t launch_inner_close(int ncta, const SysDesc* d, const CtaRef* c, Cont
 
 template <>
 int occupancy<float>(int kind, int k, int m, int e, int variant, int block) {
+  if (kind == 3) {
+    SYLV_SPECIAL_SHAPES(SYLV_TMA_RESID_OCC_)
+    kind = 2;
+  }
   if (variant >= 1 && kind < 2) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_OCC_)
   }

@@ -30,7 +30,7 @@ cudaError_t launch_update_x<double>(int k, int ncta, int block, const SysDesc* d
 template <>
 int occupancy<double>(int kind, int k, int m, int e, int variant, int block) {
   (void)variant;
-  return occupancy_impl<double>(kind, k, m, e, block);
+  return occupancy_impl<double>(kind == 3 ? 2 : kind, k, m, e, block);
 }
 
 }  // namespace sylv

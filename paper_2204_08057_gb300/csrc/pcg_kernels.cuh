@@ -402,6 +402,48 @@ __device__ __forceinline__ void after_update(ColState& cs, double rz, double rr,
   }
 }
 
+// Column state after an FP64 residual with totals ||r64||^2, ||B||^2, r.z, r.r (inner type):
+// converged, capped, failed, or the start of an inner solve with its target.
+__device__ __forceinline__ void after_residual(ColState& cs, const double (&t)[4], Control* ctl) {
+  const double rr64 = t[0], rz = t[2], rr = t[3];
+  if (cs.phase == PH_START) cs.bnorm2 = t[1];
+  cs.rr64 = rr64;
+  const double den = cs.bnorm2 > 0.0 ? cs.bnorm2 : 1.0;
+  const double rel2 = rr64 / den;
+  cs.relres = sqrt(rel2);
+  const bool capped = cs.stop_after || cs.it >= ctl->maxit || cs.outer >= ctl->max_outer;
+  if (!isfinite(rr64)) {
+    cs.phase = PH_FAILED;
+    cs.status = SYLV_E_BREAKDOWN;
+    atomicSub(&ctl->n_unfinished, 1u);
+  } else if (rel2 <= ctl->tol2) {
+    cs.phase = PH_CONVERGED;
+    cs.status = SYLV_OK;
+    atomicSub(&ctl->n_unfinished, 1u);
+  } else if (capped) {
+    cs.phase = PH_FAILED;
+    cs.status = SYLV_E_NOT_CONVERGED;
+    atomicSub(&ctl->n_unfinished, 1u);
+  } else if (!(rz > 0.0) || !isfinite(rz)) {
+    cs.phase = PH_FAILED;
+    cs.status = SYLV_E_BREAKDOWN;
+    atomicSub(&ctl->n_unfinished, 1u);
+  } else {
+    // inner target: the reduction still needed (with a safety margin), but no finer than the
+    // inner precision can deliver in one refinement step
+    const double need = ctl->tol2 * ctl->safety2 * den / rr64;
+    const double fac = need > ctl->tol_in2 ? need : ctl->tol_in2;
+    cs.phase = PH_INNER;
+    cs.first = 1;
+    cs.gamma = rz;
+    cs.rr_in0 = rr;
+    cs.rr_in = rr;
+    cs.thr_in = fac * rr;
+    cs.outer += 1;
+    atomicAdd(&ctl->n_active, 1u);
+  }
+}
+
 // This CTA's per-column partials (sum of the per-warp sums), no arrival.
 template <typename T, int NV>
 __device__ __forceinline__ void write_cta_partials(double* dst, int slot, CtaShared<T, NV>& sh,
@@ -741,47 +783,8 @@ k_residual(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas, C
   double tot[RMAX][4];
   if (!finish_partials<double, 4>(sd, cr.slot, sd.nslots[2], sh, R, tot)) return;
   if (threadIdx.x == 0) {
-    for (int r = 0; r < R; ++r) {
-      if (!sh.act[r]) continue;
-      ColState& cs = sd.st[r];
-      const double rr64 = tot[r][0], rz = tot[r][2], rr = tot[r][3];
-      if (cs.phase == PH_START) cs.bnorm2 = tot[r][1];
-      cs.rr64 = rr64;
-      const double den = cs.bnorm2 > 0.0 ? cs.bnorm2 : 1.0;
-      const double rel2 = rr64 / den;
-      cs.relres = sqrt(rel2);
-      const bool capped = cs.stop_after || cs.it >= ctl->maxit || cs.outer >= ctl->max_outer;
-      if (!isfinite(rr64)) {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else if (rel2 <= ctl->tol2) {
-        cs.phase = PH_CONVERGED;
-        cs.status = SYLV_OK;
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else if (capped) {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_NOT_CONVERGED;
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else if (!(rz > 0.0) || !isfinite(rz)) {
-        cs.phase = PH_FAILED;
-        cs.status = SYLV_E_BREAKDOWN;
-        atomicSub(&ctl->n_unfinished, 1u);
-      } else {
-        // inner target: the reduction still needed (with a safety margin), but no finer
-        // than the inner precision can deliver in one refinement step
-        const double need = ctl->tol2 * ctl->safety2 * den / rr64;
-        const double fac = need > ctl->tol_in2 ? need : ctl->tol_in2;
-        cs.phase = PH_INNER;
-        cs.first = 1;
-        cs.gamma = rz;
-        cs.rr_in0 = rr;
-        cs.rr_in = rr;
-        cs.thr_in = fac * rr;
-        cs.outer += 1;
-        atomicAdd(&ctl->n_active, 1u);
-      }
-    }
+    for (int r = 0; r < R; ++r)
+      if (sh.act[r]) after_residual(sd.st[r], tot[r], ctl);
     *sd.counter = 0u;
   }
 }

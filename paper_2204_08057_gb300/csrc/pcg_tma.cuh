@@ -666,6 +666,256 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
 }
 
 // ---------------------------------------------------------------------------------------------
+// residual (staged, mixed precision): r64 = B - G X in FP64, r = r64 rounded to FP32, d = 0,
+// z = P^{-1} r; partial ||r64||^2, ||B||^2, r . z, r . r; the last CTA decides (after_residual)
+// ---------------------------------------------------------------------------------------------
+// The FP64 operator is the pixel-block form (k(k+1) FMAs per pixel for the block plus the
+// stencil), which keeps this kernel on the FP64 pipe (1/64 of the FP32 rate on GB300): staging
+// every stream it reads lets the consumer warps wait only on that pipe.  Stage: X and B of the
+// tile (the caller's FP64 rows), the FP64 pixel block, the FP64 ELL values, the ELL columns,
+// and the FP32 scaling and FP16 factor of the preconditioner.  Used when the caller's rows can
+// be copied whole (n a multiple of TILE_PX, even ldu, 16-byte aligned X and B).
+template <int K, int E>
+struct ResidLayout {
+  static constexpr int NB = K * (K + 1) / 2, NB2 = (NB + 1) / 2;
+  // byte offsets of the regions; rows hold TILE_PX entries
+  static constexpr int X = 0;                          // K rows, FP64
+  static constexpr int B = X + K * TILE_PX * 8;        // K rows, FP64
+  static constexpr int BLK = B + K * TILE_PX * 8;      // NB rows, FP64
+  static constexpr int VAL = BLK + NB * TILE_PX * 8;   // E rows, FP64
+  static constexpr int COL = VAL + E * TILE_PX * 8;    // E rows, int32
+  static constexpr int FS = COL + E * TILE_PX * 4;     // K rows, FP32
+  static constexpr int FL = FS + K * TILE_PX * 4;      // NB2 rows, half2
+  static constexpr int STAGE_BYTES = FL + NB2 * TILE_PX * 4;
+};
+
+template <int K, int M, int E>
+__global__ void __launch_bounds__(WS_THREADS, 1)
+k_residual_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas,
+               Control* ctl) {
+  using L = ResidLayout<K, E>;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ CtaShared<double, 4> sh;
+  __shared__ __align__(8) PipeShared ps;
+  const CtaRef cr = ctas[blockIdx.x];
+  if (cr.sys < 0) return;  // idle CTA of a reassigned launch
+  const SysDesc& sd = descs[cr.sys];
+  const OpData& op = sd.op;
+  const int R = sd.R;
+  int act = 0;
+  if (threadIdx.x < RMAX) {
+    const int r = threadIdx.x;
+    int ph = PH_CONVERGED;
+    if (r < R) {
+      ph = sd.st[r].phase;
+      act = (ph == PH_START || ph == PH_INNER_DONE);
+    }
+    sh.act[r] = act;
+    sh.aux[r] = ph;
+  }
+  stage_operator<double, 4>(op, K, sh);
+  zero_wacc<double, 4>(sh, R);
+  if (threadIdx.x == 0) {
+    int na = 0;
+    for (int r = 0; r < R; ++r)
+      if (sh.act[r]) ps.cols[na++] = r;
+    ps.nact = na;
+    pipe_init(ps);
+  }
+  if (!__syncthreads_or(act)) return;
+
+  const int64_t ld = op.ld, ldu = op.ldu, n = op.n;
+  const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
+  const bool x0_zero = ctl->x0_zero != 0;
+  const Units U = count_units(sd, cr.slot, sd.nslots[3], ps.nact);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int consumed = 0;
+
+  if (warp == NCONS) {
+    producer_loop_range(ps, 0, U.n, [&](int u, int st) {
+      const int tile = cr.slot + (u / U.nact) * sd.nslots[3];
+      const int r = ps.cols[u % U.nact];
+      const bool noop = x0_zero && sh.aux[r] == PH_START;   // X = 0: no operator term
+      const int64_t base = (int64_t)tile * TILE_PX;
+      unsigned char* stage = dsm + (size_t)st * L::STAGE_BYTES;
+      const uint32_t row8 = TILE_PX * 8, row4 = TILE_PX * 4;
+      const uint32_t bytes = K * row8 + (noop ? 0u : K * row8 + L::NB * row8 + E * (row8 + row4)) +
+                             (prec ? K * row4 + L::NB2 * row4 : 0u);
+      if (lane == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&ps.full[st], bytes);
+      }
+      __syncwarp();
+      const size_t uoff = (size_t)r * K * ldu;
+      constexpr int NROWS = 2 * K + L::NB + 2 * E + K + L::NB2;
+      for (int q = lane; q < NROWS; q += 32) {
+        const void* src = nullptr;
+        void* dst = nullptr;
+        uint32_t nb = row8;
+        int x = q;
+        if (x < K) {
+          src = sd.B + uoff + (size_t)x * ldu + base;
+          dst = stage + L::B + (size_t)x * row8;
+        } else if ((x -= K) < K) {
+          if (!noop) src = sd.X + uoff + (size_t)x * ldu + base;
+          dst = stage + L::X + (size_t)x * row8;
+        } else if ((x -= K) < L::NB) {
+          if (!noop) src = op.blk64 + (size_t)x * ld + base;
+          dst = stage + L::BLK + (size_t)x * row8;
+        } else if ((x -= L::NB) < E) {
+          if (!noop) src = op.ell_val64 + (size_t)x * ld + base;
+          dst = stage + L::VAL + (size_t)x * row8;
+        } else if ((x -= E) < E) {
+          if (!noop) src = op.ell_col + (size_t)x * ld + base;
+          dst = stage + L::COL + (size_t)x * row4;
+          nb = row4;
+        } else if ((x -= E) < K) {
+          if (prec) src = op.fs32 + (size_t)x * ld + base;
+          dst = stage + L::FS + (size_t)x * row4;
+          nb = row4;
+        } else {
+          x -= K;
+          if (prec) src = op.fl16 + (size_t)x * ld + base;
+          dst = stage + L::FL + (size_t)x * row4;
+          nb = row4;
+        }
+        if (src) bulk_load(dst, src, nb, &ps.full[st]);
+      }
+    });
+  } else {
+    const int t = threadIdx.x;
+    double a_rr64 = 0.0, a_bb = 0.0, a_rz = 0.0, a_rr = 0.0;
+    for (int u = 0; u < U.n; ++u) {
+      const int st = u % NSTAGE;
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+        ps.bad = 1;
+        break;
+      }
+      const int tile = cr.slot + (u / U.nact) * sd.nslots[3];
+      const int r = ps.cols[u % U.nact];
+      const bool noop = x0_zero && sh.aux[r] == PH_START;
+      const int64_t base = (int64_t)tile * TILE_PX;
+      const int64_t i = base + t;
+      const unsigned char* stage = dsm + (size_t)st * L::STAGE_BYTES;
+      const double* sx = reinterpret_cast<const double*>(stage + L::X);
+      const double* sb = reinterpret_cast<const double*>(stage + L::B);
+      const double* sblk = reinterpret_cast<const double*>(stage + L::BLK);
+      const double* sval = reinterpret_cast<const double*>(stage + L::VAL);
+      const int32_t* scol = reinterpret_cast<const int32_t*>(stage + L::COL);
+      const size_t uoff = (size_t)r * K * ldu, off = (size_t)r * K * ld;
+      double gx[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) gx[j] = 0.0;
+      if (!noop) {
+        double xi[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) xi[j] = sx[j * TILE_PX + t];
+        // neighbours of the stencil: staged when in the tile, else the caller's X
+        const double* src[E];
+        int64_t stride[E];
+        double v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int64_t c = scol[e * TILE_PX + t];
+          v[e] = sval[e * TILE_PX + t];
+          const uint32_t loc = (uint32_t)(c - base);
+          const bool in_tile = loc < (uint32_t)TILE_PX;
+          src[e] = in_tile ? sx + loc : sd.X + uoff + c;
+          stride[e] = in_tile ? (int64_t)TILE_PX : ldu;
+        }
+        double nb[E][K];
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
+        // pixel block (packed lower triangle, row-major)
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+#pragma unroll
+          for (int b = 0; b <= a; ++b) {
+            const double pab = sblk[(a * (a + 1) / 2 + b) * TILE_PX + t];
+            gx[a] += pab * xi[b];
+            if (b != a) gx[b] += pab * xi[a];
+          }
+        }
+        double lap[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) lap[j] = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
+#pragma unroll
+        for (int j = 0; j < K; ++j) gx[j] += sh.tau[j] * lap[j];
+      }
+      float ri[K], zi[K];
+      double rr64 = 0.0, bb = 0.0;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const double bj = sb[j * TILE_PX + t];
+        const double r64 = bj - gx[j];
+        rr64 += r64 * r64;
+        bb += bj * bj;
+        ri[j] = float(r64);
+      }
+      if (prec) {
+        BlockChol<K, float> f;
+        const float* sfs = reinterpret_cast<const float*>(stage + L::FS);
+        const __half2* sfl = reinterpret_cast<const __half2*>(stage + L::FL);
+#pragma unroll
+        for (int x = 0; x < K; ++x) f.s[x] = sfs[x * TILE_PX + t];
+#pragma unroll
+        for (int x = 0; x < L::NB; x += 2) {
+          const float2 w2 = __half22float2(sfl[(x / 2) * TILE_PX + t]);
+          f.l[x] = w2.x;
+          if (x + 1 < L::NB) f.l[x + 1] = w2.y;
+        }
+        block_solve<K, float>(f, ri, zi);
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) zi[j] = ri[j];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ps.empty[st]);
+      consumed = u + 1;
+      float rzt = 0.f, rrt = 0.f;   // products in the inner type, like the inner kernels
+      if (i < n) {
+        float* rv = (float*)sd.vr + off;
+        float* dv = (float*)sd.vd + off;
+        float* zv = (float*)sd.vz + off;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          rv[(size_t)j * ld + i] = ri[j];
+          dv[(size_t)j * ld + i] = 0.f;
+          zv[(size_t)j * ld + i] = zi[j];
+          rzt += ri[j] * zi[j];
+          rrt += ri[j] * ri[j];
+        }
+      } else {
+        rr64 = bb = 0.0;
+      }
+      a_rr64 += rr64;
+      a_bb += bb;
+      a_rz += double(rzt);
+      a_rr += double(rrt);
+      if (U.nact > 1 || u + 1 == U.n) {
+        const double v4[4] = {a_rr64, a_bb, a_rz, a_rr};
+        warp_accumulate<double, 4>(sh, r, v4);
+        a_rr64 = a_bb = a_rz = a_rr = 0.0;
+      }
+    }
+  }
+  if (pipe_failed(ps, consumed, ctl)) return;
+  double tot[RMAX][4];
+  if (!finish_partials<double, 4>(sd, cr.slot, sd.nslots[3], sh, R, tot)) return;
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < R; ++r)
+      if (sh.act[r]) after_residual(sd.st[r], tot[r], ctl);
+    *sd.counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // stand-alone operator apply (staged): Y = G X for FP32 caller vectors (nrhs columns)
 // ---------------------------------------------------------------------------------------------
 // Stage: x of the tile (K rows), D, ELL values, diagonal, ELL columns.  Used when n is a

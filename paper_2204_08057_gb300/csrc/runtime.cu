@@ -77,12 +77,14 @@ struct Group {
   int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (1: staged)
   int csum = 0;             // staged pair with consumer-side sums (variants 2/3, chunks end
                             // with launch_inner_close): both staged and at most 2 columns
-  // Three CTA lists: [0] for operator (inner_apply) launches, [1] for update launches, [2] for
-  // residual and update_x launches (their kernels keep different numbers of CTAs resident).
-  int ncta[3] = {0, 0, 0};  // CTAs of every launch of that kind (fixed per configuration)
+  int rs_ok = 0;             // the staged FP64 residual serves this group's shape and tiles
+  // Four CTA lists: [0] for operator (inner_apply) launches, [1] for update launches, [2] for
+  // residual and update_x launches, [3] for staged residual launches (their kernels keep
+  // different numbers of CTAs resident).
+  int ncta[4] = {0, 0, 0, 0};  // CTAs of every launch of that kind (fixed per configuration)
   int cta_cap = 0;
-  CtaRef* d_ctas[3] = {nullptr, nullptr, nullptr};
-  CtaRef* h_ctas[3] = {nullptr, nullptr, nullptr};  // pinned staging for reassignments
+  CtaRef* d_ctas[4] = {nullptr, nullptr, nullptr, nullptr};
+  CtaRef* h_ctas[4] = {nullptr, nullptr, nullptr, nullptr};  // pinned staging for reassignments
   std::vector<int> cur_set;  // systems the CTA lists currently cover
 };
 
@@ -156,7 +158,7 @@ struct sylv_ctx {
 
 Plan::~Plan() {
   for (auto& g : groups) {
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
       cudaFree(g.d_ctas[k]);
       cudaFreeHost(g.h_ctas[k]);
     }
@@ -211,12 +213,13 @@ int default_block(int64_t n) {
 // (uploaded before each solve).
 template <typename T>
 int configure_group(Plan& P, Group& g, int block, int mult, int va, int vu) {
-  const int occ[3] = {occupancy<T>(0, g.k, g.m, g.e, va, block),
+  const int occ[4] = {occupancy<T>(0, g.k, g.m, g.e, va, block),
                       occupancy<T>(1, g.k, g.m, g.e, vu, block),
-                      occupancy<T>(2, g.k, g.m, g.e, 0, block)};
+                      occupancy<T>(2, g.k, g.m, g.e, 0, block),
+                      occupancy<T>(3, g.k, g.m, g.e, 0, block)};
   int64_t total = 0;
   for (int s : g.sys) total += ceil_div(P.hs[s]->op.n, block);
-  for (int kind = 0; kind < 3; ++kind) {
+  for (int kind = 0; kind < 4; ++kind) {
     const int64_t budget = (int64_t)P.nsm * occ[kind] * mult;
     int used = 0;
     for (int s : g.sys) {
@@ -243,6 +246,7 @@ int configure_group(Plan& P, Group& g, int block, int mult, int va, int vu) {
   int rmax = 0;
   for (int s : g.sys) rmax = std::max(rmax, P.R[s]);
   g.csum = (!P.inner_double && va == 1 && vu == 1 && rmax <= 2) ? 1 : 0;
+  g.rs_ok = (!P.inner_double && !g.has_w && block == TILE_PX && tma_available(g.k, g.m, g.e)) ? 1 : 0;
   return SYLV_OK;
 }
 
@@ -253,7 +257,7 @@ int reassign_group(Plan& P, Group& g, const std::vector<int>& set, cudaStream_t 
   if (set == g.cur_set) return SYLV_OK;
   int64_t total = 0;
   for (int sy : set) total += P.h_desc[sy].ntiles;
-  for (int kind = 0; kind < 3; ++kind) {
+  for (int kind = 0; kind < 4; ++kind) {
     const int ncta = g.ncta[kind];
     std::vector<int64_t> ns(set.size());
     int64_t sum = 0;
@@ -495,7 +499,7 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
       g.cta_cap += P.work[s].slot_cap;
     }
     g.cta_cap += 1;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
       CK(dalloc(&g.d_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
       CK(cudaMallocHost((void**)&g.h_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
     }
@@ -678,6 +682,19 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   }
   CK(launch_init_states(P.ncols, P.d_col_sys, P.d_col_rhs, P.d_desc, P.d_ctl, s));
   launches += 1;
+  // the staged FP64 residual copies the caller's rows of X and B whole: every system of the
+  // group needs whole tiles, an even leading dimension and 16-byte aligned X and B
+  std::vector<char> rs_staged(P.groups.size(), 0);
+  for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+    const Group& g = P.groups[gi];
+    bool ok = g.rs_ok != 0;
+    for (int t : g.sys) {
+      const OpData& op = P.hs[t]->op;
+      ok = ok && op.n % TILE_PX == 0 && op.ldu % 2 == 0 &&
+           ((uintptr_t)B[t] & 15u) == 0 && ((uintptr_t)X[t] & 15u) == 0;
+    }
+    rs_staged[gi] = ok ? 1 : 0;
+  }
   if (o.use_graph) {
     int rc = ensure_graph<T>(P, iters, prof ? 1 : 0);
     if (rc != SYLV_OK) return rc;
@@ -702,8 +719,13 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
     for (auto& g : P.groups)
       CK(launch_update_x<T>(g.k, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], s));
     if (prof) CK(cudaEventRecord(P.evr0, s));
-    for (auto& g : P.groups)
-      CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], P.d_ctl, s));
+    for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+      Group& g = P.groups[gi];
+      if (rs_staged[gi])
+        CK(launch_residual_staged(g.k, g.m, g.e, g.ncta[3], P.d_desc, g.d_ctas[3], P.d_ctl, s));
+      else
+        CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], P.d_ctl, s));
+    }
     if (prof) CK(cudaEventRecord(P.evr1, s));
     launches += 2 * ng;
     if ((rc = poll(P, s)) != SYLV_OK) break;
@@ -798,6 +820,7 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
       inf.slots_mult = P.groups[0].mult;
       inf.apply_staged = P.groups[0].va;
       inf.update_staged = P.groups[0].vu;
+      inf.residual_staged = rs_staged.empty() ? 0 : rs_staged[0];
     }
     if (infos) infos[t] = inf;
     if (inf.status != SYLV_OK && (worst == SYLV_OK || inf.status == SYLV_E_BREAKDOWN))
@@ -1315,6 +1338,7 @@ int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const
     tot.slots_mult = inf.slots_mult;
     tot.apply_staged = inf.apply_staged;
     tot.update_staged = inf.update_staged;
+    tot.residual_staged = inf.residual_staged;
   }
   CK(launch_var_finish(op, num, den, var, s));
   CK(cudaStreamSynchronize(s));

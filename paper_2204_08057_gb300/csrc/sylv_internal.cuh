@@ -93,9 +93,9 @@ struct SysDesc {
   OpData op;
   int R;                 // right-hand sides
   int ntiles;            // tiles of blockDim.x pixels
-  int nslots[3];         // CTAs working on this system: [0] in operator (inner_apply) launches,
-                         // [1] in update launches, [2] in residual and update_x launches
-  int pad;
+  int nslots[4];         // CTAs working on this system: [0] in operator (inner_apply) launches,
+                         // [1] in update launches, [2] in residual and update_x launches,
+                         // [3] in staged residual launches
   const double* B;       // R x k x ld
   double* X;             // R x k x ld
   void* vd;              // inner vectors, R x k x ld of the inner type
@@ -150,11 +150,15 @@ cudaError_t launch_inner_close(int ncta, const SysDesc* d, const CtaRef* c, Cont
 template <typename T>
 cudaError_t launch_residual(int k, int m, int e, int ncta, int block, const SysDesc* d,
                             const CtaRef* c, Control* ctl, cudaStream_t s);
+// Staged FP64 residual of the mixed solve (FP32 inner vectors, shapes with staged instances,
+// no mass diagonal, TILE_PX tiles, caller rows copied whole); cudaErrorNotSupported otherwise.
+cudaError_t launch_residual_staged(int k, int m, int e, int ncta, const SysDesc* d,
+                                   const CtaRef* c, Control* ctl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_update_x(int k, int ncta, int block, const SysDesc* d, const CtaRef* c,
                             cudaStream_t s);
-// Resident CTAs per SM of one kernel (kind 0: inner apply, 1: inner update, 2: residual)
-// for a shape.
+// Resident CTAs per SM of one kernel (kind 0: inner apply, 1: inner update, 2: residual,
+// 3: staged residual) for a shape.
 template <typename T>
 int occupancy(int kind, int k, int m, int e, int variant, int block);
 cudaError_t launch_init_states(int ncols, const int* col_sys, const int* col_rhs,

@@ -69,5 +69,5 @@ def test_struct_layouts_match_header():
     from paper_2204_08057_gb300 import binding as B
     # sizes implied by the header's field lists on an LP64 ABI
     assert ctypes.sizeof(B.sylv_opts) == 2 * 8 + 8 * 4
-    assert ctypes.sizeof(B.sylv_info) == 4 * 4 + 5 * 8 + 4 * 4 + 4 * 4
+    assert ctypes.sizeof(B.sylv_info) == 4 * 4 + 5 * 8 + 4 * 4 + 6 * 4
     assert ctypes.sizeof(B.sylv_problem) == 8 + 4 + 4 + 8 + 3 * 8 + 8 + 2 * 8 + 5 * 8 + 8 + 2 * 4

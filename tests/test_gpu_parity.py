@@ -130,6 +130,31 @@ def test_solve_parity(kind, H, W, k, m, nrhs, precision):
     op.close()
 
 
+@pytest.mark.parametrize("nrhs", [1, 2, 3])
+def test_staged_residual_parity(nrhs, monkeypatch):
+    """Whole tiles and an even caller leading dimension: the FP64 residual stages its streams
+    (reported in the info); with an odd leading dimension the direct kernel runs.  Cold and
+    warm starts, one to three right-hand sides, against the oracle's direct solve.  The tile
+    configuration is pinned to 256-pixel tiles with both staged inner kernels (the staged
+    residual needs 256-pixel tiles; the tuner may prefer 128 on a problem this small)."""
+    monkeypatch.setenv("SYLV_TUNE_FORCE", "256,1,1,1")
+    p = small_problem("sphere", 16, 64, 6, 9, seed=33, nrhs=nrhs)   # n = 1024, (k, m, E) = (6, 9, 4)
+    Xo, b = oracle_solution(p)
+    for ldu in (p.n, p.n + 1):
+        op = operator_for(p, ld=ldu)
+        assert op.ld == ldu
+        Bd = device_batch(b, ldu)
+        X, info = op.solve(Bd, tol=1e-11, precision=1)
+        assert info["code"] == 0, info
+        assert info["residual_staged"] == (1 if ldu % 2 == 0 else 0)
+        assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+        X0 = device_batch(Xo + 1e-3, ldu)
+        X, info = op.solve(Bd, X0=X0, tol=1e-11, precision=1)
+        assert info["code"] == 0
+        assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+        op.close()
+
+
 def test_solve_options_paths():
     """No preconditioner, no graph, profiling, warm start: same solution."""
     p = small_problem("sphere", 16, 20, 4, 6, seed=21)
