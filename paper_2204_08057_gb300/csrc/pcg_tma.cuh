@@ -850,12 +850,13 @@ k_residual_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
       }
       float ri[K], zi[K];
       double rr64 = 0.0, bb = 0.0;
+      const bool start = sh.aux[r] == PH_START;   // ||B||^2 is used by the first residual only
 #pragma unroll
       for (int j = 0; j < K; ++j) {
         const double bj = sb[j * TILE_PX + t];
         const double r64 = bj - gx[j];
         rr64 += r64 * r64;
-        bb += bj * bj;
+        if (start) bb += bj * bj;
         ri[j] = float(r64);
       }
       if (prec) {
