@@ -135,7 +135,7 @@ cudaError_t apply_x_tma(const OpData& op, const float* X, float* Y, int R, unsig
                         cudaStream_t s) {
   static bool attr = false;
   static int grid = 0;
-  const size_t smem = (size_t)tma::NSTAGE * tma::ApplyXLayout<K, M, E>::STAGE_BYTES;
+  const size_t smem = (size_t)tma::NST_X * tma::ApplyXLayout<K, M, E>::STAGE_BYTES;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tma::k_apply_tma<K, M, E>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

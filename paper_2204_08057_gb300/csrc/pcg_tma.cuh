@@ -27,7 +27,9 @@
 namespace sylv {
 namespace tma {
 
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 2;   // stages of the staged kernels' rings (stand-alone apply: NST_X)
+constexpr int NST_X = 3;
+constexpr int MAXST = 3;
 constexpr long long WAIT_BUDGET_CYCLES = 2000000000LL;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -107,16 +109,17 @@ constexpr int WS_THREADS = TILE_PX + 32;
 
 // Shared state of a warp-specialised CTA.
 struct PipeShared {
-  uint64_t full[NSTAGE];
-  uint64_t empty[NSTAGE];
+  uint64_t full[MAXST];
+  uint64_t empty[MAXST];
   int cols[RMAX];
   int nact;
   int bad;
   int issued;
 };
 
+template <int NST = NSTAGE>
 __device__ __forceinline__ void pipe_init(PipeShared& ps) {
-  for (int s = 0; s < NSTAGE; ++s) {
+  for (int s = 0; s < NST; ++s) {
     mbar_init(&ps.full[s], 1);
     mbar_init(&ps.empty[s], NCONS);
   }
@@ -942,9 +945,9 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 1> sh;
   __shared__ __align__(8) PipeShared ps;
-  __shared__ int utile[NSTAGE], ucol[NSTAGE];
+  __shared__ int utile[NST_X], ucol[NST_X];
   stage_operator<float, 1>(op, K, sh);
-  if (threadIdx.x == 0) pipe_init(ps);
+  if (threadIdx.x == 0) pipe_init<NST_X>(ps);
   __syncthreads();
   const int64_t ldu = op.ldu;
   const int ntiles = (int)(op.n / TILE_PX);
@@ -960,10 +963,10 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
       if (!end && lane == 0) next = (int)atomicAdd(ctr + 1, 1u);
       const int nu = end ? 1 : R;
       for (int r = 0; r < nu; ++r, ++u) {
-        const int st = u % NSTAGE;
-        if (u >= NSTAGE) {
+        const int st = u % NST_X;
+        if (u >= NST_X) {
           bool ok = true;
-          if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NSTAGE) - 1) & 1);
+          if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NST_X) - 1) & 1);
           ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
           if (!ok || ps.bad) {
             if (lane == 0) ps.bad = 1;
@@ -1005,8 +1008,8 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
   } else {
     const int t = threadIdx.x;
     for (int u = 0;; ++u) {
-      const int st = u % NSTAGE;
-      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+      const int st = u % NST_X;
+      if (!mbar_wait_bounded(&ps.full[st], (u / NST_X) & 1) || ps.bad) {
         ps.bad = 1;
         break;
       }
@@ -1075,7 +1078,7 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
     if (ps.bad) {
       atomicOr(ctr, 1u);
       for (int u = consumed; u < ps.issued; ++u)
-        mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+        mbar_wait_bounded(&ps.full[u % NST_X], (u / NST_X) & 1);
     }
     // every CTA's producer has finished taking tiles when its CTA gets here; the last CTA
     // resets the counters for the next launch
