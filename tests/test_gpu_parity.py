@@ -132,8 +132,8 @@ def test_solve_parity(kind, H, W, k, m, nrhs, precision):
 
 @pytest.mark.parametrize("nrhs", [1, 2, 3])
 def test_staged_residual_parity(nrhs, monkeypatch):
-    """Whole tiles and an even caller leading dimension: the FP64 residual stages its streams
-    (reported in the info); with an odd leading dimension the direct kernel runs.  Cold and
+    """Whole tiles, an even caller leading dimension and at most two columns: the FP64 residual
+    stages its streams (reported in the info); otherwise the direct kernel runs.  Cold and
     warm starts, one to three right-hand sides, against the oracle's direct solve.  The tile
     configuration is pinned to 256-pixel tiles with both staged inner kernels (the staged
     residual needs 256-pixel tiles; the tuner may prefer 128 on a problem this small)."""
@@ -146,7 +146,7 @@ def test_staged_residual_parity(nrhs, monkeypatch):
         Bd = device_batch(b, ldu)
         X, info = op.solve(Bd, tol=1e-11, precision=1)
         assert info["code"] == 0, info
-        assert info["residual_staged"] == (1 if ldu % 2 == 0 else 0)
+        assert info["residual_staged"] == (1 if ldu % 2 == 0 and nrhs <= 2 else 0)
         assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
         X0 = device_batch(Xo + 1e-3, ldu)
         X, info = op.solve(Bd, X0=X0, tol=1e-11, precision=1)
