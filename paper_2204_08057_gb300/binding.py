@@ -95,6 +95,8 @@ def load(path=None):
     lib.sylv_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]
     lib.sylv_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_int, POINTER(sylv_opts),
                                POINTER(sylv_info), c_void_p]
+    lib.sylv_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int, POINTER(sylv_opts),
+                                    POINTER(sylv_info), c_void_p]
     lib.sylv_solve_batched.argtypes = [c_int, POINTER(c_void_p), POINTER(c_void_p),
                                        POINTER(c_void_p), POINTER(c_int), POINTER(sylv_opts),
                                        POINTER(sylv_info), c_void_p]
@@ -248,6 +250,32 @@ def sylv_solve(h, B, X, nrhs, opts=None, *, k, ld, n, stream=None, allow=()):
                              ctypes.byref(opts) if opts is not None else None,
                              ctypes.byref(info), _stream(stream))
     _check(code, "sylv_solve", ok=(SYLV_OK,) + tuple(allow))
+    return code, info
+
+
+def _host_ptr(t, dtype, numel_min, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{what} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() < numel_min:
+        raise ValueError(f"{what} has {t.numel()} elements, needs {numel_min}")
+    return c_void_p(t.data_ptr())
+
+
+def sylv_solve_host(h, Yobs, X, nrhs, opts=None, *, k, m, ld, n, stream=None, allow=()):
+    """Yobs (nrhs x m x ld) and X (nrhs x k x ld): host float64 tensors (page-locked for
+    overlapped copies).  Returns (status, sylv_info); X holds the solution."""
+    import torch
+    info = sylv_info()
+    code = load().sylv_solve_host(
+        c_void_p(h), _host_ptr(Yobs, torch.float64, ((nrhs - 1) * m + m - 1) * ld + n, "Yobs"),
+        _host_ptr(X, torch.float64, ((nrhs - 1) * k + k - 1) * ld + n, "X"), int(nrhs),
+        ctypes.byref(opts) if opts is not None else None, ctypes.byref(info), _stream(stream))
+    _check(code, "sylv_solve_host", ok=(SYLV_OK,) + tuple(allow))
     return code, info
 
 

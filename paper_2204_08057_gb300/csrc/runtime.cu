@@ -154,6 +154,10 @@ struct sylv_ctx {
   size_t grad_bytes = 0;
   double* var_ws = nullptr;   // sylv_variance: solves of one chunk of probes, num, den
   size_t var_bytes = 0;
+  double* host_ws = nullptr;  // sylv_solve_host: device Yobs, B, X
+  size_t host_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_host[12] = {};   // slices of Yobs copied, start, X updated, X copied
 };
 
 Plan::~Plan() {
@@ -646,9 +650,23 @@ int poll(Plan& P, cudaStream_t s) {
   return SYLV_OK;
 }
 
+// Copies of the solution to the host for sylv_solve_host: after every refinement step's update
+// X += d (not the first, which leaves the start unchanged) the solution is copied on its own
+// stream while the FP64 residual that decides convergence runs, and the next update waits for
+// that copy; the last copy is the result.
+struct HostSink {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_x = nullptr;      // X updated
+  cudaEvent_t ev_done = nullptr;   // copy finished
+  double* host = nullptr;
+  const double* dev = nullptr;
+  size_t bytes = 0;
+  int copies = 0;
+};
+
 template <typename T>
 int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts& o,
-             sylv_info* infos, cudaStream_t s) {
+             sylv_info* infos, cudaStream_t s, HostSink* sink = nullptr) {
   const int nsys = (int)P.hs.size();
   for (int t = 0; t < nsys; ++t) {
     P.h_desc[t].op = P.hs[t]->op;  // operator scalars may have changed since the plan was built
@@ -718,9 +736,18 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   bool first_outer = true;
   while (true) {
     if (!first_outer && (rc = rebalance(P, false, s)) != SYLV_OK) return rc;
+    const bool at_start = first_outer;
     first_outer = false;
+    if (sink && sink->copies > 0) CK(cudaStreamWaitEvent(s, sink->ev_done, 0));
     for (auto& g : P.groups)
       CK(launch_update_x<T>(g.k, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], s));
+    if (sink && !at_start) {
+      CK(cudaEventRecord(sink->ev_x, s));
+      CK(cudaStreamWaitEvent(sink->cs, sink->ev_x, 0));
+      CK(cudaMemcpyAsync(sink->host, sink->dev, sink->bytes, cudaMemcpyDeviceToHost, sink->cs));
+      CK(cudaEventRecord(sink->ev_done, sink->cs));
+      ++sink->copies;
+    }
     if (prof) CK(cudaEventRecord(P.evr0, s));
     for (size_t gi = 0; gi < P.groups.size(); ++gi) {
       Group& g = P.groups[gi];
@@ -920,6 +947,10 @@ static void free_handle(sylv_ctx* h) {
   cudaFree(h->lam);
   cudaFree(h->grad_ws);
   cudaFree(h->var_ws);
+  cudaFree(h->host_ws);
+  for (auto e : h->ev_host)
+    if (e) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
 }
 
@@ -1228,7 +1259,7 @@ int sylv_apply(sylv_handle h, const void* X, void* Y, int nrhs, int dtype, sylv_
 
 static int solve_impl(int nsys, const sylv_handle* hs, const double* const* B, double* const* X,
                       const int* nrhs, const sylv_opts* o_in, sylv_info* infos,
-                      cudaStream_t s, bool single) {
+                      cudaStream_t s, bool single, HostSink* sink = nullptr) {
   sylv_opts o;
   if (o_in) o = *o_in;
   else sylv_opts_default(&o);
@@ -1273,8 +1304,8 @@ static int solve_impl(int nsys, const sylv_handle* hs, const double* const* B, d
     }
     P = it->second.get();
   }
-  return inner_double ? run_plan<double>(*P, B, X, o, infos, s)
-                      : run_plan<float>(*P, B, X, o, infos, s);
+  return inner_double ? run_plan<double>(*P, B, X, o, infos, s, sink)
+                      : run_plan<float>(*P, B, X, o, infos, s, sink);
 }
 
 int sylv_solve(sylv_handle h, const double* B, double* X, int nrhs, const sylv_opts* o,
@@ -1284,6 +1315,77 @@ int sylv_solve(sylv_handle h, const double* B, double* X, int nrhs, const sylv_o
   double* Xs[1] = {X};
   int R[1] = {nrhs};
   return solve_impl(1, &h, Bs, Xs, R, o, info, (cudaStream_t)s, true);
+}
+
+int sylv_solve_host(sylv_handle h, const double* Yobs, double* X, int nrhs, const sylv_opts* o_in,
+                    sylv_info* info, sylv_stream stream) {
+  if (!h || !Yobs || !X) return fail(SYLV_E_INVALID, "NULL argument");
+  if (nrhs < 1 || nrhs > RMAX) return fail(SYLV_E_INVALID, "nrhs out of 1..SYLV_MAX_RHS");
+  sylv_opts o;
+  if (o_in) o = *o_in;
+  else sylv_opts_default(&o);
+  int rc = check_opts(o);
+  if (rc != SYLV_OK) return rc;
+  DeviceGuard g(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const OpData& op = h->op;
+  const size_t ye = (size_t)nrhs * op.m * op.ldu, xe = (size_t)nrhs * op.k * op.ldu;
+  const size_t bytes = (ye + 2 * xe) * sizeof(double);
+  if (h->host_bytes < bytes) {
+    cudaFree(h->host_ws);
+    h->host_ws = nullptr;
+    h->host_bytes = 0;
+    CK(dalloc(&h->host_ws, bytes));
+    h->host_bytes = bytes;
+  }
+  if (!h->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (auto& e : h->ev_host) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  constexpr int NSLICE = 8;
+  cudaEvent_t* ev = h->ev_host;   // [0, NSLICE): slices, NSLICE: start, +1: X updated, +2: copied
+  double* Yd = h->host_ws;
+  double* Bd = Yd + ye;
+  double* Xd = Bd + xe;
+  cudaStream_t cs = h->copy_stream;
+  // the copy stream follows the work already queued on s
+  CK(cudaEventRecord(ev[NSLICE], s));
+  CK(cudaStreamWaitEvent(cs, ev[NSLICE], 0));
+  if (o.use_x0) CK(cudaMemcpyAsync(Xd, X, xe * sizeof(double), cudaMemcpyHostToDevice, cs));
+  // observations in pixel slices: the right-hand side of a slice is formed while the next one
+  // is copied
+  const int64_t n = op.n;
+  const int nsl = n >= (int64_t)NSLICE * 4096 ? NSLICE : 1;
+  const size_t pitch = (size_t)op.ldu * sizeof(double);
+  for (int q = 0; q < nsl; ++q) {
+    const int64_t i0 = n * q / nsl, i1 = n * (q + 1) / nsl;
+    CK(cudaMemcpy2DAsync(Yd + i0, pitch, Yobs + i0, pitch, (size_t)(i1 - i0) * sizeof(double),
+                         (size_t)nrhs * op.m, cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(ev[q], cs));
+    CK(cudaStreamWaitEvent(s, ev[q], 0));
+    CK(launch_rhs_range(op, Yd, Bd, nrhs, i0, i1, s));
+  }
+  HostSink sink;
+  sink.cs = cs;
+  sink.ev_x = ev[NSLICE + 1];
+  sink.ev_done = ev[NSLICE + 2];
+  sink.host = X;
+  sink.dev = Xd;
+  sink.bytes = xe * sizeof(double);
+  const double* Bs[1] = {Bd};
+  double* Xs[1] = {Xd};
+  int R[1] = {nrhs};
+  rc = solve_impl(1, &h, Bs, Xs, R, &o, info, s, true, &sink);
+  cudaError_t e = cudaSuccess;
+  if (sink.copies == 0) {   // the start was already the answer (or the solve stopped early)
+    e = cudaMemcpyAsync(X, Xd, xe * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  const cudaError_t e2 = cudaStreamSynchronize(cs);
+  if (rc != SYLV_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "copy of the solution to the host");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "copy of the solution to the host");
+  return SYLV_OK;
 }
 
 int sylv_solve_batched(int nsys, const sylv_handle* hs, const double* const* B,

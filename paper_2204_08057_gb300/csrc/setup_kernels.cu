@@ -198,9 +198,10 @@ __global__ void k_convert_check(const double* __restrict__ src, int64_t rows, in
 }
 
 // b = B^T C y (eq. mu*): B[r][j][i] = sum_c a_cj d_ci y[r][c][i]
-__global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restrict__ B, int R) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= op.n) return;
+__global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restrict__ B, int R,
+                      int64_t i0, int64_t i1) {
+  const int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= i1) return;
   const int64_t ld = op.ld, ldu = op.ldu;
   for (int r = 0; r < R; ++r) {
     double acc[KMAX];
@@ -459,7 +460,13 @@ cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, f
 }
 
 cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s) {
-  k_rhs<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(op, Y, B, R);
+  return launch_rhs_range(op, Y, B, R, 0, op.n, s);
+}
+
+cudaError_t launch_rhs_range(const OpData& op, const double* Y, double* B, int R, int64_t i0,
+                             int64_t i1, cudaStream_t s) {
+  if (i1 <= i0) return cudaSuccess;
+  k_rhs<<<blocks_for(i1 - i0, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(op, Y, B, R, i0, i1);
   return cudaGetLastError();
 }
 

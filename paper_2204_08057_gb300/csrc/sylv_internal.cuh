@@ -186,6 +186,9 @@ cudaError_t launch_convert_check(const double* src, int64_t rows, int64_t n, int
                                  int64_t ld_dst, float* dst32, double* dst64, int positive,
                                  unsigned int* flags, cudaStream_t s);
 cudaError_t launch_rhs(const OpData& op, const double* Y, double* B, int R, cudaStream_t s);
+// The same for pixels i0 .. i1 - 1 only.
+cudaError_t launch_rhs_range(const OpData& op, const double* Y, double* B, int R, int64_t i0,
+                             int64_t i1, cudaStream_t s);
 cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, float* fs32,
                                __half2* fl16, cudaStream_t s);
 template <typename T>

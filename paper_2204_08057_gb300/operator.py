@@ -115,6 +115,28 @@ class Operator:
         d["code"] = code
         return X, d
 
+    def solve_host(self, Yobs, X0=None, *, out=None, opts=None, stream=None,
+                   allow_not_converged=False, allow=(), **kw):
+        """Posterior mean from host observations: Yobs (nrhs, m, ld) float64 on the host
+        (page-locked for overlapped copies); returns (X on the host (nrhs, k, ld), info).  The
+        copies run inside the call, overlapping the computation (sylv_solve_host)."""
+        import torch
+        Yb = Yobs if Yobs.dim() == 3 else Yobs.unsqueeze(0)
+        nrhs = Yb.shape[0]
+        if opts is None:
+            opts = B.make_opts(**kw)
+        if out is None:
+            out = torch.empty((nrhs, self.k, self.ld), dtype=torch.float64).pin_memory()
+        if X0 is not None:
+            out.copy_(X0 if X0.dim() == 3 else X0.unsqueeze(0))
+            opts.use_x0 = 1
+        allow = tuple(allow) + ((B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ())
+        code, info = B.sylv_solve_host(self.handle, Yb, out, nrhs, opts, k=self.k, m=self.m,
+                                       ld=self.ld, n=self.n, stream=stream, allow=allow)
+        d = info.as_dict()
+        d["code"] = code
+        return out, d
+
     def solve_sylvester(self, Bv, X0=None, *, opts=None, stream=None,
                         allow_not_converged=False, allow=(), **kw):
         """X = G^{-1} B through the Sylvester form and block Lanczos (separable noise, one

@@ -61,6 +61,7 @@ def test_host_only_entry_points(lib):
     assert lib.sylv_create(ctypes.byref(h), ctypes.byref(p), None) == B.SYLV_E_INVALID
     assert "ld" in B.sylv_last_error()
     assert lib.sylv_solve(None, None, None, 1, None, None, None) == B.SYLV_E_INVALID
+    assert lib.sylv_solve_host(None, None, None, 1, None, None, None) == B.SYLV_E_INVALID
     assert lib.sylv_apply(None, None, None, 1, 0, None) == B.SYLV_E_INVALID
     lib.sylv_destroy(None)
 

@@ -155,6 +155,35 @@ def test_staged_residual_parity(nrhs, monkeypatch):
         op.close()
 
 
+@pytest.mark.parametrize("kind,H,W,nrhs", [("sphere", 16, 24, 1), ("sphere", 128, 256, 2)])
+def test_solve_from_host_buffers(kind, H, W, nrhs):
+    """sylv_solve_host (observations and solution in host memory, copies overlapped with the
+    right-hand side and the refinement steps) gives the device path's solution bit for bit:
+    one and eight pixel slices, page-locked and pageable buffers, a warm start, and a zero
+    right-hand side (answered by the first residual, before any update)."""
+    import torch
+    p = small_problem(kind, H, W, 4, 7, seed=44, nrhs=nrhs)
+    op = operator_for(p)
+    Yd = device_batch(p.Yobs, op.ld)
+    Xd, info_d = op.solve(op.rhs(Yd), tol=1e-10)
+    assert info_d["code"] == 0
+    ref = Xd.cpu()
+    Yh = Yd.cpu().pin_memory()
+    X, info = op.solve_host(Yh, tol=1e-10)
+    assert info["code"] == 0 and info["iterations"] == info_d["iterations"]
+    assert torch.equal(X, ref)
+    X2, _ = op.solve_host(Yd.cpu(), out=torch.empty_like(ref), tol=1e-10)   # pageable
+    assert torch.equal(X2, ref)
+    X3, info3 = op.solve_host(Yh, X0=ref, tol=1e-10)
+    assert info3["code"] == 0 and info3["iterations"] == 0
+    assert torch.equal(X3, ref)
+    Xz, infz = op.solve_host(torch.zeros_like(Yh), out=torch.full_like(ref, 7.0), tol=1e-10)
+    assert infz["code"] == 0 and float(Xz.abs().max()) == 0.0
+    Xo, _ = oracle_solution(p)
+    assert relerr(X.numpy()[:, :, :p.n], Xo) <= 1e-6
+    op.close()
+
+
 def test_solve_options_paths():
     """No preconditioner, no graph, profiling, warm start: same solution."""
     p = small_problem("sphere", 16, 20, 4, 6, seed=21)
