@@ -245,6 +245,79 @@ struct UpdateLayout {
   static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
 };
 
+// Operator value of one pixel from its staged data (Sec. 3.1): w_j = tau_j kappa_j^2 x_j +
+// tau_j (L x_j) (lap holds L_ii x_j, the neighbours' values are nb with ELL weights v) +
+// sum_c a_cj d_c (a_c . x); dcol: the pixel's noise weights in the stage (stride TILE_PX).
+template <int K, int M, int E, int NV>
+__device__ __forceinline__ void pixel_operator_ws(const CtaShared<float, NV>& sh, const float* dcol,
+                                                  const float (&zi)[K], float (&lap)[K],
+                                                  const float (&v)[E], const float (&nb)[E][K],
+                                                  float (&w)[K]) {
+  if constexpr (K % 2 == 0) {
+    // the same arithmetic on pairs of sources with the packed FP32 FMA of sm_100+
+    // (fma.rn.f32x2): the stencil, the prior diagonal and the block mapping
+    constexpr int K2 = K / 2;
+    float2 z2[K2], l2[K2], w2[K2];
+#pragma unroll
+    for (int q = 0; q < K2; ++q) {
+      z2[q] = make_float2(zi[2 * q], zi[2 * q + 1]);
+      l2[q] = make_float2(lap[2 * q], lap[2 * q + 1]);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float2 ve = make_float2(v[e], v[e]);
+#pragma unroll
+      for (int q = 0; q < K2; ++q)
+        l2[q] = __ffma2_rn(ve, make_float2(nb[e][2 * q], nb[e][2 * q + 1]), l2[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < K2; ++q) {
+      const float2 tk = make_float2(sh.tk2[2 * q], sh.tk2[2 * q + 1]);
+      const float2 ta = make_float2(sh.tau[2 * q], sh.tau[2 * q + 1]);
+      w2[q] = __ffma2_rn(tk, z2[q], __fmul2_rn(ta, l2[q]));
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      const float d = dcol[c * TILE_PX];
+      const float2* arow = reinterpret_cast<const float2*>(sh.A[c]);
+      float2 a2[K2];
+#pragma unroll
+      for (int q = 0; q < K2; ++q) a2[q] = arow[q];
+      float2 acc = __fmul2_rn(a2[0], z2[0]);
+#pragma unroll
+      for (int q = 1; q < K2; ++q) acc = __ffma2_rn(a2[q], z2[q], acc);
+      const float s = (acc.x + acc.y) * d;
+      const float2 s2 = make_float2(s, s);
+#pragma unroll
+      for (int q = 0; q < K2; ++q) w2[q] = __ffma2_rn(a2[q], s2, w2[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < K2; ++q) {
+      w[2 * q] = w2[q].x;
+      w[2 * q + 1] = w2[q].y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = sh.tk2[j] * zi[j] + sh.tau[j] * lap[j];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      const float d = dcol[c * TILE_PX];
+      float a[K];
+      load_row<K, float>(sh.A[c], a);
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < K; ++j) s += a[j] * zi[j];
+      s *= d;
+#pragma unroll
+      for (int j = 0; j < K; ++j) w[j] += a[j] * s;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // inner_apply (staged): p = z + beta p, q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
@@ -410,25 +483,8 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       for (int e = 0; e < E; ++e)
 #pragma unroll
         for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-#pragma unroll
-        for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
       float w[K];
-#pragma unroll
-      for (int j = 0; j < K; ++j) w[j] = sh.tk2[j] * zi[j] + sh.tau[j] * lap[j];
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        const float d = stage[(L::D + c) * TILE_PX + t];
-        float a[K];
-        load_row<K, float>(sh.A[c], a);
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < K; ++j) s += a[j] * zi[j];
-        s *= d;
-#pragma unroll
-        for (int j = 0; j < K; ++j) w[j] += a[j] * s;
-      }
+      pixel_operator_ws<K, M, E>(sh, stage + (size_t)L::D * TILE_PX + t, zi, lap, v, nb, w);
       const bool first = sh.aux[r] != 0;
       const float beta = sh.sc[r];
       float pq = 0.f;
@@ -1047,25 +1103,8 @@ k_apply_tma(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R
       for (int e = 0; e < E; ++e)
 #pragma unroll
         for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-#pragma unroll
-        for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
       float w[K];
-#pragma unroll
-      for (int j = 0; j < K; ++j) w[j] = sh.tk2[j] * xi[j] + sh.tau[j] * lap[j];
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        const float d = stage[(L::D + c) * TILE_PX + t];
-        float a[K];
-        load_row<K, float>(sh.A[c], a);
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < K; ++j) s += a[j] * xi[j];
-        s *= d;
-#pragma unroll
-        for (int j = 0; j < K; ++j) w[j] += a[j] * s;
-      }
+      pixel_operator_ws<K, M, E>(sh, stage + (size_t)L::D * TILE_PX + t, xi, lap, v, nb, w);
       __syncwarp();
       if (lane == 0) mbar_arrive(&ps.empty[st]);
       consumed = u + 1;
