@@ -1168,7 +1168,29 @@ __global__ void __launch_bounds__(NT, 2) k_lz_assemble(const Args a) {
         g[t / (K * K)][t % (K * K)] = T(a.G[(size_t)s0 * K * K + t]);
       __syncthreads();
       if (!valid) continue;
-      for (int q = 0; q < ns; ++q) {
+      // AB blocks at a time: every load of the batch is issued before its products, so that
+      // AB K loads per thread are in flight (the sums keep the step order)
+      constexpr int AB = 4;
+      int q = 0;
+      for (; q + AB <= ns; q += AB) {
+        T u[AB][K];
+#pragma unroll
+        for (int b = 0; b < AB; ++b) {
+          const T* blk = (const T*)a.basis + (size_t)(s0 + q + b) * a.bstride;
+#pragma unroll
+          for (int p = 0; p < K; ++p) u[b][p] = __ldg(blk + p * ld + i);
+        }
+#pragma unroll
+        for (int b = 0; b < AB; ++b)
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            T x = acc[j];
+#pragma unroll
+            for (int p = 0; p < K; ++p) x += u[b][p] * g[q + b][p * K + j];
+            acc[j] = x;
+          }
+      }
+      for (; q < ns; ++q) {
         const T* blk = (const T*)a.basis + (size_t)(s0 + q) * a.bstride;
         T u[K];
 #pragma unroll
