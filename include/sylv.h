@@ -174,13 +174,14 @@ int sylv_solve(sylv_handle h, const double* B, double* X, int nrhs, const sylv_o
 /* Posterior mean from observations in host memory: X = G^{-1} b with b = B^T C y (eq. mu*,
  * as sylv_rhs forms it), solved as sylv_solve does.  Yobs: host, nrhs x m x ld FP64 (the
  * observation maps of each right-hand side).  X: host, nrhs x k x ld FP64 (the start when
- * o->use_x0; holds the result on return).  The copies overlap the computation: the maps go
- * to the device in pixel slices while the right-hand side of the slices already there is
- * formed, and the solution comes back after every refinement step's update X += d while the
- * FP64 residual that decides convergence runs (the last copy is the result).  Page-locked
- * host memory lets the copies run asynchronously; pageable memory works but copies at its
- * own pace.  Device work space ((m + 2k) x ld doubles per right-hand side) is kept in the
- * handle between calls.  Returns as sylv_solve; the host X is complete when it returns. */
+ * o->use_x0; holds the result on return).  The transfers hide behind computation: page-locked
+ * maps are read in place by the right-hand-side kernel (through their device alias),
+ * pageable ones go to the device in pixel slices while the right-hand side of the slices
+ * already there is formed; the solution comes back (on two copy streams) after every
+ * refinement step's update X += d while the FP64 residual that decides convergence runs (the
+ * last copy is the result).  Device work space ((m + 2k) x ld doubles per right-hand side) is
+ * kept in the handle between calls.  Returns as sylv_solve; the host X is complete when it
+ * returns. */
 int sylv_solve_host(sylv_handle h, const double* Yobs, double* X, int nrhs, const sylv_opts* o,
                     sylv_info* info, sylv_stream s);
 

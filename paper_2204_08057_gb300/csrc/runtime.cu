@@ -156,8 +156,8 @@ struct sylv_ctx {
   size_t var_bytes = 0;
   double* host_ws = nullptr;  // sylv_solve_host: device Yobs, B, X
   size_t host_bytes = 0;
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_host[12] = {};   // slices of Yobs copied, start, X updated, X copied
+  cudaStream_t copy_stream = nullptr, copy_stream2 = nullptr;
+  cudaEvent_t ev_host[12] = {};   // slices of Yobs copied, start, X updated, X copied (x2)
 };
 
 Plan::~Plan() {
@@ -655,9 +655,9 @@ int poll(Plan& P, cudaStream_t s) {
 // stream while the FP64 residual that decides convergence runs, and the next update waits for
 // that copy; the last copy is the result.
 struct HostSink {
-  cudaStream_t cs = nullptr;
-  cudaEvent_t ev_x = nullptr;      // X updated
-  cudaEvent_t ev_done = nullptr;   // copy finished
+  cudaStream_t cs[2] = {nullptr, nullptr};    // the two halves go to two copy engines
+  cudaEvent_t ev_x = nullptr;                 // X updated
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};   // copies finished
   double* host = nullptr;
   const double* dev = nullptr;
   size_t bytes = 0;
@@ -738,14 +738,22 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
     if (!first_outer && (rc = rebalance(P, false, s)) != SYLV_OK) return rc;
     const bool at_start = first_outer;
     first_outer = false;
-    if (sink && sink->copies > 0) CK(cudaStreamWaitEvent(s, sink->ev_done, 0));
+    if (sink && sink->copies > 0) {
+      CK(cudaStreamWaitEvent(s, sink->ev_done[0], 0));
+      CK(cudaStreamWaitEvent(s, sink->ev_done[1], 0));
+    }
     for (auto& g : P.groups)
       CK(launch_update_x<T>(g.k, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], s));
     if (sink && !at_start) {
       CK(cudaEventRecord(sink->ev_x, s));
-      CK(cudaStreamWaitEvent(sink->cs, sink->ev_x, 0));
-      CK(cudaMemcpyAsync(sink->host, sink->dev, sink->bytes, cudaMemcpyDeviceToHost, sink->cs));
-      CK(cudaEventRecord(sink->ev_done, sink->cs));
+      const size_t half = (sink->bytes / 2) & ~(size_t)255;
+      for (int c = 0; c < 2; ++c) {
+        const size_t off = c == 0 ? 0 : half, len = c == 0 ? half : sink->bytes - half;
+        CK(cudaStreamWaitEvent(sink->cs[c], sink->ev_x, 0));
+        CK(cudaMemcpyAsync((char*)sink->host + off, (const char*)sink->dev + off, len,
+                           cudaMemcpyDeviceToHost, sink->cs[c]));
+        CK(cudaEventRecord(sink->ev_done[c], sink->cs[c]));
+      }
       ++sink->copies;
     }
     if (prof) CK(cudaEventRecord(P.evr0, s));
@@ -951,6 +959,7 @@ static void free_handle(sylv_ctx* h) {
   for (auto e : h->ev_host)
     if (e) cudaEventDestroy(e);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->copy_stream2) cudaStreamDestroy(h->copy_stream2);
   delete h;
 }
 
@@ -1340,10 +1349,12 @@ int sylv_solve_host(sylv_handle h, const double* Yobs, double* X, int nrhs, cons
   }
   if (!h->copy_stream) {
     CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->copy_stream2, cudaStreamNonBlocking));
     for (auto& e : h->ev_host) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   constexpr int NSLICE = 8;
-  cudaEvent_t* ev = h->ev_host;   // [0, NSLICE): slices, NSLICE: start, +1: X updated, +2: copied
+  // [0, NSLICE): slices, NSLICE: start, +1: X updated, +2, +3: copies back finished
+  cudaEvent_t* ev = h->ev_host;
   double* Yd = h->host_ws;
   double* Bd = Yd + ye;
   double* Xd = Bd + xe;
@@ -1352,23 +1363,38 @@ int sylv_solve_host(sylv_handle h, const double* Yobs, double* X, int nrhs, cons
   CK(cudaEventRecord(ev[NSLICE], s));
   CK(cudaStreamWaitEvent(cs, ev[NSLICE], 0));
   if (o.use_x0) CK(cudaMemcpyAsync(Xd, X, xe * sizeof(double), cudaMemcpyHostToDevice, cs));
-  // observations in pixel slices: the right-hand side of a slice is formed while the next one
-  // is copied
   const int64_t n = op.n;
-  const int nsl = n >= (int64_t)NSLICE * 4096 ? NSLICE : 1;
-  const size_t pitch = (size_t)op.ldu * sizeof(double);
-  for (int q = 0; q < nsl; ++q) {
-    const int64_t i0 = n * q / nsl, i1 = n * (q + 1) / nsl;
-    CK(cudaMemcpy2DAsync(Yd + i0, pitch, Yobs + i0, pitch, (size_t)(i1 - i0) * sizeof(double),
-                         (size_t)nrhs * op.m, cudaMemcpyHostToDevice, cs));
-    CK(cudaEventRecord(ev[q], cs));
-    CK(cudaStreamWaitEvent(s, ev[q], 0));
-    CK(launch_rhs_range(op, Yd, Bd, nrhs, i0, i1, s));
+  // page-locked maps: the right-hand-side kernel reads them where they are, through their
+  // device alias (no staging copy); pageable ones go to the device in pixel slices, the
+  // right-hand side of a slice being formed while the next one is copied
+  cudaPointerAttributes pa{};
+  const bool direct = cudaPointerGetAttributes(&pa, Yobs) == cudaSuccess &&
+                      pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr;
+  (void)cudaGetLastError();
+  if (direct) {
+    if (o.use_x0) {
+      CK(cudaEventRecord(ev[0], cs));
+      CK(cudaStreamWaitEvent(s, ev[0], 0));
+    }
+    CK(launch_rhs(op, (const double*)pa.devicePointer, Bd, nrhs, s));
+  } else {
+    const int nsl = n >= (int64_t)NSLICE * 4096 ? NSLICE : 1;
+    const size_t pitch = (size_t)op.ldu * sizeof(double);
+    for (int q = 0; q < nsl; ++q) {
+      const int64_t i0 = n * q / nsl, i1 = n * (q + 1) / nsl;
+      CK(cudaMemcpy2DAsync(Yd + i0, pitch, Yobs + i0, pitch, (size_t)(i1 - i0) * sizeof(double),
+                           (size_t)nrhs * op.m, cudaMemcpyHostToDevice, cs));
+      CK(cudaEventRecord(ev[q], cs));
+      CK(cudaStreamWaitEvent(s, ev[q], 0));
+      CK(launch_rhs_range(op, Yd, Bd, nrhs, i0, i1, s));
+    }
   }
   HostSink sink;
-  sink.cs = cs;
+  sink.cs[0] = cs;
+  sink.cs[1] = h->copy_stream2;
   sink.ev_x = ev[NSLICE + 1];
-  sink.ev_done = ev[NSLICE + 2];
+  sink.ev_done[0] = ev[NSLICE + 2];
+  sink.ev_done[1] = ev[NSLICE + 3];
   sink.host = X;
   sink.dev = Xd;
   sink.bytes = xe * sizeof(double);
@@ -1381,7 +1407,9 @@ int sylv_solve_host(sylv_handle h, const double* Yobs, double* X, int nrhs, cons
     e = cudaMemcpyAsync(X, Xd, xe * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
-  const cudaError_t e2 = cudaStreamSynchronize(cs);
+  cudaError_t e2 = cudaStreamSynchronize(cs);
+  const cudaError_t e3 = cudaStreamSynchronize(h->copy_stream2);
+  if (e2 == cudaSuccess) e2 = e3;
   if (rc != SYLV_OK) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "copy of the solution to the host");
   if (e2 != cudaSuccess) return cuda_fail(e2, "copy of the solution to the host");
