@@ -977,10 +977,28 @@ __global__ void __launch_bounds__(WS_THREADS, 3) k_lz_a_tma(const Args a) {
       for (int e = 0; e < E; ++e)
 #pragma unroll
         for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
+      if constexpr (K % 2 == 0) {   // pairs of columns with the packed FP32 FMA (fma.rn.f32x2)
+        float2 l2[K / 2];
 #pragma unroll
-      for (int e = 0; e < E; ++e)
+        for (int q = 0; q < K / 2; ++q) l2[q] = make_float2(lap[2 * q], lap[2 * q + 1]);
 #pragma unroll
-        for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
+        for (int e = 0; e < E; ++e) {
+          const float2 ve = make_float2(v[e], v[e]);
+#pragma unroll
+          for (int q = 0; q < K / 2; ++q)
+            l2[q] = __ffma2_rn(ve, make_float2(nb[e][2 * q], nb[e][2 * q + 1]), l2[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) {
+          lap[2 * q] = l2[q].x;
+          lap[2 * q + 1] = l2[q].y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int j = 0; j < K; ++j) lap[j] += v[e] * nb[e][j];
+      }
       const float ninv = stage[L::NUINV * TILE_PX + t], nu = stage[L::NU * TILE_PX + t];
       float vv[K], qv[K], w[K];
       solve_right<K, float>(uu, sh.Rc, sh.rci, vv);
