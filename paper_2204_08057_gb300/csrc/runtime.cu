@@ -203,11 +203,6 @@ const bool g_staged_apply = [] {
 std::mutex g_plan_mu;
 std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> g_plans;
 
-int default_block(int64_t n) {
-  (void)n;
-  return TILE_PX;
-}
-
 // ------------------------------------------------------------------------------------------
 // tiling of a group and the autotuner
 // ------------------------------------------------------------------------------------------
@@ -1037,7 +1032,6 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   h->explicit_A = p->A != nullptr;
   // validate the CSR and find the ELL width
   unsigned int* dflags = nullptr;
-  int rc = SYLV_OK;
   auto bail = [&](int code) {
     cudaFree(dflags);
     free_handle(h);
@@ -1196,7 +1190,6 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
     return bail(cuda_fail(e, "pixel-block set-up"));
   cudaFree(dflags);
   *out = h;
-  (void)rc;
   return SYLV_OK;
 }
 
