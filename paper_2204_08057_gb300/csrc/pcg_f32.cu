@@ -130,19 +130,20 @@ int residual_tma_occupancy() {
   return nb < 1 ? 1 : nb;
 }
 
-template <int K, int M, int E>
-cudaError_t apply_x_tma(const OpData& op, const float* X, float* Y, int R, unsigned int* err,
-                        cudaStream_t s) {
+template <int K, int M, int E, bool OPS>
+cudaError_t apply_x_tma_impl(const OpData& op, const float* X, float* Y, int R, unsigned int* err,
+                             cudaStream_t s) {
   static bool attr = false;
   static int grid = 0;
-  const size_t smem = (size_t)tma::NST_X * tma::ApplyXLayout<K, M, E>::STAGE_BYTES;
+  const auto kern = OPS ? tma::k_apply_tma_ops<K, M, E> : tma::k_apply_tma<K, M, E>;
+  const size_t smem = OPS ? (size_t)tma::ApplyXOpsLayout<K, M, E>::SMEM
+                          : (size_t)tma::NST_X * tma::ApplyXLayout<K, M, E>::STAGE_BYTES;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tma::k_apply_tma<K, M, E>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0, dev = 0, nsm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tma::k_apply_tma<K, M, E>,
-                                                  tma::WS_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, tma::WS_THREADS, smem);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     grid = nsm * (occ < 1 ? 1 : occ);
@@ -150,8 +151,16 @@ cudaError_t apply_x_tma(const OpData& op, const float* X, float* Y, int R, unsig
   }
   const int ntiles = (int)(op.n / TILE_PX);
   const int g = ntiles < grid ? ntiles : grid;
-  tma::k_apply_tma<K, M, E><<<g, tma::WS_THREADS, smem, s>>>(op, X, Y, R, err);
+  kern<<<g, tma::WS_THREADS, smem, s>>>(op, X, Y, R, err);
   return cudaGetLastError();
+}
+
+// One or two columns: one ring of whole stages; three or more: operator rows once per tile.
+template <int K, int M, int E>
+cudaError_t apply_x_tma(const OpData& op, const float* X, float* Y, int R, unsigned int* err,
+                        cudaStream_t s) {
+  return R >= 3 ? apply_x_tma_impl<K, M, E, true>(op, X, Y, R, err, s)
+                : apply_x_tma_impl<K, M, E, false>(op, X, Y, R, err, s);
 }
 
 }  // namespace

@@ -77,6 +77,27 @@ def test_apply_parity(kind, H, W, k, m, pad):
     op.close()
 
 
+@pytest.mark.parametrize("nrhs", [3, 8])
+def test_staged_apply_many_columns(nrhs):
+    """The staged stand-alone apply stages a tile's operator rows once for all its columns
+    (more columns than ring stages): every column against the oracle, within the FP32 bound."""
+    import torch
+    p = small_problem("sphere", 16, 64, 6, 9, seed=77)   # n = 1024: whole tiles
+    op = operator_for(p)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((nrhs, p.k, p.n))
+    A = model.powerlaw_mixing(p.nu, p.beta)
+    L = oracle_L(p)
+    Xd = device_batch(X, p.n).to(torch.float32)
+    Y32 = op.apply(Xd).cpu().numpy().astype(np.float64)
+    X32 = Xd.cpu().numpy().astype(np.float64)
+    for r in range(nrhs):
+        ref = model.apply(L, p.D, p.tau, p.kappa, A, X32[r])
+        bound = abs_apply(p, X32[r], A)
+        assert np.all(np.abs(Y32[r] - ref) <= 64 * U32 * bound * 1.01 + 1e-30), r
+    op.close()
+
+
 def test_rhs_parity():
     p = small_problem("sphere", 19, 23, 5, 7, seed=9, nrhs=3)
     ld = p.n + 7
