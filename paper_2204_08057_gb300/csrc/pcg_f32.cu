@@ -1,5 +1,5 @@
 // Iteration kernels with inner type float: the generic kernels and the bulk-copy staged ones.
-#include "pcg_tma.cuh"
+#include "apply_ops.cuh"
 
 namespace sylv {
 
