@@ -66,6 +66,24 @@ def test_host_only_entry_points(lib):
     lib.sylv_destroy(None)
 
 
+def test_host_solve_argument_checks(lib):
+    """sylv_solve_host's binding checks its host buffers before any device work."""
+    import torch
+    from paper_2204_08057_gb300 import binding as B
+    Y = torch.zeros((1, 3, 16), dtype=torch.float64)
+    X = torch.zeros((1, 2, 16), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        B.sylv_solve_host(0, Y.float(), X, 1, k=2, m=3, ld=16, n=16)
+    with pytest.raises(ValueError):
+        B.sylv_solve_host(0, Y[:, :, :8], X, 1, k=2, m=3, ld=16, n=16)
+    with pytest.raises(ValueError):
+        B.sylv_solve_host(0, Y, X.t() if X.dim() == 2 else X.transpose(1, 2), 1, k=2, m=3,
+                          ld=16, n=16)
+    assert lib.sylv_solve_host(None, ctypes.c_void_p(Y.data_ptr()),
+                               ctypes.c_void_p(X.data_ptr()), 1, None, None,
+                               None) == B.SYLV_E_INVALID
+
+
 def test_struct_layouts_match_header():
     from paper_2204_08057_gb300 import binding as B
     # sizes implied by the header's field lists on an LP64 ABI
