@@ -112,7 +112,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-# algorithmic bytes per pixel (kernel table)
+# algorithmic bytes per pixel: every stream a kernel must read or write once per pixel
 # ---------------------------------------------------------------------------------------------
 def bytes_inner_apply(k, m, E, s=4):
     # read z, p, q (3k) + D (m) + ELL values (E) + diagonal (1); write p, q (2k); ELL cols int32
@@ -525,7 +525,8 @@ def _base_line(args, metric, value, unit, config, higher=False):
     return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value, "higher_is_better": higher,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-            "data": "synthetic (seeded; see DESIGN.md input recipe)", "config": config}
+            "data": "synthetic (seeded sphere maps shaped like Planck: GMRF-smooth sources, "
+                    "power-law or printed mixing)", "config": config}
 
 
 def run_batched(args):
