@@ -51,14 +51,14 @@ enum {
                              /* the last iterate and info the reached residual           */
   SYLV_E_BREAKDOWN = 5,      /* a CG scalar became non-positive or non-finite            */
   SYLV_E_TIMEOUT = 6,        /* a bounded device-side wait expired                       */
-  SYLV_E_UNSUPPORTED = 7     /* valid but outside what this build handles (e.g. k > 8)   */
+  SYLV_E_UNSUPPORTED = 7     /* valid but outside what this library handles (e.g. k > 8) */
 };
 
 enum { SYLV_F32 = 0, SYLV_F64 = 1 };                  /* element type for sylv_apply      */
 enum { SYLV_PREC_F64 = 0, SYLV_PREC_MIXED = 1 };      /* solve precision                  */
 enum { SYLV_PRECOND_NONE = 0, SYLV_PRECOND_BLOCK_JACOBI = 1 };
 
-/* Limits of this build. */
+/* Limits of this library. */
 #define SYLV_MAX_K 8      /* sources                                   */
 #define SYLV_MAX_M 16     /* channels                                  */
 #define SYLV_MAX_DEGREE 8 /* off-diagonal entries per Laplacian row    */
