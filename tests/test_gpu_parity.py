@@ -46,7 +46,7 @@ CASES = [
     ("lattice", 37, 41, 3, 5, 0),     # 1517 px: 6 tiles of 256, ragged tail
     ("sphere", 20, 33, 6, 9, 5),      # ld > n
     ("lattice", 9, 11, 1, 1, 3),      # scalar case
-    ("sphere", 16, 17, 8, 16, 0),     # largest k and m of this build
+    ("sphere", 16, 17, 8, 16, 0),     # largest k and m the library takes
     ("lattice", 12, 30, 4, 7, 64),
     ("sphere", 3, 4, 2, 3, 1),        # smaller than one tile
     ("sphere", 16, 64, 6, 9, 0),      # whole tiles, aligned rows: staged FP32 apply
@@ -357,7 +357,7 @@ def test_error_statuses():
     with pytest.raises(Bn.SylvError):
         Operator(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=D, tau=p.tau,
                  kappa=p.kappa, nu=p.nu, beta=p.beta)
-    # a row with 9 off-diagonal entries exceeds this build's ELL width
+    # a row with 9 off-diagonal entries exceeds the library's ELL width
     n = 10
     rowptr = np.array([0, 10] + list(range(12, 12 + 2 * 9, 2)), dtype=np.int32)
     col = np.concatenate([np.arange(10), np.ravel([[i, 0] for i in range(1, 10)])])
