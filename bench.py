@@ -768,7 +768,9 @@ def run_sylvester(args):
         "kernel_ms_per_solve": {"pass_a": info_prof["ms_apply"], "pass_b": info_prof["ms_update"],
                                 "residual64_and_assembly": info_prof["ms_residual"],
                                 "timing": "CUDA events around every launch, one extra solve"},
-        "roofline": {"bound": "hbm", "kernel": f"k_lz_a<{p.k},{E},float>",
+        "roofline": {"bound": "hbm",
+                     "kernel": (f"k_lz_a_tma<{p.k},{E}>" if info_prof.get("apply_staged")
+                                else f"k_lz_a<{p.k},{E},float>"),
                      "achieved": ba / (ms_a * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": ba / (ms_a * 1e-3) / 1e9 / peak, "traffic": None,
                      "bytes_per_launch": ba, "ms_per_launch": ms_a,
