@@ -5,6 +5,7 @@ compiled in parallel and linked with the static CUDA runtime; no PyTorch headers
 """
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -59,10 +60,23 @@ def _stale():
 
 
 def build(force=False, verbose_ptxas=False, quiet=True):
-    """Compiles and links libsylv.so if any source is newer than it.  Returns its path."""
+    """Compiles and links libsylv.so if any source is newer than it.  Returns its path.
+    Processes that build at once (one per rank) take turns on a lock file; a process that
+    finds the library fresh once it holds the lock does not rebuild it."""
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not _stale():
+                return LIB
+            return _build_locked(verbose_ptxas, quiet)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose_ptxas, quiet):
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         results = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
     objs = [r[0] for r in results]
