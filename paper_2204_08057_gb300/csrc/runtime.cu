@@ -498,11 +498,12 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
       g.cta_cap += P.work[s].slot_cap;
     }
     g.cta_cap += 1;
+    P.groups.push_back(g);  // owned by the plan before its lists are allocated
+    Group& gp = P.groups.back();
     for (int k = 0; k < 4; ++k) {
-      CK(dalloc(&g.d_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
-      CK(cudaMallocHost((void**)&g.h_ctas[k], (size_t)g.cta_cap * sizeof(CtaRef)));
+      CK(dalloc(&gp.d_ctas[k], (size_t)gp.cta_cap * sizeof(CtaRef)));
+      CK(cudaMallocHost((void**)&gp.h_ctas[k], (size_t)gp.cta_cap * sizeof(CtaRef)));
     }
-    P.groups.push_back(g);
   }
   for (int s = 0; s < nsys; ++s) {
     const OpData& op = hs[s]->op;
@@ -717,9 +718,16 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   }
   const long max_polls = (long)o.maxit / iters + 4L * (o.max_outer + 2) + 16;
   bool gave_up = false;
-  std::vector<cudaEvent_t> direct_events;
+  struct Events {  // destroyed on every return
+    std::vector<cudaEvent_t> v;
+    ~Events() {
+      for (auto e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } direct;
+  std::vector<cudaEvent_t>& direct_events = direct.v;
   if (prof && !o.use_graph) {
-    direct_events.resize(2 * iters + 1);
+    direct_events.assign(2 * iters + 1, nullptr);
     for (auto& e : direct_events) CK(cudaEventCreate(&e));
   }
   int rc = SYLV_OK;
@@ -809,7 +817,6 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
       break;
     }
   }
-  for (auto e : direct_events) cudaEventDestroy(e);
   if (rc != SYLV_OK) return rc;
   CK(cudaEventRecord(P.ev1, s));
   // read back per-column states
@@ -1340,10 +1347,18 @@ int sylv_solve_host(sylv_handle h, const double* Yobs, double* X, int nrhs, cons
     CK(dalloc(&h->host_ws, bytes));
     h->host_bytes = bytes;
   }
-  if (!h->copy_stream) {
-    CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&h->copy_stream2, cudaStreamNonBlocking));
-    for (auto& e : h->ev_host) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // created on first use; each is kept only once it exists, so a failed call is retried whole
+  for (cudaStream_t* cs : {&h->copy_stream, &h->copy_stream2}) {
+    if (*cs) continue;
+    cudaStream_t t = nullptr;
+    CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+    *cs = t;
+  }
+  for (auto& e : h->ev_host) {
+    if (e) continue;
+    cudaEvent_t t = nullptr;
+    CK(cudaEventCreateWithFlags(&t, cudaEventDisableTiming));
+    e = t;
   }
   constexpr int NSLICE = 8;
   // [0, NSLICE): slices, NSLICE: start, +1: X updated, +2, +3: copies back finished
