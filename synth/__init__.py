@@ -15,6 +15,12 @@ from .grids import (  # noqa: F401
     laplacian_csr_from_edges,
 )
 from .physical import PLANCK_A_PRINTED, PLANCK_T_PRINTED  # noqa: F401
+from .order import (  # noqa: F401
+    blocked_order,
+    permute_graph,
+    permute_problem,
+    outside_tile_fraction,
+)
 from .problems import (  # noqa: F401
     PLANCK_NU,
     Problem,

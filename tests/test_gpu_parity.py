@@ -176,6 +176,26 @@ def test_staged_residual_parity(nrhs, monkeypatch):
         op.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_blocked_pixel_order_parity(precision, monkeypatch):
+    """The workload's grid in 16 x 16-pixel blocks (a renumbering that keeps most stencil
+    neighbours inside a pixel's own 256-pixel tile): the staged kernels' solution is the
+    oracle's solution of the row-major problem, renumbered."""
+    monkeypatch.setenv("SYLV_TUNE_FORCE", "256,1,1,1")
+    p = small_problem("sphere", 32, 64, 6, 9, seed=41)   # n = 2048: 8 tiles of 16 x 16 blocks
+    perm = synth.blocked_order(32, 64, 16, 16)
+    q = synth.permute_problem(p, perm)
+    Xo, b = oracle_solution(p)
+    op = operator_for(q)
+    # cond(G) is ~8.7e5 here, so a relative solution error of 1e-8 needs relres ~1e-12
+    X, info = op.solve(device_batch(b[:, :, perm], q.n), tol=1e-12 if precision == 0 else 1e-11,
+                       precision=precision)
+    assert info["code"] == 0, info
+    assert relerr(X.cpu().numpy()[:, :, :q.n], Xo[:, :, perm]) <= (1e-8 if precision == 0
+                                                                  else 1e-6)
+    op.close()
+
+
 @pytest.mark.parametrize("kind,H,W,nrhs", [("sphere", 16, 24, 1), ("sphere", 128, 256, 2)])
 def test_solve_from_host_buffers(kind, H, W, nrhs):
     """sylv_solve_host (observations and solution in host memory, copies overlapped with the
