@@ -33,8 +33,9 @@ SYLV_PRIOR_IGMRF = 1
 MAX_K, MAX_M, MAX_DEGREE, MAX_RHS = 8, 16, 8, 16
 
 EXPORTED = ["sylv_opts_default", "sylv_create", "sylv_rhs", "sylv_apply", "sylv_solve",
-            "sylv_solve_batched", "sylv_backward", "sylv_destroy", "sylv_strerror",
-            "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester", "sylv_variance", "sylv_set_params"]
+            "sylv_solve_host", "sylv_solve_batched", "sylv_backward", "sylv_destroy",
+            "sylv_strerror", "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester",
+            "sylv_variance", "sylv_set_params"]
 
 
 class sylv_problem(ctypes.Structure):

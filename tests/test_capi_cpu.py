@@ -43,6 +43,11 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_binding_covers_the_header():
+    from paper_2204_08057_gb300 import binding as B
+    assert sorted(B.EXPORTED) == sorted(declared_functions())
+
+
 def test_host_only_entry_points(lib):
     from paper_2204_08057_gb300 import binding as B
     o = B.sylv_opts_default()
