@@ -56,3 +56,14 @@ def test_rank0_instance_is_the_single_gpu_workload():
     a = bench.rank_problem(2, 0, scale=32)
     b = synth.config_problem(2, scale=32)
     assert np.array_equal(a.D, b.D) and np.array_equal(a.Yobs, b.Yobs)
+
+
+def test_blocked_order_applies_to_every_rank():
+    import bench
+    import synth
+    perm = synth.blocked_order(32, 64, 16, 16)
+    for rank in (0, 1):
+        row = bench.rank_problem(2, rank, scale=32)
+        blk = bench.rank_problem(2, rank, scale=32, order="blocked")
+        assert np.array_equal(blk.D, row.D[:, perm]) and np.array_equal(blk.Yobs, row.Yobs[:, :, perm])
+        assert blk.name == row.name + "_blocked"
