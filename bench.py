@@ -128,9 +128,59 @@ def bytes_inner_update(k, m, s=4):
     return (8 * k) * s + 2 * (k * (k + 1) // 2)
 
 
+def fp64_ops_inner(k, E):
+    """FP64 floating-point operations per pixel of one FP64 PCG iteration (an FMA is two), as
+    the FP64 kernels compute them: the operator kernel (pixel block k^2 FMAs, stencil E k, the
+    tau scaling k, p and q updates 2k, p . q k) and the update kernel (d and r updates 2k,
+    block solve k(k-1) FMAs and 4k multiplies, r . z and r . r 2k)."""
+    apply_fma = k * k + E * k + 4 * k
+    update_fma, update_mul = k * k + 3 * k, 4 * k
+    return 2 * apply_fma + 2 * update_fma + update_mul
+
+
+def bytes_inner_fp64(k, E):
+    """Bytes per pixel of one FP64 PCG iteration: operator kernel reads z, p, q, the FP64 pixel
+    block (k(k+1)/2), ELL values (FP64) and columns, writes p, q; update kernel reads d, p, r,
+    q and the FP64 factor (k + k(k+1)/2), writes d, r, z."""
+    nb = k * (k + 1) // 2
+    return (5 * k * 8 + nb * 8 + E * 8 + 4 * E) + (7 * k * 8 + (k + nb) * 8)
+
+
+def fp64_peak_tflops(dev):
+    """Measured FP64 peak of this GPU: a cuBLAS DGEMM of 4096^3 (2 n^3 operations) through
+    torch, best of 5 timed with CUDA events after 2 warm-ups (the dense FP64 rate this part
+    reaches; the FP64 PCG kernels do FMAs and multiplies on the same units)."""
+    import torch
+    n = 4096
+    g = torch.Generator(device=dev).manual_seed(0)
+    a = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    b = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    for _ in range(2):
+        torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
 def bytes_apply(k, m, E, R=1, s=4):
     # read X (R k) + D (m) + ELL values (E) + diagonal (1); write Y (R k); ELL cols int32
     return (2 * R * k + m + E + 1) * s + 4 * E
+
+
+def kernel_name(kind, variant, k, m, E):
+    """Name of the inner kernel a solve ran (variant as reported in sylv_info)."""
+    shape = f"{k},{m},{E}" if E else f"{k},0,0"
+    if kind == "apply":
+        return {0: f"k_inner_apply<{shape},float>", 1: f"k_inner_apply_tma<{shape}>",
+                2: f"k_inner_apply_mc<{shape}>"}[variant]
+    return {0: f"k_inner_update<{shape},float>", 1: f"k_inner_update_tma<{k},{m}>",
+            2: f"k_inner_update_mc<{k},{m}>"}[variant]
 
 
 KERNEL_SOURCES = ["pcg_kernels.cuh", "pcg_tma.cuh", "sylv_internal.cuh"]
@@ -200,6 +250,27 @@ def oracle_pcg_sample(p, seconds, iters_ref):
     }
 
 
+def oracle_pcg_full(p):
+    """Times one whole solve of the oracle's block-Jacobi PCG (FP64, numpy/scipy) on the full
+    workload to recursive relres 1e-8, and reports its true FP64 relres.  Returns a
+    cpu_baseline dict (a measured solve, no projection)."""
+    from oracle import model, solve
+    L = model.laplacian_from_csr(p.graph.rowptr, p.graph.col, p.graph.val, p.n)
+    A = model.powerlaw_mixing(p.nu, p.beta)
+    b = model.rhs(p.D, p.Yobs[0], A)
+    t0 = time.perf_counter()
+    x, it, rel_rec, secs = solve.pcg_block_jacobi(L, p.D, p.tau, p.kappa, A, b, eps=1e-8)
+    wall = time.perf_counter() - t0
+    rel_true = solve.relres(L, p.D, p.tau, p.kappa, A, x, b)
+    return {
+        "value": secs * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+        "sample": (f"one whole solve of the oracle's FP64 block-Jacobi PCG (numpy/scipy, default "
+                   f"threading) on the full {p.name} system to relres 1e-8: {it} iterations in "
+                   f"{secs:.1f} s ({wall:.1f} s with set-up), true relres {rel_true:.2e}"),
+        "measured": "whole solve", "iterations": it, "relres_true": rel_true,
+    }
+
+
 def stored_iterations(config):
     path = os.path.join(ROOT, "tests", "golden", f"oracle_pcg_iterations_c{config}.json")
     try:
@@ -217,11 +288,16 @@ def run_reference(args, rank, world):
     p = synth.config_problem(args.config, scale=args.scale)
     iters = stored_iterations(args.config)
     vals = []
+    walls = []
     sample = None
+    # a step is one bounded sample of the solve (the whole run stays within a few minutes);
+    # the value is the sample's ms per iteration times the oracle's iteration count to 1e-8
     per_step = max(3.0, min(args.cpu_seconds, 150.0 / max(args.steps + args.warmup, 1)))
     for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         cb = oracle_pcg_sample(p, per_step, iters or 1)
         if step >= args.warmup:
+            walls.append(time.perf_counter() - t0)
             vals.append(cb["value"])
             sample = cb
     v = float(np.mean(vals))
@@ -229,15 +305,26 @@ def run_reference(args, rank, world):
         sample["sample"] += " [no stored oracle iteration count: value is ms per iteration]"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "nrhs": 1,
-                       "tol": 1e-8},
+            "ms_per_step": float(np.mean(walls)) * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "precision": "FP64 (the CPU oracle)",
+            "value_is": "projection: ms per oracle iteration (timed) x the oracle's iteration "
+                        "count to relres 1e-8; ms_per_step is the wall time of one bounded "
+                        "sample step",
+            "config": main_config(p),
             "cpu_baseline": {"value": v, "unit": "ms", "cores": sample["cores"],
                              "kind": "oracle", "sample": sample["sample"]},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def main_config(p):
+    """The `config` of the main workload's line (both arms print the same)."""
+    return {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "nrhs": 1, "tol": 1e-8,
+            "l2": "inputs larger than L2 (working set ~%d MB)"
+                  % int((p.n * (5 * p.k * 4 + 2 * p.k * 8 + p.m * 12 + 44)) / 1e6),
+            "per_rank": "independent instance per rank (own seed)"}
 
 
 def with_order(p, order):
@@ -357,7 +444,9 @@ def run_ours(args, rank, world, local_rank):
     assert last["code"] == 0, last
 
     # ---- plain FP64 PCG on the same system ----------------------------------------------------
-    kw64 = dict(tol=1e-8, precision=0, profile=1)
+    # timed without per-kernel events like the mixed solve; then one profiled solve gives its
+    # kernel times for the FP64 roofline
+    kw64 = dict(tol=1e-8, precision=0, profile=0)
     X64, info64 = op.solve(B, **kw64)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -367,7 +456,26 @@ def run_ours(args, rank, world, local_rank):
     f1.record(stream)
     barrier()
     ms64 = f0.elapsed_time(f1) / max(args.fp64_steps, 1)
+    _, info64p = op.solve(B, tol=1e-8, precision=0, profile=1)
     relerr_mixed_vs_fp64 = float(torch.linalg.norm(X - X64) / torch.linalg.norm(X64))
+    peak64 = fp64_peak_tflops(dev)
+    its64 = max(info64p["iterations"], 1)
+    ms_it64 = (info64p["ms_apply"] + info64p["ms_update"]) / its64
+    flops64 = fp64_ops_inner(p.k, E) * p.n
+    bytes64 = bytes_inner_fp64(p.k, E) * p.n
+    fp64_roof = {
+        "bound": "fp64",
+        "achieved_tflops": flops64 / (ms_it64 * 1e-3) / 1e12, "peak_tflops": peak64,
+        "frac_fp64": flops64 / (ms_it64 * 1e-3) / 1e12 / peak64,
+        "achieved_gbs": bytes64 / (ms_it64 * 1e-3) / 1e9,
+        "frac_hbm": bytes64 / (ms_it64 * 1e-3) / 1e9 / load_peaks()[0],
+        "ms_per_iteration": ms_it64, "flops_per_pixel_iteration": fp64_ops_inner(p.k, E),
+        "bytes_per_pixel_iteration": bytes_inner_fp64(p.k, E),
+        "kernels": ["k_inner_apply<%d,%d,%d,double>" % (p.k, p.m, E),
+                    "k_inner_update<%d,%d,%d,double>" % (p.k, p.m, E)],
+        "peak_source": "cuBLAS DGEMM 4096^3 through torch, best of 5 (CUDA events), measured "
+                       "in this run; clocks as sampled for the line",
+        "timing": "CUDA events around every launch in one profiled FP64 solve"}
 
     # ---- stand-alone operator apply (FP32), inputs larger than L2 ----------------------------
     X32 = X.to(torch.float32)
@@ -395,12 +503,10 @@ def run_ours(args, rank, world, local_rank):
     n_ap = n_up = sum(i["iterations"] for i in infos)
     shape = f"{p.k},{p.m},{E}" if E else f"{p.k},0,0"
     if tot_apply >= tot_update:
-        kname = (f"k_inner_apply_tma<{shape}>" if last["apply_staged"]
-                 else f"k_inner_apply<{shape},float>")
+        kname = kernel_name("apply", last["apply_staged"], p.k, p.m, E)
         avg_ms, per_px = tot_apply / n_ap, bytes_inner_apply(p.k, p.m, E)
     else:
-        kname = (f"k_inner_update_tma<{p.k},{p.m}>" if last["update_staged"]
-                 else f"k_inner_update<{shape},float>")
+        kname = kernel_name("update", last["update_staged"], p.k, p.m, E)
         avg_ms, per_px = tot_update / n_up, bytes_inner_update(p.k, p.m)
     achieved = per_px * p.n / (avg_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -436,8 +542,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- CPU oracle baseline (rank 0, N = 1) -------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters = stored_iterations(args.config) or info64["iterations"]
-        cpu = oracle_pcg_sample(p, args.cpu_seconds, iters)
+        cpu = oracle_pcg_full(p)
 
     if rank == 0:
         line = {
@@ -446,11 +551,8 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded sphere maps shaped like Planck: GMRF-smooth sources, "
                     "lognormal noise, power-law mixing)",
-            "config": {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "nrhs": 1,
-                       "tol": 1e-8, "precision": "mixed (FP32 inner PCG, FP64 refinement)",
-                       "l2": "inputs larger than L2 (working set ~%d MB)"
-                             % int((p.n * (5 * p.k * 4 + 2 * p.k * 8 + p.m * 12 + 44)) / 1e6),
-                       "per_rank": "independent instance per rank (own seed)"},
+            "config": main_config(p),
+            "precision": "mixed (FP32 inner PCG, FP64 refinement)",
             "iterations": last["iterations"], "outer": last["outer"],
             "relres": last["relres"],
             "autotune": {"tile": last["tile"], "slots_mult": last["slots_mult"],
@@ -463,7 +565,8 @@ def run_ours(args, rank, world, local_rank):
             "rhs": {"ms": ms_rhs, "gbs": rhs_bytes / (ms_rhs * 1e-3) / 1e9},
             "fp64_pcg": {"ms": ms64, "iterations": info64["iterations"],
                          "relres": info64["relres"], "speedup_mixed": ms64 / ms,
-                         "relerr_mixed_vs_fp64": relerr_mixed_vs_fp64},
+                         "relerr_mixed_vs_fp64": relerr_mixed_vs_fp64,
+                         "roofline": fp64_roof},
             "apply": {"ms": ms_apply, "gbs": apply_gbs, "frac": apply_gbs / peak,
                       "bytes": apply_bytes, "dtype": "f32"},
             "roofline": roofline,
@@ -545,41 +648,74 @@ def _base_line(args, metric, value, unit, config, higher=False):
 
 def run_batched(args):
     """64 independent lattice systems (sides 128..1024, k in 3..6, m = k + 2) in one
-    sylv_solve_batched call vs the same systems solved one by one and vs FP64 batched."""
+    sylv_solve_batched call vs the same systems solved one by one and vs FP64 batched.
+    Under torchrun the 64 systems are split across the ranks (balanced on pixels x sources,
+    no collective on the data path): each rank solves its subset in one batched call and the
+    value is the slowest rank's time for the whole batch (total work fixed: strong scaling)."""
     import torch
     import synth
     from paper_2204_08057_gb300 import build as _build
     from paper_2204_08057_gb300.operator import solve_batched
+    from paper_2204_08057_gb300.partition import partition_batch
     _build.build()
-    torch.cuda.set_device(0)
-    probs = synth.batch_problems(64)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    shapes = synth.batch_shapes(64)
+    parts = partition_batch([s * s * k for s, k in shapes], world)
+    mine = parts[rank]
+    probs = synth.batch_problems(64, indices=mine)
     ops = [make_operator(p) for p in probs]
     Bs = [op.rhs(torch.from_numpy(p.Yobs).cuda()) for op, p in zip(ops, probs)]
     stream = torch.cuda.current_stream()
     kw = dict(tol=1e-8, precision=1, profile=1)
     for _ in range(args.warmup):
         Xs, infos = solve_batched(ops, Bs, **kw)
-    clocks = ClockSampler(0) if not args.no_clocks else None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank) if not args.no_clocks else None
     if clocks:
         clocks.start()
         time.sleep(0.5)
+    barrier()
     ms, (Xs, infos) = _timed(stream, lambda: solve_batched(ops, Bs, **kw), args.steps)
+    barrier()
     clk = clocks.stop() if clocks else None
+    ms = max_over_ranks(ms, dist, torch.device("cuda", local_rank))
     assert all(i["status"] == 0 for i in infos), infos
-    for op, b in zip(ops, Bs):
-        op.solve(b, tol=1e-8)
-    ms_seq, _ = _timed(stream, lambda: [op.solve(b, tol=1e-8) for op, b in zip(ops, Bs)], 1)
-    solve_batched(ops, Bs, tol=1e-8, precision=0)
-    ms64, (X64, i64) = _timed(stream, lambda: solve_batched(ops, Bs, tol=1e-8, precision=0), 1)
-    rel = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(Xs, X64))
-    ntot = sum(p.n for p in probs)
+    extra = {}
+    if world == 1:
+        for op, b in zip(ops, Bs):
+            op.solve(b, tol=1e-8)
+        ms_seq, _ = _timed(stream, lambda: [op.solve(b, tol=1e-8) for op, b in zip(ops, Bs)], 1)
+        solve_batched(ops, Bs, tol=1e-8, precision=0)
+        ms64, (X64, i64) = _timed(stream, lambda: solve_batched(ops, Bs, tol=1e-8, precision=0),
+                                  1)
+        rel = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+                  for a, b in zip(Xs, X64))
+        extra = {"sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms,
+                 "fp64_batched_ms": ms64, "speedup_vs_fp64": ms64 / ms,
+                 "max_relerr_mixed_vs_fp64": rel}
+    ntot = sum(s * s for s, _ in shapes)
     line = _base_line(args, "batched solve time to relres 1e-8 (64 systems, one call)", ms, "ms",
-                      {"workload": "batch64_lattice128-1024_k3-6", "systems": len(probs),
+                      {"workload": "batch64_lattice128-1024_k3-6", "systems": len(shapes),
                        "total_pixels": ntot, "tol": 1e-8, "precision": "mixed"})
+    line.update(extra)
     line.update({
-        "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms,
-        "fp64_batched_ms": ms64, "speedup_vs_fp64": ms64 / ms,
-        "max_relerr_mixed_vs_fp64": rel,
+        "n_gpus": world, "scaling": "strong" if world > 1 else "weak",
+        "partition": {"systems_per_rank": [len(q) for q in parts],
+                      "work_per_rank": [sum(shapes[i][0] ** 2 * shapes[i][1] for i in q)
+                                        for q in parts],
+                      "rule": "largest first to the least-loaded rank, work = n k"},
         "iterations_max": max(i["iterations"] for i in infos),
         "relres_max": max(i["relres"] for i in infos),
         "kernel_ms_per_solve": {"inner_apply": infos[0]["ms_apply"],
@@ -587,9 +723,12 @@ def run_batched(args):
                                 "residual64": infos[0]["ms_residual"]},
         "gpu_launches": infos[0]["launches"], "clocks": clk,
     })
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     for op in ops:
         op.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_differentiable(args):

@@ -131,8 +131,10 @@ typedef struct {
   /* configuration the autotuner chose for the inner kernels (first shape group)          */
   int32_t tile;        /* pixels per tile = threads per CTA                                 */
   int32_t slots_mult;  /* CTA slots as a multiple of the resident CTAs                      */
-  int32_t apply_staged;  /* 1: operator kernel stages its streams with bulk copies         */
-  int32_t update_staged; /* 1: update kernel stages its streams with bulk copies           */
+  int32_t apply_staged;  /* operator kernel: 0 direct loads; 1 bulk-copy staged per (tile,  */
+                         /* right-hand side); 2 multi-column: a tile's operator data staged */
+                         /* once and kept in registers for all its right-hand sides         */
+  int32_t update_staged; /* update kernel, the same three variants                          */
   int32_t residual_staged; /* 1: the FP64 residual kernel stages its streams (mixed mode,
                               whole tiles, even ldu, 16-byte aligned X and B)              */
   int32_t reserved_info;   /* 0                                                          */
@@ -260,19 +262,22 @@ int sylv_solve_sylvester(sylv_handle h, const double* B, double* X, int nrhs,
                          const sylv_opts* o, sylv_info* info, sylv_stream s);
 
 /* Allocation-free variant of sylv_solve (the paper has no counterpart; this is a service for
- * callers that cannot allocate).  Some callers cannot call cudaMalloc, or any routine that
- * allocates, at the point where they solve: a real-time pipeline whose memory is reserved
- * at start-up, a process held to a fixed device-memory budget, or a loop that must not incur
- * an allocator's implicit synchronisation.  This entry point runs the same preconditioned CG
+ * callers that cannot allocate). Some callers cannot call cudaMalloc, or any routine that
+ * allocates, at the point where they solve: a real-time pipeline whose memory is reserved at
+ * start-up, a process held to a fixed device-memory budget, or a loop that must not incur an
+ * allocator's implicit synchronisation. This entry point runs the same preconditioned CG
  * inside FP64 refinement as sylv_solve (same arguments and results, without the staged
  * kernels, CUDA graphs or per-kernel timing; info->ms_total is host wall time) and keeps its
  * whole workspace in one file-scope device array of 16 MiB that every GPU loading the library
- * holds until the process exits.  It allocates nothing: no device or pinned memory, events,
- * graphs or host heap.  The array's device address is looked up on the first call on each
- * device, so that first call should come before any stream capture.  All calls share the
- * array: calls that overlap on the GPU (other streams or threads) race; serialise them.
- * Problems whose workspace (about 20 * nrhs * k * n bytes in mixed precision, 40 in FP64)
- * exceeds the array return SYLV_E_UNSUPPORTED.  Synchronises s. */
+ * holds until the process exits. It allocates nothing: no device or pinned memory, events,
+ * graphs or host heap (error text goes to a fixed per-thread buffer). The array's device
+ * address is looked up on the first call on each device, so that first call should come
+ * before any stream capture; it stays valid for the process, so neither this entry point nor
+ * any handle may be used after a cudaDeviceReset. All calls share the array: calls that
+ * overlap on the GPU (other streams or threads) race; serialise them. Every return, error
+ * returns included, leaves the stream idle. Problems whose workspace (about 20 * nrhs * k * n
+ * bytes in mixed precision, 40 in FP64) exceeds the array return SYLV_E_UNSUPPORTED.
+ * Synchronises s. */
 int sylv_solve_noalloc(sylv_handle h, const double* B, double* X, int nrhs,
                        const sylv_opts* o, sylv_info* info, sylv_stream s);
 

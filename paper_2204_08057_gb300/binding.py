@@ -6,6 +6,7 @@ and the current CUDA stream are passed through.  The library must have been buil
 (``paper_2204_08057_gb300.build.build()``); there is no fallback when it is missing.
 """
 
+import collections
 import ctypes
 import os
 from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_void_p
@@ -13,6 +14,9 @@ from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_void_
 import numpy as np
 
 from . import build as _build
+
+# successful calls of entry points that build device state, by name (handles made so far)
+calls = collections.Counter()
 
 SYLV_OK = 0
 SYLV_E_INVALID = 1
@@ -211,6 +215,7 @@ def sylv_create(*, n, k, m, ld, L_rowptr, L_col, L_val, D, tau, kappa, nu=None, 
         setattr(p, name, ptr)
     h = c_void_p()
     _check(load().sylv_create(ctypes.byref(h), ctypes.byref(p), _stream(stream)), "sylv_create")
+    calls["sylv_create"] += 1
     return h.value
 
 

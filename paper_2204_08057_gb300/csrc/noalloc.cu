@@ -11,11 +11,16 @@
 //
 // Properties (also stated in include/sylv.h):
 // * Nothing is allocated: no cudaMalloc/cudaFree, no pinned host buffers, no events, no CUDA
-//   graphs, no heap memory on the host; control data travels through stack variables.
+//   graphs, no heap memory on the host (error messages go to a fixed per-thread buffer);
+//   control data travels through stack variables.
 // * The array exists once per device for the life of the process (every GPU that loads the
 //   library holds it).  Its device address is looked up with cudaGetSymbolAddress the first
 //   time the entry point runs on a device (with that device current); that first call should
-//   therefore come before any stream capture.
+//   therefore come before any stream capture.  The address is kept for the process: after a
+//   cudaDeviceReset (which also invalidates every handle) the module may load elsewhere, so
+//   neither handles nor this entry point may be used after one.
+// * Every return leaves the stream idle: on an error after the first launch the call waits
+//   for the work it queued before it returns.
 // * Every call shares the array, so calls that overlap on the GPU (two streams, two threads)
 //   race and corrupt each other; serialise them.  Each call rewrites everything it reads
 //   before reading it (the kernels that start a solve clear the counters and CG state).
@@ -72,6 +77,20 @@ int cuda_msg(cudaError_t e, const char* what) {
   do {                                                     \
     cudaError_t _e = (call);                               \
     if (_e != cudaSuccess) return cuda_msg(_e, #call);     \
+  } while (0)
+
+// The same inside the solve loop, where kernels may already be queued on s: before returning,
+// wait (ignoring the result) until they have finished, so that no return leaves work running
+// on the shared array, which the caller's next call would race with.
+#define NA_CK_DRAIN(call)                                  \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) {                               \
+      const int _rc = cuda_msg(_e, #call);                 \
+      (void)cudaStreamSynchronize(s);                      \
+      (void)cudaGetLastError();                            \
+      return _rc;                                          \
+    }                                                      \
   } while (0)
 
 struct Poll {
@@ -163,7 +182,7 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   NA_CK(cudaMemcpyAsync(d_cols, cols, 2 * R * sizeof(int), cudaMemcpyHostToDevice, s));
   if (!o.use_x0)
     NA_CK(cudaMemsetAsync(X, 0, (size_t)R * K * op.ldu * sizeof(double), s));
-  NA_CK(launch_init_states(R, d_cols, d_cols + R, d_desc, d_ctl, s));
+  NA_CK_DRAIN(launch_init_states(R, d_cols, d_cols + R, d_desc, d_ctl, s));
   long launches = 1;
 
   const int iters = o.check_every > 0 ? o.check_every : 16;
@@ -171,8 +190,8 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   long polls = 0;
   Poll pl;
   auto poll = [&]() -> int {
-    NA_CK(cudaMemcpyAsync(&pl, d_ctl, sizeof pl, cudaMemcpyDeviceToHost, s));
-    NA_CK(cudaStreamSynchronize(s));
+    NA_CK_DRAIN(cudaMemcpyAsync(&pl, d_ctl, sizeof pl, cudaMemcpyDeviceToHost, s));
+    NA_CK_DRAIN(cudaStreamSynchronize(s));
     ++polls;
     if (pl.error) return fail_msg(SYLV_E_TIMEOUT, "a bounded device-side wait expired");
     return SYLV_OK;
@@ -180,8 +199,8 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
   int rc = SYLV_OK;
   bool gave_up = false;
   while (true) {
-    NA_CK(launch_update_x<T>(K, nslots, TILE_PX, d_desc, d_cta, s));
-    NA_CK(launch_residual<T>(K, op.m, op.E, nslots, TILE_PX, d_desc, d_cta, d_ctl, s));
+    NA_CK_DRAIN(launch_update_x<T>(K, nslots, TILE_PX, d_desc, d_cta, s));
+    NA_CK_DRAIN(launch_residual<T>(K, op.m, op.E, nslots, TILE_PX, d_desc, d_cta, d_ctl, s));
     launches += 2;
     if ((rc = poll()) != SYLV_OK) return rc;
     if (pl.n_unfinished == 0u) break;
@@ -191,8 +210,9 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
         break;
       }
       for (int it = 0; it < iters; ++it) {
-        NA_CK(launch_inner_apply<T>(K, op.m, op.E, 0, nslots, TILE_PX, d_desc, d_cta, d_ctl, s));
-        NA_CK(launch_inner_update<T>(K, op.m, op.E, 0, nslots, TILE_PX, d_desc, d_cta, d_ctl,
+        NA_CK_DRAIN(launch_inner_apply<T>(K, op.m, op.E, 0, nslots, TILE_PX, d_desc, d_cta,
+                                          d_ctl, s));
+        NA_CK_DRAIN(launch_inner_update<T>(K, op.m, op.E, 0, nslots, TILE_PX, d_desc, d_cta, d_ctl,
                                      s));
       }
       launches += 2L * iters;
@@ -204,8 +224,8 @@ int solve_in_scratch(const OpData& op, int device, const double* B, double* X, i
     }
   }
   ColState st[RMAX];
-  NA_CK(cudaMemcpyAsync(st, sd.st, R * sizeof(ColState), cudaMemcpyDeviceToHost, s));
-  NA_CK(cudaStreamSynchronize(s));
+  NA_CK_DRAIN(cudaMemcpyAsync(st, sd.st, R * sizeof(ColState), cudaMemcpyDeviceToHost, s));
+  NA_CK_DRAIN(cudaStreamSynchronize(s));
   sylv_info inf;
   std::memset(&inf, 0, sizeof inf);
   for (int r = 0; r < R; ++r) {

@@ -1,5 +1,9 @@
 // Iteration kernels with inner type float: the generic kernels and the bulk-copy staged ones.
+#include <cstdlib>
+#include <cstring>
+
 #include "apply_ops.cuh"
+#include "pcg_mc.cuh"
 
 namespace sylv {
 
@@ -82,6 +86,53 @@ cudaError_t update_tma(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl
 }
 
 template <int K, int M, int E>
+cudaError_t apply_mc(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl, cudaStream_t s) {
+  static bool attr = false;
+  constexpr size_t smem = tma::mc_apply_smem<K, M, E>();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tma::k_inner_apply_mc<K, M, E>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  tma::k_inner_apply_mc<K, M, E><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
+  return cudaGetLastError();
+}
+
+template <int K, int M>
+cudaError_t update_mc(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl, cudaStream_t s) {
+  static bool attr = false;
+  constexpr size_t smem = tma::mc_update_smem<K>();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tma::k_inner_update_mc<K, M>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  tma::k_inner_update_mc<K, M><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
+  return cudaGetLastError();
+}
+
+template <int K, int M, int E>
+int mc_occupancy(int kind) {
+  int nb = 0;
+  if (kind == 0) {
+    constexpr size_t smem = tma::mc_apply_smem<K, M, E>();
+    cudaFuncSetAttribute(tma::k_inner_apply_mc<K, M, E>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_apply_mc<K, M, E>,
+                                                  tma::WS_THREADS, smem);
+  } else {
+    constexpr size_t smem = tma::mc_update_smem<K>();
+    cudaFuncSetAttribute(tma::k_inner_update_mc<K, M>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tma::k_inner_update_mc<K, M>,
+                                                  tma::WS_THREADS, smem);
+  }
+  return nb < 1 ? 1 : nb;
+}
+
+template <int K, int M, int E>
 int tma_occupancy(int kind) {
   int nb = 0;
   if (kind == 0) {
@@ -130,14 +181,18 @@ int residual_tma_occupancy() {
   return nb < 1 ? 1 : nb;
 }
 
-template <int K, int M, int E, bool OPS>
+// variant 0: one ring of whole stages (k_apply_tma); 1: operator slots once per tile and a
+// ring of x rows (k_apply_tma_ops); 2: the multi-column kernel (k_apply_mc)
+template <int K, int M, int E, int V>
 cudaError_t apply_x_tma_impl(const OpData& op, const float* X, float* Y, int R, unsigned int* err,
                              cudaStream_t s) {
   static bool attr = false;
   static int grid = 0;
-  const auto kern = OPS ? tma::k_apply_tma_ops<K, M, E> : tma::k_apply_tma<K, M, E>;
-  const size_t smem = OPS ? (size_t)tma::ApplyXOpsLayout<K, M, E>::SMEM
-                          : (size_t)tma::NST_X * tma::ApplyXLayout<K, M, E>::STAGE_BYTES;
+  const auto kern = V == 2 ? tma::k_apply_mc<K, M, E>
+                           : (V == 1 ? tma::k_apply_tma_ops<K, M, E> : tma::k_apply_tma<K, M, E>);
+  const size_t smem = V == 2 ? tma::mc_applyx_smem<K, M, E>()
+                             : (V == 1 ? (size_t)tma::ApplyXOpsLayout<K, M, E>::SMEM
+                                       : (size_t)tma::NST_X * tma::ApplyXLayout<K, M, E>::STAGE_BYTES);
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -155,12 +210,19 @@ cudaError_t apply_x_tma_impl(const OpData& op, const float* X, float* Y, int R, 
   return cudaGetLastError();
 }
 
-// One or two columns: one ring of whole stages; three or more: operator rows once per tile.
+// One or two columns: one ring of whole stages; three or more: the multi-column kernel
+// (SYLV_APPLY_MANY=ops selects the kernel with operator slots and a ring of x rows instead).
+const int g_apply_many = [] {
+  const char* v = std::getenv("SYLV_APPLY_MANY");
+  return (v && std::strcmp(v, "ops") == 0) ? 1 : 2;
+}();
+
 template <int K, int M, int E>
 cudaError_t apply_x_tma(const OpData& op, const float* X, float* Y, int R, unsigned int* err,
                         cudaStream_t s) {
-  return R >= 3 ? apply_x_tma_impl<K, M, E, true>(op, X, Y, R, err, s)
-                : apply_x_tma_impl<K, M, E, false>(op, X, Y, R, err, s);
+  if (R < 3) return apply_x_tma_impl<K, M, E, 0>(op, X, Y, R, err, s);
+  return g_apply_many == 1 ? apply_x_tma_impl<K, M, E, 1>(op, X, Y, R, err, s)
+                           : apply_x_tma_impl<K, M, E, 2>(op, X, Y, R, err, s);
 }
 
 }  // namespace
@@ -181,12 +243,17 @@ cudaError_t launch_apply_staged(const OpData& op, const float* X, float* Y, int 
   return cudaErrorNotSupported;
 }
 
-#define SYLV_TMA_APPLY_(K_, M_, E_) \
-  if (k == K_ && m == M_ && e == E_) return apply_tma<K_, M_, E_>(ncta, d, c, ctl, variant - 1, s);
-#define SYLV_TMA_UPDATE_(K_, M_, E_) \
-  if (k == K_ && m == M_ && e == E_) return update_tma<K_, M_>(ncta, d, c, ctl, variant - 1, s);
-#define SYLV_TMA_OCC_(K_, M_, E_) \
-  if (k == K_ && m == M_ && e == E_) return tma_occupancy<K_, M_, E_>(kind);
+#define SYLV_TMA_APPLY_(K_, M_, E_)                                              \
+  if (k == K_ && m == M_ && e == E_)                                             \
+    return variant == 4 ? apply_mc<K_, M_, E_>(ncta, d, c, ctl, s)               \
+                        : apply_tma<K_, M_, E_>(ncta, d, c, ctl, variant - 1, s);
+#define SYLV_TMA_UPDATE_(K_, M_, E_)                                             \
+  if (k == K_ && m == M_ && e == E_)                                             \
+    return variant == 4 ? update_mc<K_, M_>(ncta, d, c, ctl, s)                  \
+                        : update_tma<K_, M_>(ncta, d, c, ctl, variant - 1, s);
+#define SYLV_TMA_OCC_(K_, M_, E_)                                                \
+  if (k == K_ && m == M_ && e == E_)                                             \
+    return variant == 2 ? mc_occupancy<K_, M_, E_>(kind) : tma_occupancy<K_, M_, E_>(kind);
 #define SYLV_TMA_RESID_(K_, M_, E_) \
   if (k == K_ && m == M_ && e == E_) return residual_tma<K_, M_, E_>(ncta, d, c, ctl, s);
 #define SYLV_TMA_RESID_OCC_(K_, M_, E_) \
@@ -204,7 +271,7 @@ cudaError_t launch_inner_apply<float>(int k, int m, int e, int variant, int ncta
                                       const SysDesc* d, const CtaRef* c, Control* ctl,
                                       cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  if (variant >= 1 && variant <= 3) {
+  if (variant >= 1 && variant <= 4) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_APPLY_)
   }
   return launch_inner_apply_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
@@ -214,7 +281,7 @@ cudaError_t launch_inner_update<float>(int k, int m, int e, int variant, int nct
                                        const SysDesc* d, const CtaRef* c, Control* ctl,
                                        cudaStream_t s) {
   if (ncta <= 0) return cudaSuccess;
-  if (variant >= 1 && variant <= 3) {
+  if (variant >= 1 && variant <= 4) {
     SYLV_SPECIAL_SHAPES(SYLV_TMA_UPDATE_)
   }
   return launch_inner_update_impl<float>(k, m, e, ncta, block, d, c, ctl, s);

@@ -19,18 +19,25 @@ using namespace sylv;
 // errors
 // ------------------------------------------------------------------------------------------
 namespace {
-thread_local std::string g_last_error;
+// Text of the last error of this thread, in a fixed buffer: setting it never allocates (the
+// allocation-free solve reports its errors through it too); longer messages are cut.
+constexpr size_t LAST_ERROR_BYTES = 512;
+thread_local char g_last_error[LAST_ERROR_BYTES] = "";
 
-int fail(int code, const std::string& msg) {
-  g_last_error = msg;
+void store_error(const char* msg) {
+  std::snprintf(g_last_error, LAST_ERROR_BYTES, "%s", msg ? msg : "");
+}
+
+int fail(int code, const char* msg) {
+  store_error(msg);
   return code;
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
-  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
-                  ")";
+  std::snprintf(g_last_error, LAST_ERROR_BYTES, "%s: %s (%s)", what, cudaGetErrorName(e),
+                cudaGetErrorString(e));
   (void)cudaGetLastError();  // clear a sticky-free error so later calls are not confused
-  return fail(e == cudaErrorMemoryAllocation ? SYLV_E_NOMEM : SYLV_E_CUDA, m);
+  return e == cudaErrorMemoryAllocation ? SYLV_E_NOMEM : SYLV_E_CUDA;
 }
 
 #define CK(call)                                          \
@@ -74,7 +81,9 @@ struct Group {
   std::vector<int> sys;     // systems of the group
   int block = TILE_PX;      // pixels per tile = threads per CTA
   int mult = 1;             // CTA slots = mult x resident CTAs
-  int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (1: staged)
+  int va = 0, vu = 0;       // kernel variant of inner_apply / inner_update (0: direct, 1: staged
+                            // per (tile, column) unit, 2: multi-column, a tile's operator data
+                            // staged once for all its columns)
   int csum = 0;             // staged pair with consumer-side sums (variants 2/3, chunks end
                             // with launch_inner_close): both staged and at most 2 columns
   int rs_ok = 0;             // the staged FP64 residual serves this group's shape and tiles
@@ -325,6 +334,8 @@ int rebalance(Plan& P, bool want_inner, cudaStream_t s) {
   return SYLV_OK;
 }
 
+const char* const kVariantName[3] = {"direct", "staged", "multi-column"};
+
 struct TuneChoice {
   int block, mult, va, vu;
   float ms;
@@ -364,12 +375,14 @@ int time_inner(Plan& P, Group& g, int kind, int reps, float* ms_out) {
                          cudaMemcpyHostToDevice, s));
     }
     CK(cudaEventRecord(P.evr0, s));
+    // consumer-side pair: launch variant 2 (the column states as stored, no sums at the start)
+    const int v = g.csum ? 2 : ((kind == 0 ? g.va : g.vu) == 2 ? 4 : (kind == 0 ? g.va : g.vu));
     if (kind == 0)
-      CK(launch_inner_apply<T>(g.k, g.m, g.e, g.csum ? 2 : g.va, g.ncta[0], g.block, P.d_desc,
-                               g.d_ctas[0], P.d_ctl, s));
+      CK(launch_inner_apply<T>(g.k, g.m, g.e, v, g.ncta[0], g.block, P.d_desc, g.d_ctas[0],
+                               P.d_ctl, s));
     else
-      CK(launch_inner_update<T>(g.k, g.m, g.e, g.csum ? 2 : g.vu, g.ncta[1], g.block, P.d_desc,
-                                g.d_ctas[1], P.d_ctl, s));
+      CK(launch_inner_update<T>(g.k, g.m, g.e, v, g.ncta[1], g.block, P.d_desc, g.d_ctas[1],
+                                P.d_ctl, s));
     CK(cudaEventRecord(P.evr1, s));
     CK(cudaStreamSynchronize(s));
     float ms = 0;
@@ -395,6 +408,20 @@ int tune_group(Plan& P, Group& g) {
   }
   int lg = 0;
   while ((int64_t(1) << (lg + 1)) <= ntot) ++lg;
+  const TuneChoice dflt{TILE_PX, 1, 0, can_tma ? 1 : 0, 0.f};
+  // SYLV_TUNE_FORCE="tile,mult,apply_variant,update_variant" pins a configuration (used to
+  // profile exactly the configuration a timed run chose, and by tests of one kernel variant);
+  // it takes precedence over the cache of earlier choices
+  if (const char* f = std::getenv("SYLV_TUNE_FORCE")) {
+    TuneChoice c = dflt;
+    if (std::sscanf(f, "%d,%d,%d,%d", &c.block, &c.mult, &c.va, &c.vu) == 4 &&
+        (c.block == 128 || c.block == TILE_PX) && c.mult >= 1 && c.mult <= 4) {
+      if (!can_tma || c.block != TILE_PX) c.va = c.vu = 0;
+      c.va = std::min(std::max(c.va, 0), 2);
+      c.vu = std::min(std::max(c.vu, 0), 2);
+      return configure_group<T>(P, g, c.block, c.mult, c.va, c.vu);
+    }
+  }
   const std::vector<int> key = {P.device, (int)dbl, g.k, g.m, g.e, g.has_w, rmax, lg,
                                 (int)g.sys.size()};
   {
@@ -403,17 +430,6 @@ int tune_group(Plan& P, Group& g) {
     if (it != g_tune.end()) {
       const TuneChoice& c = it->second;
       return configure_group<T>(P, g, c.block, c.mult, c.va, c.vu);
-    }
-  }
-  const TuneChoice dflt{TILE_PX, 1, 0, can_tma ? 1 : 0, 0.f};
-  // SYLV_TUNE_FORCE="tile,mult,apply_variant,update_variant" pins a configuration (used to
-  // profile exactly the configuration a timed run chose)
-  if (const char* f = std::getenv("SYLV_TUNE_FORCE")) {
-    TuneChoice c = dflt;
-    if (std::sscanf(f, "%d,%d,%d,%d", &c.block, &c.mult, &c.va, &c.vu) == 4 &&
-        (c.block == 128 || c.block == TILE_PX) && c.mult >= 1 && c.mult <= 4) {
-      if (!can_tma || c.block != TILE_PX) c.va = c.vu = 0;
-      return configure_group<T>(P, g, c.block, c.mult, c.va ? 1 : 0, c.vu ? 1 : 0);
     }
   }
   if (!g_autotune) return configure_group<T>(P, g, dflt.block, dflt.mult, dflt.va, dflt.vu);
@@ -436,6 +452,11 @@ int tune_group(Plan& P, Group& g) {
       cands.push_back({TILE_PX, mult, 1, 0, 0.f});
       cands.push_back({TILE_PX, mult, 0, 1, 0.f});
       cands.push_back({TILE_PX, mult, 1, 1, 0.f});
+      if (rmax >= 2) {   // multi-column kernels: operator data once per tile for all columns
+        cands.push_back({TILE_PX, mult, 2, 2, 0.f});
+        cands.push_back({TILE_PX, mult, 2, 1, 0.f});
+        cands.push_back({TILE_PX, mult, 1, 2, 0.f});
+      }
     }
   }
   TuneChoice best = dflt;
@@ -462,8 +483,7 @@ int tune_group(Plan& P, Group& g) {
                    "sylv autotune: %s k=%d m=%d E=%d systems=%zu nrhs<=%d n=%lld -> tile %d, "
                    "slots x%d, apply %s, update %s (%.3f ms per iteration)\n",
                    dbl ? "fp64" : "fp32", g.k, g.m, g.e, g.sys.size(), rmax, (long long)ntot,
-                   best.block, best.mult, best.va ? "staged" : "direct",
-                   best.vu ? "staged" : "direct", best.ms);
+                   best.block, best.mult, kVariantName[best.va], kVariantName[best.vu], best.ms);
   }
   return configure_group<T>(P, g, best.block, best.mult, best.va, best.vu);
 }
@@ -570,22 +590,29 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
   return SYLV_OK;
 }
 
+// Launch variant of the group's operator (kind 0) or update (kind 1) kernel at iteration `it`
+// of a chunk (see launch_inner_apply): consumer-side sums 2/3, multi-column 4, else 0/1.
+int kernel_variant(const Group& g, int kind, int it) {
+  if (g.csum) return kind == 0 ? (it == 0 ? 2 : 3) : 3;
+  const int v = kind == 0 ? g.va : g.vu;
+  return v == 2 ? 4 : v;
+}
+
 // Iteration `it` of a chunk of `iters`.  Groups with consumer-side sums: the chunk's first
 // operator kernel reads the stored states, every other kernel first sums its predecessor's
 // partials, and the chunk ends with the state change of its last update (launch_inner_close).
 template <typename T>
 int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent_t e_end,
                            bool capture_events, int it, int iters) {
-  for (auto& g : P.groups) {
-    const int va = g.csum ? (it == 0 ? 2 : 3) : g.va;
-    CK(launch_inner_apply<T>(g.k, g.m, g.e, va, g.ncta[0], g.block, P.d_desc, g.d_ctas[0], P.d_ctl, s));
-  }
+  for (auto& g : P.groups)
+    CK(launch_inner_apply<T>(g.k, g.m, g.e, kernel_variant(g, 0, it), g.ncta[0], g.block,
+                             P.d_desc, g.d_ctas[0], P.d_ctl, s));
   if (e_mid)
     CK(capture_events ? cudaEventRecordWithFlags(e_mid, s, cudaEventRecordExternal)
                       : cudaEventRecord(e_mid, s));
   for (auto& g : P.groups)
-    CK(launch_inner_update<T>(g.k, g.m, g.e, g.csum ? 3 : g.vu, g.ncta[1], g.block, P.d_desc,
-                              g.d_ctas[1], P.d_ctl, s));
+    CK(launch_inner_update<T>(g.k, g.m, g.e, kernel_variant(g, 1, it), g.ncta[1], g.block,
+                              P.d_desc, g.d_ctas[1], P.d_ctl, s));
   if (it == iters - 1)
     for (auto& g : P.groups)
       if (g.csum) CK(launch_inner_close(g.ncta[1], P.d_desc, g.d_ctas[1], P.d_ctl, s));
@@ -867,8 +894,8 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
       worst = inf.status;
   }
   if (worst == SYLV_E_NOT_CONVERGED)
-    g_last_error = gave_up ? "solve stopped: poll limit reached" : "tolerance not reached";
-  if (worst == SYLV_E_BREAKDOWN) g_last_error = "CG breakdown (non-positive or non-finite scalar)";
+    store_error(gave_up ? "solve stopped: poll limit reached" : "tolerance not reached");
+  if (worst == SYLV_E_BREAKDOWN) store_error("CG breakdown (non-positive or non-finite scalar)");
   return worst;
 }
 
@@ -895,7 +922,7 @@ int handle_view(sylv_handle h, OpData* op, int* device) {
   *device = h->device;
   return SYLV_OK;
 }
-void set_last_error(const char* msg) { g_last_error = msg; }
+void set_last_error(const char* msg) { store_error(msg); }
 }  // namespace sylv
 
 // ------------------------------------------------------------------------------------------
@@ -933,7 +960,7 @@ const char* sylv_strerror(int code) {
   }
 }
 
-const char* sylv_last_error(void) { return g_last_error.c_str(); }
+const char* sylv_last_error(void) { return g_last_error; }
 
 static void free_handle(sylv_ctx* h) {
   if (!h) return;
@@ -1486,7 +1513,7 @@ int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const
   tot.launches += 1;
   tot.status = worst;
   if (info) *info = tot;
-  if (worst != SYLV_OK) g_last_error = "a probe solve did not reach the tolerance";
+  if (worst != SYLV_OK) store_error("a probe solve did not reach the tolerance");
   return worst;
 }
 

@@ -27,6 +27,7 @@ from .problems import (  # noqa: F401
     make_problem,
     config_problem,
     batch_problems,
+    batch_shapes,
     separable_problem,
     igmrf_problem,
     rademacher_probes,

@@ -219,17 +219,30 @@ def rademacher_probes(count: int, k: int, n: int, seed: int) -> np.ndarray:
     return rng.integers(0, 2, size=(count, k, n)).astype(np.float64) * 2.0 - 1.0
 
 
-def batch_problems(count=64, side_range=(128, 1024), *, seed=None) -> List[Problem]:
-    """Batched workload: ``count`` independent periodic lattices of log-uniform side, k in
-    {3,4,5,6} uniform, m = k + 2, own kappa (log-spaced 0.01..1, permuted), beta and noise."""
+def _batch_draws(count, side_range, seed):
     seed = CONFIG_SEED_BASE + 3 if seed is None else seed
     rng = np.random.Generator(np.random.PCG64(seed))
     lo, hi = np.log(side_range[0]), np.log(side_range[1])
     sides = np.round(np.exp(rng.uniform(lo, hi, size=count))).astype(int)
     ks = rng.integers(3, 7, size=count)
     sub = rng.integers(0, 2**62, size=count)
+    return sides, ks, sub
+
+
+def batch_shapes(count=64, side_range=(128, 1024), *, seed=None):
+    """(side, k) of each system of ``batch_problems`` (same draws), without building them."""
+    sides, ks, _ = _batch_draws(count, side_range, seed)
+    return [(int(a), int(b)) for a, b in zip(sides, ks)]
+
+
+def batch_problems(count=64, side_range=(128, 1024), *, seed=None,
+                   indices=None) -> List[Problem]:
+    """Batched workload: ``count`` independent periodic lattices of log-uniform side, k in
+    {3,4,5,6} uniform, m = k + 2, own kappa (log-spaced 0.01..1, permuted), beta and noise.
+    ``indices``: build only these members (the same problems as in the whole batch)."""
+    sides, ks, sub = _batch_draws(count, side_range, seed)
     out = []
-    for b in range(count):
+    for b in (range(count) if indices is None else indices):
         k = int(ks[b])
         m = k + 2
         g = _grid("lattice", int(sides[b]), int(sides[b]))

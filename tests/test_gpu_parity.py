@@ -77,7 +77,7 @@ def test_apply_parity(kind, H, W, k, m, pad):
     op.close()
 
 
-@pytest.mark.parametrize("nrhs", [3, 8])
+@pytest.mark.parametrize("nrhs", [3, 8, 16])
 def test_staged_apply_many_columns(nrhs):
     """The staged stand-alone apply stages a tile's operator rows once for all its columns
     (more columns than ring stages): every column against the oracle, within the FP32 bound."""
@@ -174,6 +174,68 @@ def test_staged_residual_parity(nrhs, monkeypatch):
         assert info["code"] == 0
         assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
         op.close()
+
+
+MC_CASES = [
+    ("sphere", 16, 64, 6, 9, 5, 1),    # whole tiles: the staged FP64 residual is skipped (R > 2)
+    ("sphere", 20, 30, 6, 9, 8, 1),    # ragged last tile
+    ("lattice", 24, 24, 4, 7, 6, 1),
+    ("lattice", 21, 19, 3, 5, 7, 1),
+    ("sphere", 18, 40, 5, 7, 8, 0),    # no preconditioner: empty operator slots in the update
+    ("sphere", 16, 32, 6, 8, 2, 1),    # two columns through the multi-column pair as well
+]
+
+
+@pytest.mark.parametrize("kind,H,W,k,m,nrhs,precond", MC_CASES)
+def test_multi_column_solve_parity(kind, H, W, k, m, nrhs, precond, monkeypatch):
+    """The multi-column inner kernels (a tile's operator data staged once and kept in
+    registers for all its columns; pixel block formed from the noise maps) pinned by the
+    tuner override: every right-hand side against the oracle's direct solve (mixed, 1e-6),
+    with a caller leading dimension above n."""
+    from paper_2204_08057_gb300 import binding as Bn
+    monkeypatch.setenv("SYLV_TUNE_FORCE", "256,1,2,2")
+    p = small_problem(kind, H, W, k, m, seed=90 + nrhs, nrhs=nrhs)
+    ld = p.n + 7
+    op = operator_for(p, ld=ld)
+    Xo, b = oracle_solution(p)
+    pc = Bn.SYLV_PRECOND_BLOCK_JACOBI if precond else Bn.SYLV_PRECOND_NONE
+    X, info = op.solve(device_batch(b, ld), tol=1e-11, precision=1, precond=pc,
+                       maxit=100000)
+    assert info["code"] == 0, info
+    assert (info["apply_staged"], info["update_staged"]) == (2, 2), info
+    X = X.cpu().numpy()[:, :, :p.n]
+    for r in range(nrhs):
+        assert relerr(X[r], Xo[r]) <= 1e-6, r
+    # a warm start (the first inner iteration skips p and q) from a perturbed solution
+    X0 = device_batch(Xo + 1e-3, ld)
+    X, info = op.solve(device_batch(b, ld), X0=X0, tol=1e-11, precision=1, precond=pc,
+                       maxit=100000)
+    assert info["code"] == 0, info
+    assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+    op.close()
+
+
+def test_multi_column_igmrf_shape(monkeypatch):
+    """The multi-column pair on the intrinsic GMRF shape (L^2: 12 off-diagonals per row) with
+    the printed App. B mixing, four right-hand sides, against the oracle's direct solve."""
+    monkeypatch.setenv("SYLV_TUNE_FORCE", "256,1,2,2")
+    g = synth.latlong_sphere(16, 32)
+    rng = np.random.default_rng(8)
+    A = synth.PLANCK_A_PRINTED
+    nu_pix = np.exp(0.3 * rng.standard_normal(g.n))
+    D = (synth.PLANCK_T_PRINTED * 1e-6)[:, None] * nu_pix[None, :]
+    Xt = rng.standard_normal((4, 4, g.n))
+    Y = np.stack([A @ x + rng.standard_normal((9, g.n)) / np.sqrt(D) for x in Xt])
+    p = synth.Problem("paper_sphere16x32", g, 4, 9, np.array([2.0, 0.5, 1.0, 3.0]),
+                      np.full(4, 0.3), synth.PLANCK_NU, np.zeros(4), D, Y, Xt[0], 1e-8, {},
+                      A=A.copy(), prior="igmrf")
+    op = operator_for(p)
+    Xo, b = oracle_solution(p)
+    X, info = op.solve(device_batch(b, p.n), tol=1e-10, precision=1)
+    assert info["code"] == 0, info
+    assert (info["apply_staged"], info["update_staged"]) == (2, 2), info
+    assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+    op.close()
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -319,6 +381,42 @@ def test_autograd_function_fd():
                               p.kappa, p.nu, p.beta, p.Yobs[0], h=1e-6)
     for got, ref in zip((tau.grad, kappa.grad, beta.grad), fd):
         assert np.allclose(got.numpy(), ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+def test_autograd_reuses_one_handle_across_parameters():
+    """Two forwards at different parameters and their backwards in reverse order: each result
+    and gradient against the oracle at its own parameters, with one sylv_create in total (the
+    handle moves between parameter values by sylv_set_params)."""
+    import torch
+    from paper_2204_08057_gb300 import binding as Bn
+    from paper_2204_08057_gb300.autograd import SylvProblem, sylv_solve_differentiable
+    from oracle import gradient
+    p = small_problem("sphere", 8, 10, 3, 5, seed=17)
+    prob = SylvProblem(rowptr=p.graph.rowptr, col=p.graph.col, val=p.graph.val, D=p.D, nu=p.nu)
+    Y = device_batch(p.Yobs, p.n)[0]
+    Xt = torch.as_tensor(p.X_true, device="cuda")
+    L = oracle_L(p)
+    thetas = [(p.tau, p.kappa, p.beta), (p.tau * 1.3, p.kappa * 0.8, p.beta + 0.1)]
+    made = Bn.calls["sylv_create"]
+    leaves, losses = [], []
+    for tau0, kappa0, beta0 in thetas:
+        t = [torch.tensor(v, dtype=torch.float64, requires_grad=True)
+             for v in (tau0, kappa0, beta0)]
+        X = sylv_solve_differentiable(Y, *t, prob, tol=1e-12, precision=0)
+        Xo = gradient.posterior_mean(L, p.D, tau0, kappa0, p.nu, beta0, p.Yobs[0])[0][0]
+        assert relerr(X.detach().cpu().numpy()[:, :p.n], Xo) <= 1e-8
+        leaves.append(t)
+        losses.append(((X - Xt) ** 2).sum())
+    for q in (1, 0):           # the second forward's backward first, then the first's
+        losses[q].backward()
+        tau0, kappa0, beta0 = thetas[q]
+        Xo = gradient.posterior_mean(L, p.D, tau0, kappa0, p.nu, beta0, p.Yobs[0])[0][0]
+        ga = gradient.adjoint_gradient(L, p.D, tau0, kappa0, p.nu, beta0, p.Yobs[0], Xo,
+                                       2 * (Xo - p.X_true))
+        for got, ref in zip((x.grad for x in leaves[q]), ga[:3]):
+            assert np.abs(got.numpy() - ref).max() <= 1e-7 * np.abs(ref).max(), (q, got, ref)
+    assert Bn.calls["sylv_create"] - made == 1
+    prob.close()
 
 
 def test_single_pixel_and_isolated_pixels():
