@@ -54,6 +54,10 @@ def parse():
                     help="N steps of parameter learning on the 512 x 1024 workload, warm and cold")
     ap.add_argument("--variance", type=int, default=0, metavar="S",
                     help="posterior variances of the workload from S Rademacher probes")
+    ap.add_argument("--variance-probing", type=int, default=0, metavar="P",
+                    help="posterior variances of the workload by probing with a distance-(P-1) "
+                         "colouring (P^2 k probes), with the change against P/2 as the error "
+                         "estimate")
     ap.add_argument("--separable", action="store_true",
                     help="separable special case of the workload: block-Lanczos Sylvester "
                          "solver (Algorithms 4 and 5) against the preconditioned CG")
@@ -840,6 +844,34 @@ def bytes_lanczos_b(k, s=4):
     return (3 * k + 1) * s
 
 
+class DeviceMemory:
+    """Device memory the library allocated between marks: the drop in cudaMemGetInfo's free
+    bytes minus the growth of torch's reserved pool over the same interval."""
+
+    def __init__(self):
+        import torch
+        torch.cuda.synchronize()
+        self.last = self._now()
+        self.marks = {}
+
+    @staticmethod
+    def _now():
+        import torch
+        free, _ = torch.cuda.mem_get_info()
+        return free, torch.cuda.memory_reserved()
+
+    def mark(self, name):
+        import torch
+        torch.cuda.synchronize()
+        now = self._now()
+        if name is not None:
+            self.marks[name] = int((self.last[0] - now[0]) - (now[1] - self.last[1]))
+        self.last = now
+
+    def get(self, name):
+        return self.marks.get(name)
+
+
 def run_sylvester(args):
     """Separable special case of the workload (noise d_ci = t_c nu_i, one prior shape): time
     to relres 1e-8 of the block-Lanczos Sylvester solver (mixed and FP64) against the
@@ -852,7 +884,9 @@ def run_sylvester(args):
     _build.build()
     torch.cuda.set_device(0)
     p = synth.separable_problem(args.config, scale=args.scale if args.scale > 1 else None)
+    mem = DeviceMemory()
     op = make_operator(p)
+    mem.mark("handle")
     B = op.rhs(torch.from_numpy(p.Yobs).cuda())
     stream = torch.cuda.current_stream()
     E = int(np.max(np.diff(p.graph.rowptr))) - 1
@@ -865,6 +899,12 @@ def run_sylvester(args):
 
     def cg(prec):
         return op.solve(B, precision=prec, **kw)
+
+    mem.mark(None)
+    cg(1)
+    mem.mark("pcg_mixed_workspace")
+    lz(1)
+    mem.mark("lanczos_mixed_workspace")
 
     def cg_plain(prec):
         from paper_2204_08057_gb300 import binding as _B
@@ -901,6 +941,33 @@ def run_sylvester(args):
         return {"ms": ms, "iterations": inf["iterations"], "outer": inf["outer"],
                 "relres": inf["relres"]}
 
+    # bounded memory: a fresh handle whose basis budget holds 48 blocks (runs restart there)
+    os.environ["SYLV_LZ_BASIS_MB"] = str(int(np.ceil(48 * p.k * p.n * 4 / 2 ** 20)) + 1)
+    op_b = make_operator(p)
+    mem.mark(None)
+    op_b.solve_sylvester(B, precision=1, inner_tol=1e-5, **kw)
+    mem.mark("lanczos_mixed_workspace_bounded")
+    ms_lzb, (_, info_lzb) = _timed(stream, lambda: op_b.solve_sylvester(
+        B, precision=1, inner_tol=1e-5, **kw), args.steps)
+    del os.environ["SYLV_LZ_BASIS_MB"]
+    op_b.close()
+    block_bytes = p.k * p.n * 4
+    steps_per_run = -(-info_lz["iterations"] // max(info_lz["outer"], 1))
+    memory = {
+        "handle_bytes": mem.get("handle"),
+        "pcg_mixed_workspace_bytes": mem.get("pcg_mixed_workspace"),
+        "lanczos_mixed_workspace_bytes": mem.get("lanczos_mixed_workspace"),
+        "lanczos_basis_block_bytes": block_bytes,
+        "lanczos_steps_per_run": steps_per_run,
+        "lanczos_basis_bytes_used": steps_per_run * block_bytes,
+        "bounded": {"workspace_bytes": mem.get("lanczos_mixed_workspace_bounded"),
+                    "basis_blocks": 48, "ms": ms_lzb, "iterations": info_lzb["iterations"],
+                    "runs": info_lzb["outer"]},
+        "how": "cudaMemGetInfo deltas around each first call, minus what torch's allocator "
+               "reserved meanwhile; the basis is allocated to its capacity (up to 384 blocks "
+               "or 60 % of free memory) at the first Lanczos call",
+    }
+
     line = _base_line(args, "solve time to relres 1e-8, separable special case "
                             "(block-Lanczos Sylvester solver, mixed)", ms_lz, "ms",
                       {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "nrhs": 1,
@@ -916,6 +983,7 @@ def run_sylvester(args):
         "lanczos_time_share_of_cg": {"mixed": ms_lz / ms_cgp, "fp64": ms_lz64 / ms_cgp64,
                                      "note": "Sec. 4 compares the Sylvester method with CG "
                                              "applied directly to the Kronecker system"},
+        "memory": memory,
         "speedup_vs_pcg_mixed": ms_cg / ms_lz, "speedup_vs_pcg_fp64": ms_cg64 / ms_lz,
         "relerr_lanczos_vs_pcg": rel,
         "kernel_ms_per_solve": {"pass_a": info_prof["ms_apply"], "pass_b": info_prof["ms_update"],
@@ -1049,6 +1117,55 @@ def run_variance(args):
     op.close()
 
 
+def run_variance_probing(args):
+    """Posterior variances diag(G^{-1}) of the 1024 x 2048 workload by probing
+    (sylv_variance_probing: one 0/1 probe per colour and source, made on the device, solved 16
+    at a time): colourings with P and P/2 colours per side; the pixel-wise change between the
+    two estimates is the error estimate of the coarser one and bounds that of the finer one
+    from above when the couplings decay with distance."""
+    import torch
+    import synth
+    from paper_2204_08057_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(0)
+    p = synth.config_problem(args.config, scale=args.scale if args.scale > 1 else None)
+    op = make_operator(p)
+    P = int(args.variance_probing)
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=1e-8, precision=1)
+    col_f = synth.grid_colouring(p.graph, P)
+    col_c = synth.grid_colouring(p.graph, max(P // 2, 1))
+    op.variance_probing(col_c, max(P // 2, 1) ** 2, **kw)          # warm-up (plans, tuner)
+    clocks = ClockSampler(0) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.5)
+    ms, (var, info) = _timed(stream, lambda: op.variance_probing(col_f, P * P, **kw), 1)
+    clk = clocks.stop() if clocks else None
+    ms_c, (var_c, info_c) = _timed(stream, lambda: op.variance_probing(col_c, max(P // 2, 1) ** 2,
+                                                                       **kw), 1)
+    assert info["code"] == 0 and info_c["code"] == 0, (info, info_c)
+    v, vc = var[:, :p.n], var_c[:, :p.n]
+    rel = (v - vc).abs() / v.abs()
+    nprobe = P * P * p.k
+    line = _base_line(args, "posterior variances diag(G^-1) by probing with a distance colouring "
+                            "(%d probes, solves to relres 1e-8, 16 at a time)" % nprobe, ms, "ms",
+                      {"workload": p.name, "n": p.n, "k": p.k, "m": p.m, "colours": P * P,
+                       "probes": nprobe, "tol": 1e-8, "precision": "mixed",
+                       "l2": "inputs larger than L2"})
+    line.update({"ms_per_probe": ms / nprobe, "iterations_max": info["iterations"],
+                 "variance_range": [float(v.min()), float(v.max())],
+                 "all_positive": bool((v > 0).all()),
+                 "error_estimate": {"max_rel_change_vs_half": float(rel.max()),
+                                    "median_rel_change_vs_half": float(rel.median()),
+                                    "coarse_colours": max(P // 2, 1) ** 2,
+                                    "coarse_ms": ms_c,
+                                    "per_source_max": [float(x) for x in rel.max(dim=1).values]},
+                 "gpu_launches": info["launches"], "clocks": clk})
+    print(json.dumps(line), flush=True)
+    op.close()
+
+
 def run_learn(args):
     """Parameter learning on the 512 x 1024 sphere (k = 4, m = 7): N gradient steps over
     (log tau, log kappa, beta) on ||X - X_true||^2, each a parameter update in place, the
@@ -1112,6 +1229,9 @@ def main():
         return
     if args.impl == "ours" and args.variance > 0:
         run_variance(args)
+        return
+    if args.impl == "ours" and args.variance_probing > 0:
+        run_variance_probing(args)
         return
     if args.impl == "ours" and args.paper_model:
         run_paper_model(args)

@@ -135,8 +135,10 @@ typedef struct {
                          /* right-hand side); 2 multi-column: a tile's operator data staged */
                          /* once and kept in registers for all its right-hand sides         */
   int32_t update_staged; /* update kernel, the same three variants                          */
-  int32_t residual_staged; /* 1: the FP64 residual kernel stages its streams (mixed mode,
-                              whole tiles, even ldu, 16-byte aligned X and B)              */
+  int32_t residual_staged; /* the true residual of the refinement: 0 FP64; 1 FP64, staged */
+                           /* (whole tiles, even ldu, 16-byte aligned X and B, at most two */
+                           /* right-hand sides); 2 double-float on the FP32 pipe (mixed    */
+                           /* mode, see sylv_residual); 3 double-float, staged             */
   int32_t reserved_info;   /* 0                                                          */
 } sylv_info;
 
@@ -160,6 +162,17 @@ int sylv_rhs(sylv_handle h, const double* Yobs, double* B, int nrhs, sylv_stream
  * sum_c d_ci a_c (a_c . x_i).  X, Y: device, nrhs x k x ld of float (dtype SYLV_F32) or
  * double (SYLV_F64); X and Y must not overlap.  Asynchronous on s. */
 int sylv_apply(sylv_handle h, const void* X, void* Y, int nrhs, int dtype, sylv_stream s);
+
+/* True residual R = B - G X of approximate solutions (the residual Algorithm 2 stops on,
+ * evaluated on the iterate itself as the refinement loop does each step; eq. mu*).  B, X, R:
+ * device, nrhs x k x ld FP64; R must not overlap B or X.  Computed as in the mixed-precision
+ * solve: in double-float arithmetic on the FP32 pipe (FP32 pairs; no FP64 operation) when the
+ * handle's pixel blocks, Laplacian weights and tau lie in [2^-40, 2^40] (zeros allowed), with an
+ * error below (k + E + 4) 2^-45 (|b| + |G||X|) per element (E: off-diagonals per row of the
+ * prior shape) while the pixel's X and B lie in [2^-60, 2^61); pixels outside that range, and
+ * handles outside it, are computed in FP64.  Asynchronous on s. */
+int sylv_residual(sylv_handle h, const double* B, const double* X, int nrhs, double* R,
+                  sylv_stream s);
 
 /* Solves G X = B (eq. mu*) by preconditioned conjugate gradients (Algorithm 2 with the
  * pixel-block Jacobi preconditioner) inside an FP64 iterative-refinement loop: each
@@ -235,6 +248,20 @@ int sylv_set_params(sylv_handle h, const double* tau, const double* kappa, const
  * error.  Synchronises s. */
 int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const sylv_opts* o,
                   sylv_info* info, sylv_stream s);
+
+/* Posterior variances by probing (eq. Q*; the probing method for the diagonal of a matrix
+ * inverse of Tang and Saad, 2012): given a colouring of the pixels in which two pixels of one
+ * colour are more than d steps apart on the graph of L, the probes are the 0/1 vectors of one
+ * colour in one source, ncolours * k of them, made on the device SYLV_MAX_RHS at a time and
+ * solved as sylv_variance does.  The estimate at (j, i) is the sum of the entries of G^{-1}
+ * between (j, i) and every (j, i') of the same colour: the variance plus the couplings between
+ * pixels more than d steps apart, which decay with the distance (so the error falls as d
+ * grows; comparing two distances estimates it).  Deterministic, and positive wherever those
+ * couplings are.  colour: device, n int32 values in [0, ncolours).  var: device, k x ld FP64
+ * output.  Otherwise as sylv_variance; SYLV_E_INVALID if a colour is out of range.
+ * Synchronises s. */
+int sylv_variance_probing(sylv_handle h, const int32_t* colour, int ncolours, double* var,
+                          const sylv_opts* o, sylv_info* info, sylv_stream s);
 
 /* Solves the same system through its Sylvester form (Sec. 3.3, eq. Axb-Sylv) with the block
  * Lanczos method of Algorithms 4 and 5.  Applies when the noise precision is separable,

@@ -39,7 +39,7 @@ MAX_K, MAX_M, MAX_DEGREE, MAX_RHS = 8, 16, 8, 16
 EXPORTED = ["sylv_opts_default", "sylv_create", "sylv_rhs", "sylv_apply", "sylv_solve",
             "sylv_solve_host", "sylv_solve_batched", "sylv_backward", "sylv_destroy",
             "sylv_strerror", "sylv_last_error", "sylv_solve_noalloc", "sylv_solve_sylvester",
-            "sylv_variance", "sylv_set_params"]
+            "sylv_variance", "sylv_set_params", "sylv_residual", "sylv_variance_probing"]
 
 
 class sylv_problem(ctypes.Structure):
@@ -98,6 +98,7 @@ def load(path=None):
     lib.sylv_create.argtypes = [POINTER(c_void_p), POINTER(sylv_problem), c_void_p]
     lib.sylv_rhs.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p]
     lib.sylv_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p]
+    lib.sylv_residual.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]
     lib.sylv_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_int, POINTER(sylv_opts),
                                POINTER(sylv_info), c_void_p]
     lib.sylv_solve_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int, POINTER(sylv_opts),
@@ -114,6 +115,8 @@ def load(path=None):
                                          POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
     lib.sylv_variance.argtypes = [c_void_p, c_void_p, c_int, c_void_p, POINTER(sylv_opts),
                                   POINTER(sylv_info), c_void_p]
+    lib.sylv_variance_probing.argtypes = [c_void_p, c_void_p, c_int, c_void_p,
+                                          POINTER(sylv_opts), POINTER(sylv_info), c_void_p]
     lib.sylv_set_params.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double),
                                     POINTER(c_double), POINTER(c_double), POINTER(c_double),
                                     c_void_p]
@@ -246,6 +249,16 @@ def sylv_apply(h, X, Y, nrhs, *, k, ld, n, stream=None):
            "sylv_apply")
 
 
+def sylv_residual(h, B, X, R, nrhs, *, k, ld, n, stream=None):
+    """R = B - G X (FP64 device tensors nrhs x k x ld)."""
+    import torch
+    need = ((nrhs - 1) * k + k - 1) * ld + n
+    _check(load().sylv_residual(c_void_p(h), _dev_ptr(B, torch.float64, need, "B"),
+                                _dev_ptr(X, torch.float64, need, "X"), int(nrhs),
+                                _dev_ptr(R, torch.float64, need, "R"), _stream(stream)),
+           "sylv_residual")
+
+
 def sylv_solve(h, B, X, nrhs, opts=None, *, k, ld, n, stream=None, allow=()):
     """Returns (status, sylv_info).  Raises on statuses outside SYLV_OK and ``allow``."""
     import torch
@@ -367,6 +380,21 @@ def sylv_variance(h, Z, nprobe, var, opts=None, *, k, ld, n, stream=None, allow=
     _check(code, "sylv_variance", ok=(SYLV_OK,) + tuple(allow))
     return code, info
 
+
+
+def sylv_variance_probing(h, colour, ncolours, var, opts=None, *, k, ld, n, stream=None,
+                          allow=()):
+    """Posterior variances from the probes of a pixel colouring (see sylv.h).  colour: int32
+    device tensor (n).  Returns (status, info)."""
+    import torch
+    info = sylv_info()
+    code = load().sylv_variance_probing(c_void_p(h), _dev_ptr(colour, torch.int32, n, "colour"),
+                                        int(ncolours),
+                                        _dev_ptr(var, torch.float64, (k - 1) * ld + n, "var"),
+                                        ctypes.byref(opts) if opts is not None else None,
+                                        ctypes.byref(info), _stream(stream))
+    _check(code, "sylv_variance_probing", ok=(SYLV_OK,) + tuple(allow))
+    return code, info
 
 def sylv_set_params(h, *, k, m, tau, kappa, nu=None, beta=None, A=None, stream=None):
     """New tau, kappa and mixing for an existing handle (see sylv.h)."""

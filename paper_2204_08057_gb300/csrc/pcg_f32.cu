@@ -4,6 +4,7 @@
 
 #include "apply_ops.cuh"
 #include "pcg_mc.cuh"
+#include "resid_df.cuh"
 
 namespace sylv {
 
@@ -286,6 +287,59 @@ cudaError_t launch_inner_update<float>(int k, int m, int e, int variant, int nct
   }
   return launch_inner_update_impl<float>(k, m, e, ncta, block, d, c, ctl, s);
 }
+cudaError_t launch_residual_df(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                               const CtaRef* c, Control* ctl, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+#define CALL(K, M, E) k_residual_df<K, M, E><<<ncta, block, 0, s>>>(d, c, ctl)
+  SYLV_DISPATCH_SHAPE(k, m, e)
+#undef CALL
+  return cudaGetLastError();
+}
+
+namespace {
+template <int K, int M, int E>
+size_t residual_tma_df_smem() {
+  return (size_t)tma::NSTAGE * tma::ResidLayout<K, E>::STAGE_BYTES + 2 * sizeof(DfTile<K>);
+}
+
+template <int K, int M, int E>
+cudaError_t residual_tma_df(int ncta, const SysDesc* d, const CtaRef* c, Control* ctl,
+                            cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = residual_tma_df_smem<K, M, E>();
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_residual_tma_df<K, M, E>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_residual_tma_df<K, M, E><<<ncta, tma::WS_THREADS, smem, s>>>(d, c, ctl);
+  return cudaGetLastError();
+}
+}  // namespace
+
+#define SYLV_TMA_RESID_DF_(K_, M_, E_) \
+  if (k == K_ && m == M_ && e == E_) return residual_tma_df<K_, M_, E_>(ncta, d, c, ctl, s);
+
+cudaError_t launch_residual_staged_df(int k, int m, int e, int ncta, const SysDesc* d,
+                                      const CtaRef* c, Control* ctl, cudaStream_t s) {
+  if (ncta <= 0) return cudaSuccess;
+  SYLV_SPECIAL_SHAPES(SYLV_TMA_RESID_DF_)
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_residual_out(const OpData& op, const double* B, const double* X, int R,
+                                double* Rout, int use_df, cudaStream_t s) {
+  const int k = op.k, m = op.m, e = op.E;
+  const int64_t ntiles = (op.n + TILE_PX - 1) / TILE_PX;
+  const int grid = (int)(ntiles < 65536 ? ntiles : 65536);
+#define CALL(K, M, E) \
+  k_residual_out<K, M, E><<<grid, TILE_PX, 0, s>>>(op, B, X, R, Rout, use_df)
+  SYLV_DISPATCH_SHAPE(k, m, e)
+#undef CALL
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_residual<float>(int k, int m, int e, int ncta, int block, const SysDesc* d,
                                    const CtaRef* c, Control* ctl, cudaStream_t s) {

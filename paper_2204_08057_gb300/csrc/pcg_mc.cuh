@@ -21,7 +21,7 @@
 // Dot products: each unit's per-warp sums go to the column's per-warp accumulators, the last CTA
 // of a system sums them in a fixed order (the last-CTA protocol of pcg_kernels.cuh).  Every
 // mbarrier wait is bounded; on expiry the CTA records SYLV_E_TIMEOUT, thread 0 waits (bounded)
-// for the copies still in flight (the last MC_NVS vector units and MC_NOP operator slots
+// for the copies still in flight (the last ring-depth vector units and MC_NOP operator slots
 // issued are the only ones that can be), and the CTA leaves without publishing partial sums.
 #pragma once
 
@@ -31,11 +31,14 @@ namespace sylv {
 namespace tma {
 
 constexpr int MC_NOP = 2;   // operator slots
-constexpr int MC_NVS = 3;   // vector stages
+constexpr int MC_NVS = 3;   // vector stages of the inner kernels (18-24 KB each)
+constexpr int MC_NVS_X = 8; // vector stages of the stand-alone apply (k rows, 4-8 KB each: a
+                            // deeper ring keeps as many bytes in flight)
 
+template <int NVS = MC_NVS>
 struct McPipe {
   uint64_t ofull[MC_NOP], oempty[MC_NOP];
-  uint64_t vfull[MC_NVS], vempty[MC_NVS];
+  uint64_t vfull[NVS], vempty[NVS];
   int otile[MC_NOP];        // tile staged in an operator slot (-1: no more tiles)
   int cols[RMAX];           // active columns
   int nact;
@@ -44,12 +47,13 @@ struct McPipe {
   int v_issued;             // vector units issued
 };
 
-__device__ __forceinline__ void mc_init(McPipe& mp) {
+template <int NVS>
+__device__ __forceinline__ void mc_init(McPipe<NVS>& mp) {
   for (int s = 0; s < MC_NOP; ++s) {
     mbar_init(&mp.ofull[s], 1);
     mbar_init(&mp.oempty[s], NCONS);
   }
-  for (int s = 0; s < MC_NVS; ++s) {
+  for (int s = 0; s < NVS; ++s) {
     mbar_init(&mp.vfull[s], 1);
     mbar_init(&mp.vempty[s], NCONS);
   }
@@ -61,7 +65,9 @@ __device__ __forceinline__ void mc_init(McPipe& mp) {
 
 // Producer side: lane 0 waits (bounded) for the consumers to release a slot or stage; the
 // result is broadcast to the warp.  false: give up (timeout, or the consumers gave up).
-__device__ __forceinline__ bool mc_wait_release(McPipe& mp, uint64_t* bar, uint32_t parity) {
+template <int NVS>
+__device__ __forceinline__ bool mc_wait_release(McPipe<NVS>& mp, uint64_t* bar,
+                                                uint32_t parity) {
   const int lane = threadIdx.x & 31;
   bool ok = true;
   if (lane == 0) ok = mbar_wait_bounded(bar, parity);
@@ -77,8 +83,9 @@ __device__ __forceinline__ bool mc_wait_release(McPipe& mp, uint64_t* bar, uint3
 // slot, bar) issues the tile's operator rows into the slot and arms bar with their bytes;
 // vec_issue(tile, col, stage, bar) the same for one column's vector rows.  After the last
 // tile a sentinel slot (tile -1, no copies) tells the consumers to stop.
-template <typename NextTile, typename OpIssue, typename VecIssue>
-__device__ __forceinline__ void mc_produce(McPipe& mp, unsigned char* opbuf, int op_bytes,
+template <int NVS, typename NextTile, typename OpIssue, typename VecIssue>
+__device__ __forceinline__ void mc_produce(McPipe<NVS>& mp, unsigned char* opbuf,
+                                           int op_bytes,
                                            unsigned char* vecbuf, int vec_bytes,
                                            NextTile&& next_tile, OpIssue&& op_issue,
                                            VecIssue&& vec_issue) {
@@ -102,8 +109,8 @@ __device__ __forceinline__ void mc_produce(McPipe& mp, unsigned char* opbuf, int
     op_issue(tile, opbuf + (size_t)os * op_bytes, &mp.ofull[os]);
     if (lane == 0) mp.o_issued = lt + 1;
     for (int a = 0; a < na; ++a, ++u) {
-      const int vs = u % MC_NVS;
-      if (u >= MC_NVS && !mc_wait_release(mp, &mp.vempty[vs], ((u / MC_NVS) - 1) & 1)) return;
+      const int vs = u % NVS;
+      if (u >= NVS && !mc_wait_release(mp, &mp.vempty[vs], ((u / NVS) - 1) & 1)) return;
       fence_proxy_async();
       vec_issue(tile, mp.cols[a], vecbuf + (size_t)vs * vec_bytes, &mp.vfull[vs]);
       if (lane == 0) mp.v_issued = u + 1;
@@ -114,8 +121,9 @@ __device__ __forceinline__ void mc_produce(McPipe& mp, unsigned char* opbuf, int
 // Consumer warps.  on_tile(tile, slot) reads the slot into registers (the slot is released
 // right after); on_unit(tile, col, stage, release) computes one column of the tile from the
 // stage and calls release() once it has read the stage.
-template <typename OnTile, typename OnUnit>
-__device__ __forceinline__ void mc_consume(McPipe& mp, const unsigned char* opbuf, int op_bytes,
+template <int NVS, typename OnTile, typename OnUnit>
+__device__ __forceinline__ void mc_consume(McPipe<NVS>& mp, const unsigned char* opbuf,
+                                           int op_bytes,
                                            const unsigned char* vecbuf, int vec_bytes,
                                            OnTile&& on_tile, OnUnit&& on_unit) {
   const int lane = threadIdx.x & 31;
@@ -133,8 +141,8 @@ __device__ __forceinline__ void mc_consume(McPipe& mp, const unsigned char* opbu
     __syncwarp();
     if (lane == 0) mbar_arrive(&mp.oempty[os]);
     for (int a = 0; a < na; ++a, ++u) {
-      const int vs = u % MC_NVS;
-      if (!mbar_wait_bounded(&mp.vfull[vs], (u / MC_NVS) & 1) || mp.bad) {
+      const int vs = u % NVS;
+      if (!mbar_wait_bounded(&mp.vfull[vs], (u / NVS) & 1) || mp.bad) {
         mp.bad = 1;
         return;
       }
@@ -149,13 +157,14 @@ __device__ __forceinline__ void mc_consume(McPipe& mp, const unsigned char* opbu
 
 // After both roles: on a recorded timeout, flag it, wait (bounded) for the copies that can
 // still be in flight and report true (the caller leaves without partial sums).
-__device__ __forceinline__ bool mc_failed(McPipe& mp, unsigned int* err) {
+template <int NVS>
+__device__ __forceinline__ bool mc_failed(McPipe<NVS>& mp, unsigned int* err) {
   __syncthreads();
   if (!mp.bad) return false;
   if (threadIdx.x == 0) {
     atomicOr(err, 1u);
-    for (int u = mp.v_issued > MC_NVS ? mp.v_issued - MC_NVS : 0; u < mp.v_issued; ++u)
-      mbar_wait_bounded(&mp.vfull[u % MC_NVS], (u / MC_NVS) & 1);
+    for (int u = mp.v_issued > NVS ? mp.v_issued - NVS : 0; u < mp.v_issued; ++u)
+      mbar_wait_bounded(&mp.vfull[u % NVS], (u / NVS) & 1);
     for (int t = mp.o_issued > MC_NOP ? mp.o_issued - MC_NOP : 0; t < mp.o_issued; ++t)
       mbar_wait_bounded(&mp.ofull[t % MC_NOP], (t / MC_NOP) & 1);
   }
@@ -291,7 +300,7 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
   using VR = McApplyVec<K>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 1> sh;
-  __shared__ __align__(8) McPipe mp;
+  __shared__ __align__(8) McPipe<> mp;
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
@@ -422,7 +431,8 @@ struct McUpdateRows {
 
 template <int K>
 constexpr size_t mc_update_smem() {
-  return (size_t)MC_NOP * McUpdateRows<K>::OP_BYTES + (size_t)MC_NVS * McUpdateRows<K>::VEC_BYTES;
+  return (size_t)MC_NOP * McUpdateRows<K>::OP_BYTES +
+         (size_t)MC_NVS * McUpdateRows<K>::VEC_BYTES;
 }
 
 template <int K, int M>
@@ -432,7 +442,7 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   using L = McUpdateRows<K>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 2> sh;   // (mixing rows unused here: the factor is stored)
-  __shared__ __align__(8) McPipe mp;
+  __shared__ __align__(8) McPipe<> mp;
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
@@ -573,7 +583,7 @@ struct McXVec {
 
 template <int K, int M, int E>
 constexpr size_t mc_applyx_smem() {
-  return (size_t)MC_NOP * McOpRows<M, E>::BYTES + (size_t)MC_NVS * McXVec<K>::BYTES;
+  return (size_t)MC_NOP * McOpRows<M, E>::BYTES + (size_t)MC_NVS_X * McXVec<K>::BYTES;
 }
 
 template <int K, int M, int E>
@@ -583,7 +593,7 @@ k_apply_mc(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R,
   using OR = McOpRows<M, E>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<float, 1> sh;
-  __shared__ __align__(8) McPipe mp;
+  __shared__ __align__(8) McPipe<MC_NVS_X> mp;
   stage_operator<float, 1>(op, K, sh);
   if (threadIdx.x == 0) {
     for (int r = 0; r < R; ++r) mp.cols[r] = r;

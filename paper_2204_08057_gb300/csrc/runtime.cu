@@ -156,6 +156,9 @@ struct sylv_ctx {
                                       // CTAs done
   float* fs32 = nullptr;
   __half2* fl16 = nullptr;
+  float* blk_hl = nullptr;    // pixel blocks as FP32 pairs (double-float residual)
+  float* val_hl = nullptr;    // ELL values as FP32 pairs
+  int val_df_bad = 0;         // an ELL value lies outside the double-float range
   std::unique_ptr<Plan> plan[2];  // single-system plans, [inner_double]
   double* lam = nullptr;
   size_t lam_bytes = 0;
@@ -201,6 +204,15 @@ Plan::~Plan() {
 }
 
 namespace {
+
+// The mixed solve's true residual: double-float (default), SYLV_RESIDUAL=f64 the FP64 kernels,
+// SYLV_RESIDUAL=plain the double-float kernel without staging; read at every solve.
+int residual_mode() {
+  const char* v = std::getenv("SYLV_RESIDUAL");
+  if (v && std::strcmp(v, "f64") == 0) return 0;
+  if (v && std::strcmp(v, "plain") == 0) return 2;
+  return 1;
+}
 
 // SYLV_STAGED_APPLY=0 keeps the stand-alone FP32 apply on the direct kernel.
 const bool g_staged_apply = [] {
@@ -728,16 +740,27 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   // are (tile, column) pairs that re-stage the tile's pixel blocks for every column, so with
   // more than two columns the direct kernel is faster (8 columns, 50M pixels: 292 against
   // 325 ms per solve)
+  // In mixed precision the residual is formed in double-float on the FP32 pipe when every
+  // system of the group allows it (operator entries in its range): staged (k_residual_tma_df)
+  // where the caller's rows can be copied whole, else k_residual_df; the FP64 kernels are bound
+  // by the FP64 unit.  rs_staged: 0 direct FP64, 1 staged FP64, 2 double-float, 3 staged
+  // double-float.
+  const int rmode = residual_mode();
   std::vector<char> rs_staged(P.groups.size(), 0);
   for (size_t gi = 0; gi < P.groups.size(); ++gi) {
     const Group& g = P.groups[gi];
+    bool df = !P.inner_double && rmode != 0;
     bool ok = g.rs_ok != 0;
+    int rmax = 0;
     for (int t : g.sys) {
       const OpData& op = P.hs[t]->op;
-      ok = ok && P.R[t] <= 2 && op.n % TILE_PX == 0 && op.ldu % 2 == 0 &&
+      df = df && op.df_ok;
+      rmax = std::max(rmax, P.R[t]);
+      ok = ok && op.n % TILE_PX == 0 && op.ldu % 2 == 0 &&
            ((uintptr_t)B[t] & 15u) == 0 && ((uintptr_t)X[t] & 15u) == 0;
     }
-    rs_staged[gi] = ok ? 1 : 0;
+    if (df) rs_staged[gi] = (ok && rmode == 1) ? 3 : 2;
+    else rs_staged[gi] = (ok && rmax <= 2) ? 1 : 0;
   }
   if (o.use_graph) {
     int rc = ensure_graph<T>(P, iters, prof ? 1 : 0);
@@ -789,7 +812,13 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
     if (prof) CK(cudaEventRecord(P.evr0, s));
     for (size_t gi = 0; gi < P.groups.size(); ++gi) {
       Group& g = P.groups[gi];
-      if (rs_staged[gi])
+      if (rs_staged[gi] == 3)
+        CK(launch_residual_staged_df(g.k, g.m, g.e, g.ncta[3], P.d_desc, g.d_ctas[3], P.d_ctl,
+                                     s));
+      else if (rs_staged[gi] == 2)
+        CK(launch_residual_df(g.k, g.m, g.e, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], P.d_ctl,
+                              s));
+      else if (rs_staged[gi] == 1)
         CK(launch_residual_staged(g.k, g.m, g.e, g.ncta[3], P.d_desc, g.d_ctas[3], P.d_ctl, s));
       else
         CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], P.d_ctl, s));
@@ -980,6 +1009,8 @@ static void free_handle(sylv_ctx* h) {
   cudaFree(h->fac64);
   cudaFree(h->fs32);
   cudaFree(h->fl16);
+  cudaFree(h->blk_hl);
+  cudaFree(h->val_hl);
   cudaFree(h->apply_err);
   cudaFree(h->lam);
   cudaFree(h->grad_ws);
@@ -1025,7 +1056,46 @@ static int set_scalars(OpData& op, const double* tau, const double* kappa, const
     op.tk2_64[j] = tau[j] * kappa[j] * kappa[j];
     op.tau32[j] = (float)op.tau64[j];
     op.tk2_32[j] = (float)op.tk2_64[j];
+    op.tau_hl[0][j] = (float)tau[j];
+    op.tau_hl[1][j] = (float)(tau[j] - (double)op.tau_hl[0][j]);
   }
+  return SYLV_OK;
+}
+
+// tau within the double-float residual's range (every nonzero operator entry in [2^-40, 2^40])
+static bool tau_in_df_range(const OpData& op) {
+  for (int j = 0; j < op.k; ++j)
+    if (!(op.tau64[j] >= 0x1p-40 && op.tau64[j] <= 0x1p40)) return false;
+  return true;
+}
+
+// FP32 pairs of the pixel blocks (and, with `vals`, of the ELL values) for the double-float
+// residual; sets op.df_ok.  Synchronises s.
+static int split_operator(sylv_ctx* h, OpData& op, bool vals, cudaStream_t s) {
+  const size_t ld = (size_t)op.ld, nb = (size_t)op.k * (op.k + 1) / 2;
+  const size_t ne = (size_t)std::max(op.E, 1);
+  unsigned int* dflag = nullptr;
+  unsigned int hflag[2] = {0, 0};
+  cudaError_t e = cudaSuccess;
+  if (!h->blk_hl) e = dalloc(&h->blk_hl, 2 * nb * ld * sizeof(float));
+  if (e == cudaSuccess && !h->val_hl) e = dalloc(&h->val_hl, 2 * ne * ld * sizeof(float));
+  if (e == cudaSuccess) e = dalloc(&dflag, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, 2 * sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = launch_split_hl(op.blk64, nb, ld, h->blk_hl, dflag, s);
+  if (e == cudaSuccess && vals) {
+    e = cudaMemsetAsync(h->val_hl, 0, 2 * ne * ld * sizeof(float), s);
+    if (e == cudaSuccess && op.E > 0)
+      e = launch_split_hl(op.ell_val64, op.E, ld, h->val_hl, dflag + 1, s);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hflag, dflag, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dflag);
+  if (e != cudaSuccess) return cuda_fail(e, "double-float operator copies");
+  if (vals) h->val_df_bad = hflag[1] != 0;
+  op.blk_hl = h->blk_hl;
+  op.val_hl = h->val_hl;
+  op.df_ok = (hflag[0] == 0 && !h->val_df_bad && tau_in_df_range(op)) ? 1 : 0;
   return SYLV_OK;
 }
 
@@ -1222,6 +1292,10 @@ int sylv_create(sylv_handle* out, const sylv_problem* p, sylv_stream stream) {
   if ((e = launch_block_setup(op, h->blk64, h->fac64, h->fs32, h->fl16, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return bail(cuda_fail(e, "pixel-block set-up"));
+  {
+    const int rc2 = split_operator(h, op, true, s);
+    if (rc2 != SYLV_OK) return bail(rc2);
+  }
   cudaFree(dflags);
   *out = h;
   return SYLV_OK;
@@ -1239,6 +1313,8 @@ int sylv_set_params(sylv_handle h, const double* tau, const double* kappa, const
   // the pixel blocks and their factors depend on tau, kappa and A
   CK(launch_block_setup(op, h->blk64, h->fac64, h->fs32, h->fl16, s));
   CK(cudaStreamSynchronize(s));
+  rc = split_operator(h, op, false, s);
+  if (rc != SYLV_OK) return rc;
   h->op = op;
   h->explicit_A = A != nullptr;
   lanczos_release(h);   // separability and Lhat were derived from the old scalars
@@ -1290,6 +1366,15 @@ int sylv_apply(sylv_handle h, const void* X, void* Y, int nrhs, int dtype, sylv_
   } else {
     return fail(SYLV_E_INVALID, "dtype must be SYLV_F32 or SYLV_F64");
   }
+  return SYLV_OK;
+}
+
+int sylv_residual(sylv_handle h, const double* B, const double* X, int nrhs, double* R,
+                  sylv_stream s) {
+  if (!h || !B || !X || !R) return fail(SYLV_E_INVALID, "NULL argument");
+  if (nrhs < 1) return fail(SYLV_E_INVALID, "nrhs must be >= 1");
+  DeviceGuard g(h->device);
+  CK(launch_residual_out(h->op, B, X, nrhs, R, h->op.df_ok, (cudaStream_t)s));
   return SYLV_OK;
 }
 
@@ -1457,10 +1542,11 @@ int sylv_solve_batched(int nsys, const sylv_handle* hs, const double* const* B,
   return solve_impl(nsys, hs, B, X, nrhs, o, infos, (cudaStream_t)s, false);
 }
 
-int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const sylv_opts* o_in,
-                  sylv_info* info, sylv_stream stream) {
-  if (!h || !Z || !var) return fail(SYLV_E_INVALID, "NULL argument");
-  if (nprobe < 1) return fail(SYLV_E_INVALID, "nprobe must be >= 1");
+// The probe loop of sylv_variance and sylv_variance_probing: nprobe probes, SYLV_MAX_RHS at a
+// time, each chunk's probes either the caller's (Z) or generated from a colouring (colour).
+static int variance_impl(sylv_handle h, const double* Z, const int32_t* colour, int ncol,
+                         int nprobe, double* var, const sylv_opts* o_in, sylv_info* info,
+                         sylv_stream stream) {
   sylv_opts o;
   if (o_in) o = *o_in;
   else sylv_opts_default(&o);
@@ -1470,7 +1556,8 @@ int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const
   const OpData& op = h->op;
   const int chunk = std::min(nprobe, RMAX);
   const size_t xelems = (size_t)chunk * op.k * op.ldu, kelems = (size_t)op.k * op.ld;
-  const size_t bytes = (xelems + 2 * kelems) * sizeof(double);
+  // X of a chunk, num, den, a flag word (and the chunk's generated probes)
+  const size_t bytes = ((colour ? 2 : 1) * xelems + 2 * kelems + 1) * sizeof(double);
   if (h->var_bytes < bytes) {
     cudaFree(h->var_ws);
     h->var_ws = nullptr;
@@ -1481,13 +1568,16 @@ int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const
   double* X = h->var_ws;
   double* num = X + xelems;
   double* den = num + kelems;
-  CK(cudaMemsetAsync(num, 0, 2 * kelems * sizeof(double), s));
+  unsigned int* flag = (unsigned int*)(den + kelems);
+  double* Zg = colour ? (double*)(flag + 2) : nullptr;
+  CK(cudaMemsetAsync(num, 0, 2 * kelems * sizeof(double) + sizeof(double), s));
   sylv_info tot;
   std::memset(&tot, 0, sizeof(tot));
   int worst = SYLV_OK;
   for (int s0 = 0; s0 < nprobe; s0 += chunk) {
     const int r = std::min(chunk, nprobe - s0);
-    const double* Zc = Z + (size_t)s0 * op.k * op.ldu;
+    const double* Zc = Z ? Z + (size_t)s0 * op.k * op.ldu : Zg;
+    if (colour) CK(launch_probe_fill(op, colour, ncol, s0, r, Zg, flag, s));
     sylv_info inf;
     int rc = sylv_solve(h, Zc, X, r, &o, &inf, stream);
     if (rc != SYLV_OK && rc != SYLV_E_NOT_CONVERGED) return rc;
@@ -1501,7 +1591,7 @@ int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const
     tot.ms_apply += inf.ms_apply;
     tot.ms_update += inf.ms_update;
     tot.ms_residual += inf.ms_residual;
-    tot.launches += inf.launches + 1;
+    tot.launches += inf.launches + (colour ? 2 : 1);
     tot.tile = inf.tile;
     tot.slots_mult = inf.slots_mult;
     tot.apply_staged = inf.apply_staged;
@@ -1509,12 +1599,32 @@ int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const
     tot.residual_staged = inf.residual_staged;
   }
   CK(launch_var_finish(op, num, den, var, s));
+  unsigned int hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (hflag) return fail(SYLV_E_INVALID, "a pixel's colour lies outside [0, ncolours)");
   tot.launches += 1;
   tot.status = worst;
   if (info) *info = tot;
   if (worst != SYLV_OK) store_error("a probe solve did not reach the tolerance");
   return worst;
+}
+
+int sylv_variance(sylv_handle h, const double* Z, int nprobe, double* var, const sylv_opts* o_in,
+                  sylv_info* info, sylv_stream stream) {
+  if (!h || !Z || !var) return fail(SYLV_E_INVALID, "NULL argument");
+  if (nprobe < 1) return fail(SYLV_E_INVALID, "nprobe must be >= 1");
+  return variance_impl(h, Z, nullptr, 0, nprobe, var, o_in, info, stream);
+}
+
+int sylv_variance_probing(sylv_handle h, const int32_t* colour, int ncolours, double* var,
+                          const sylv_opts* o_in, sylv_info* info, sylv_stream stream) {
+  if (!h || !colour || !var) return fail(SYLV_E_INVALID, "NULL argument");
+  if (ncolours < 1) return fail(SYLV_E_INVALID, "ncolours must be >= 1");
+  if ((int64_t)ncolours * h->op.k > INT32_MAX)
+    return fail(SYLV_E_INVALID, "ncolours * k too large");
+  return variance_impl(h, nullptr, colour, ncolours, ncolours * h->op.k, var, o_in, info,
+                       stream);
 }
 
 int sylv_backward(sylv_handle h, const double* Xhat, const double* dLdX, const double* Yobs,

@@ -173,6 +173,22 @@ __global__ void k_var_accum(int64_t n, int k, int64_t ldu, int64_t ld, const dou
   den[j * ld + i] = b;
 }
 
+// Probes s = 0..R-1 of a colouring: probe p0 + s is colour q = (p0 + s) / k in source
+// j = (p0 + s) % k, i.e. Z[s][j'][i] = 1 where j' = j and colour[i] = q, else 0.  Colours
+// outside [0, ncol) are flagged.
+__global__ void k_probe_fill(int64_t n, int k, int64_t ldu, const int32_t* __restrict__ colour,
+                             int ncol, int p0, int R, double* __restrict__ Z,
+                             unsigned int* flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = colour[i];
+  if (c < 0 || c >= ncol) atomicOr(flag, 1u);
+  for (int s = 0; s < R; ++s) {
+    const int q = (p0 + s) / k, j0 = (p0 + s) % k;
+    for (int j = 0; j < k; ++j) Z[((int64_t)s * k + j) * ldu + i] = (j == j0 && c == q) ? 1.0 : 0.0;
+  }
+}
+
 __global__ void k_var_finish(int64_t n, int k, int64_t ldu, int64_t ld,
                              const double* __restrict__ num, const double* __restrict__ den,
                              double* var) {
@@ -217,6 +233,23 @@ __global__ void k_rhs(OpData op, const double* __restrict__ Y, double* __restric
     for (int j = 0; j < KMAX; ++j)
       if (j < op.k) B[((int64_t)r * op.k + j) * ldu + i] = acc[j];
   }
+}
+
+// FP32 pairs of an FP64 array (the double-float residual's operator copies): hi = fl32(v),
+// lo = fl32(v - hi), so v = hi + lo to 2^-48 |v|.  Flags entries outside what the double-float
+// residual takes (nonzero with |v| outside [2^-40, 2^40], or not finite).
+__global__ void __launch_bounds__(256) k_split_hl(const double* __restrict__ src, int64_t total,
+                                                  int64_t rows_ld, float* __restrict__ dst,
+                                                  unsigned int* flag) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const double v = src[t];
+  const float h = (float)v;
+  const float l = (float)(v - (double)h);
+  dst[t] = h;
+  dst[rows_ld + t] = l;
+  const double a = fabs(v);
+  if (!isfinite(v) || (v != 0.0 && (a < 0x1p-40 || a > 0x1p40))) atomicOr(flag, 1u);
 }
 
 // Pixel blocks P_i (FP64) and their scaled Cholesky factors, once per handle.
@@ -432,6 +465,13 @@ cudaError_t launch_var_accum(const OpData& op, const double* Z, const double* X,
   return cudaGetLastError();
 }
 
+cudaError_t launch_probe_fill(const OpData& op, const int32_t* colour, int ncol, int p0, int R,
+                              double* Z, unsigned int* flag, cudaStream_t s) {
+  k_probe_fill<<<blocks_for(op.n, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(op.n, op.k, op.ldu, colour,
+                                                                     ncol, p0, R, Z, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_var_finish(const OpData& op, const double* num, const double* den,
                               double* var, cudaStream_t s) {
   const int64_t tot = (int64_t)op.k * op.n;
@@ -456,6 +496,15 @@ cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, f
 #define CALL(K) k_block_setup<K><<<nb, 256, 0, s>>>(op, blk64, fac64, fs32, fl16)
   SYLV_DISPATCH_K(op.k, CALL)
 #undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_hl(const double* src, int64_t rows, int64_t ld, float* dst,
+                            unsigned int* flag, cudaStream_t s) {
+  const int64_t total = rows * ld;
+  if (total == 0) return cudaSuccess;
+  k_split_hl<<<blocks_for(total, SETUP_BLOCK), SETUP_BLOCK, 0, s>>>(src, total, total, dst,
+                                                                    flag);
   return cudaGetLastError();
 }
 

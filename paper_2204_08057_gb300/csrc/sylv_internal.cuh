@@ -79,6 +79,13 @@ struct OpData {
   const __half2* fl16;       // ceil(K(K+1)/2 / 2) x ld: its triangular factor in FP16, two
                              // entries per pixel and row (entry a in row a/2, lane a%2); the
                              // FP32 inner preconditioner; entries lie in [-1, 1e3]
+  const float* blk_hl;       // 2 K(K+1)/2 x ld: blk64 as FP32 pairs, hi rows then lo rows
+                             // (blk64 = hi + lo to 2^-48), for the double-float residual
+  const float* val_hl;       // 2 E x ld: ell_val64 the same way
+  int df_ok;                 // every nonzero entry of blk64, ell_val64 and tau lies in
+                             // [2^-40, 2^40]: the double-float residual applies
+  int pad_df;
+  float tau_hl[2][KMAX];     // tau as an FP32 pair
   float A32[MMAX * KMAX];    // A[c * k + j]
   double A64[MMAX * KMAX];
   float tau32[KMAX];
@@ -176,6 +183,10 @@ cudaError_t launch_var_accum(const OpData& op, const double* Z, const double* X,
                              double* num, double* den, cudaStream_t s);
 cudaError_t launch_var_finish(const OpData& op, const double* num, const double* den,
                               double* var, cudaStream_t s);
+// R probing vectors of a colouring (probes p0 .. p0 + R - 1; probe t is colour t / k in
+// source t % k) into Z (R x k x ldu); *flag set if a colour lies outside [0, ncol).
+cudaError_t launch_probe_fill(const OpData& op, const int32_t* colour, int ncol, int p0, int R,
+                              double* Z, unsigned int* flag, cudaStream_t s);
 // Intrinsic GMRF prior shape: the ELL width of L^2 (atomic max into *width), then L^2 itself
 // into new ELL arrays of that width and a new diagonal.
 cudaError_t launch_square_count(const OpData& op, unsigned int* width, cudaStream_t s);
@@ -191,6 +202,21 @@ cudaError_t launch_rhs_range(const OpData& op, const double* Y, double* B, int R
                              int64_t i1, cudaStream_t s);
 cudaError_t launch_block_setup(const OpData& op, double* blk64, double* fac64, float* fs32,
                                __half2* fl16, cudaStream_t s);
+// dst[q][i] = hi, dst[rows + q][i] = lo of src[q][i] (q < rows, i < ld); sets *flag if a
+// nonzero entry lies outside [2^-40, 2^40] or is not finite.
+cudaError_t launch_split_hl(const double* src, int64_t rows, int64_t ld, float* dst,
+                            unsigned int* flag, cudaStream_t s);
+// Stand-alone residual Rout = B - G X (FP64 caller vectors, nrhs columns), double-float when
+// use_df (else FP64).
+cudaError_t launch_residual_out(const OpData& op, const double* B, const double* X, int R,
+                                double* Rout, int use_df, cudaStream_t s);
+// The same with bulk-copy staging (the conditions and CTA list of launch_residual_staged).
+cudaError_t launch_residual_staged_df(int k, int m, int e, int ncta, const SysDesc* d,
+                                      const CtaRef* c, Control* ctl, cudaStream_t s);
+// Mixed-precision residual of the refinement loop in double-float (handles with df_ok), over
+// the residual CTA list with tiles of `block` pixels.
+cudaError_t launch_residual_df(int k, int m, int e, int ncta, int block, const SysDesc* d,
+                               const CtaRef* c, Control* ctl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_apply(const OpData& op, const T* X, T* Y, int R, cudaStream_t s);
 cudaError_t launch_apply_staged(const OpData& op, const float* X, float* Y, int R,

@@ -99,6 +99,16 @@ class Operator:
                      stream=stream)
         return Y
 
+    def residual(self, Bv, X, stream=None):
+        """R = B - G X (float64 (R, k, ld)), as the mixed-precision solve forms it."""
+        import torch
+        Bb = self._batch(Bv.to(torch.float64), self.k)
+        Xb = self._batch(X.to(torch.float64), self.k)
+        out = torch.empty_like(Bb)
+        B.sylv_residual(self.handle, Bb, Xb, out, Bb.shape[0], k=self.k, ld=self.ld, n=self.n,
+                        stream=stream)
+        return out
+
     def solve(self, Bv, X0=None, *, opts=None, stream=None, allow_not_converged=False,
               allow=(), **kw):
         """X = G^{-1} B; returns (X, info dict)."""
@@ -163,6 +173,23 @@ class Operator:
         allow = (B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ()
         code, info = B.sylv_variance(self.handle, Zb, Zb.shape[0], var, opts, k=self.k,
                                      ld=self.ld, n=self.n, stream=stream, allow=allow)
+        d = info.as_dict()
+        d["code"] = code
+        return var, d
+
+    def variance_probing(self, colour, ncolours, *, opts=None, stream=None,
+                         allow_not_converged=False, **kw):
+        """Posterior variances diag(G^{-1}) (k, ld) from the probing vectors of a pixel
+        colouring (colour: n integers in [0, ncolours))."""
+        import torch
+        col = _to_device(colour, torch.int32, self.device)
+        if opts is None:
+            opts = B.make_opts(**kw)
+        var = torch.zeros((self.k, self.ld), dtype=torch.float64, device=self.device)
+        allow = (B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ()
+        code, info = B.sylv_variance_probing(self.handle, col, int(ncolours), var, opts,
+                                             k=self.k, ld=self.ld, n=self.n, stream=stream,
+                                             allow=allow)
         d = info.as_dict()
         d["code"] = code
         return var, d

@@ -28,6 +28,8 @@ from .problems import (  # noqa: F401
     config_problem,
     batch_problems,
     batch_shapes,
+    colouring_probes,
+    grid_colouring,
     separable_problem,
     igmrf_problem,
     rademacher_probes,

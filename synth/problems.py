@@ -235,6 +235,33 @@ def batch_shapes(count=64, side_range=(128, 1024), *, seed=None):
     return [(int(a), int(b)) for a, b in zip(sides, ks)]
 
 
+def grid_colouring(graph: GridGraph, p: int) -> np.ndarray:
+    """Colour of every pixel of a grid graph, (r mod p) * p + (c mod p): p^2 colours, and two
+    distinct pixels of one colour are at least p steps apart on the grid (a distance-(p - 1)
+    colouring).  A periodic side must be a multiple of p (longitude always; latitude too on
+    the periodic lattice) so that the wrap-around keeps that property."""
+    if p < 1:
+        raise ValueError("p must be >= 1")
+    if graph.W % p or (graph.kind == "lattice" and graph.H % p):
+        raise ValueError(f"a periodic side of the {graph.kind} is not a multiple of p = {p}")
+    r = np.repeat(np.arange(graph.H, dtype=np.int64), graph.W)
+    c = np.tile(np.arange(graph.W, dtype=np.int64), graph.H)
+    return ((r % p) * p + c % p).astype(np.int64)
+
+
+def colouring_probes(graph: GridGraph, k: int, p: int) -> np.ndarray:
+    """(p^2 k, k, n) probing vectors of a distance-(p - 1) colouring: probe (q, j) is 1 on the
+    pixels of colour q in source j and 0 elsewhere, so every (source, pixel) entry is covered
+    by exactly one probe."""
+    col = grid_colouring(graph, p)
+    Z = np.zeros((p * p * k, k, graph.n))
+    for q in range(p * p):
+        mask = col == q
+        for j in range(k):
+            Z[q * k + j, j, mask] = 1.0
+    return Z
+
+
 def batch_problems(count=64, side_range=(128, 1024), *, seed=None,
                    indices=None) -> List[Problem]:
     """Batched workload: ``count`` independent periodic lattices of log-uniform side, k in

@@ -86,10 +86,20 @@ def test_sphere_2M_bench_workload_rows_and_residual():
     assert info["code"] == 0
     b = model.rhs(p.D, p.Yobs[0], A)
     assert np.allclose(B.cpu().numpy()[0], b, rtol=1e-12, atol=1e-12 * np.abs(b).max())
-    r = b - model.apply(L, p.D, p.tau, p.kappa, A, X.cpu().numpy()[0])
+    Xh = X.cpu().numpy()[0]
+    r = b - model.apply(L, p.D, p.tau, p.kappa, A, Xh)
     rel = np.linalg.norm(r) / np.linalg.norm(b)
     assert rel <= 1.0e-8 * 1.001
     assert abs(rel - info["relres"]) <= 1e-3 * rel
+    # the refinement's double-float residual of that solution, element by element on the
+    # sampled rows (b and G X cancel to eight digits there)
+    assert info["residual_staged"] in (2, 3)     # double-float (staged where the rows allow)
+    Rd = op.residual(B, X).cpu().numpy()[0][:, rows]
+    ref_rows = b[:, rows] - model.apply_rows(L, p.D, p.tau, p.kappa, A, Xh, rows)
+    scale = np.abs(b[:, rows]) + model.apply_rows(abs(L), p.D, np.abs(p.tau), np.abs(p.kappa),
+                                                  np.abs(A), np.abs(Xh), rows)
+    E = int(np.max(np.diff(p.graph.rowptr))) - 1
+    assert np.all(np.abs(Rd - ref_rows) <= (p.k + E + 4) * 2.0 ** -45 * scale)
     op.close()
 
 

@@ -153,12 +153,14 @@ def test_solve_parity(kind, H, W, k, m, nrhs, precision):
 
 @pytest.mark.parametrize("nrhs", [1, 2, 3])
 def test_staged_residual_parity(nrhs, monkeypatch):
-    """Whole tiles, an even caller leading dimension and at most two columns: the FP64 residual
-    stages its streams (reported in the info); otherwise the direct kernel runs.  Cold and
-    warm starts, one to three right-hand sides, against the oracle's direct solve.  The tile
-    configuration is pinned to 256-pixel tiles with both staged inner kernels (the staged
-    residual needs 256-pixel tiles; the tuner may prefer 128 on a problem this small)."""
+    """With the FP64 residual selected (SYLV_RESIDUAL=f64): whole tiles, an even caller leading
+    dimension and at most two columns stage its streams (reported in the info); otherwise the
+    direct kernel runs.  Cold and warm starts, one to three right-hand sides, against the
+    oracle's direct solve.  The tile configuration is pinned to 256-pixel tiles with both
+    staged inner kernels (the staged residual needs 256-pixel tiles; the tuner may prefer 128
+    on a problem this small)."""
     monkeypatch.setenv("SYLV_TUNE_FORCE", "256,1,1,1")
+    monkeypatch.setenv("SYLV_RESIDUAL", "f64")
     p = small_problem("sphere", 16, 64, 6, 9, seed=33, nrhs=nrhs)   # n = 1024, (k, m, E) = (6, 9, 4)
     Xo, b = oracle_solution(p)
     for ldu in (p.n, p.n + 1):
@@ -174,6 +176,102 @@ def test_staged_residual_parity(nrhs, monkeypatch):
         assert info["code"] == 0
         assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
         op.close()
+
+
+def _df_bound(p, E, X, b, A):
+    """(k + E + 4) 2^-45 (|b| + |G||X|) element-wise: the stated error bound of the
+    double-float residual (each output sums at most k + 1 products and a stencil of E, every
+    product leaving below 2^-45 of itself in the compensation and the operand splits)."""
+    return (p.k + E + 4) * 2.0 ** -45 * (np.abs(b) + abs_apply(p, X, A))
+
+
+RESID_CASES = [
+    ("lattice", 37, 41, 3, 5, 2),     # ragged last tile, two columns
+    ("sphere", 20, 33, 6, 9, 1),
+    ("sphere", 16, 17, 8, 16, 3),     # largest k and m
+    ("lattice", 9, 11, 1, 1, 1),      # scalar case
+]
+
+
+@pytest.mark.parametrize("kind,H,W,k,m,nrhs", RESID_CASES)
+def test_residual_double_float_elementwise(kind, H, W, k, m, nrhs):
+    """sylv_residual (the refinement's true residual, double-float on the FP32 pipe) against
+    the oracle's FP64 b - G X element by element, on a nearly converged X (|r| ~ 1e-9 |b|, so
+    b and G X cancel to nine digits), within the stated bound; its typical error is far below."""
+    p = small_problem(kind, H, W, k, m, seed=60 + k, nrhs=nrhs)
+    ld = p.n + 3
+    op = operator_for(p, ld=ld)
+    A = model.powerlaw_mixing(p.nu, p.beta)
+    L = oracle_L(p)
+    rng = np.random.default_rng(k + m)
+    X = rng.standard_normal((nrhs, k, p.n)) * np.exp(rng.uniform(-3, 3, size=(nrhs, k, 1)))
+    X[:, :, ::7] = 0.0                                   # exact zeros are split too
+    GX = np.stack([model.apply(L, p.D, p.tau, p.kappa, A, x) for x in X])
+    b = GX + 1e-9 * np.abs(GX).max() * rng.standard_normal(GX.shape)
+    ref = b - GX
+    R = op.residual(device_batch(b, ld), device_batch(X, ld)).cpu().numpy()[:, :, :p.n]
+    E = op_degree_of(p)
+    err = np.abs(R - ref)
+    scale = np.stack([np.abs(b[r]) + abs_apply(p, X[r], A) for r in range(nrhs)])
+    assert np.all(err <= np.stack([_df_bound(p, E, X[r], b[r], A) for r in range(nrhs)]))
+    assert np.sqrt(np.mean((err / scale) ** 2)) <= 2.0 ** -46
+    op.close()
+
+
+def test_residual_outside_double_float_range_uses_fp64():
+    """Pixels whose X lies outside the split's range, and a handle whose tau exceeds 2^40, are
+    computed in FP64: still within the FP64 bound of the oracle's residual."""
+    p = small_problem("sphere", 12, 20, 4, 6, seed=3)
+    A = model.powerlaw_mixing(p.nu, p.beta)
+    L = oracle_L(p)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((1, p.k, p.n))
+    X[0, 1, 5] = 1e-30                                   # below 2^-60
+    X[0, 2, 40] = 3e20                                   # above 2^61
+    for tau_scale in (1.0, 1e13):
+        q = synth.Problem(p.name, p.graph, p.k, p.m, p.tau * tau_scale, p.kappa, p.nu, p.beta,
+                          p.D, p.Yobs, p.X_true, p.tol, {})
+        op = operator_for(q)
+        GX = model.apply(L, q.D, q.tau, q.kappa, A, X[0])
+        b = GX + 1e-6 * rng.standard_normal(GX.shape)
+        R = op.residual(device_batch(b, p.n), device_batch(X, p.n)).cpu().numpy()[0]
+        bound = 64 * U64 * (np.abs(b) + abs_apply(q, X[0], A)) + \
+            _df_bound(q, op_degree_of(q), X[0], b, A)
+        assert np.all(np.abs(R - (b - GX)) <= bound), tau_scale
+        op.close()
+
+
+@pytest.mark.parametrize("nrhs,pad", [(1, 0), (2, 0), (3, 0), (8, 0), (1, 1), (3, 1)])
+def test_double_float_residual_in_the_solve(nrhs, pad, monkeypatch):
+    """Mixed solves whose true residual is formed in double-float: staged (whole tiles, an even
+    caller leading dimension) for one to eight right-hand sides, plain otherwise (odd ld); cold
+    and warm starts against the oracle's direct solve, and a warm start holding values below
+    the double-float range at some pixels (recomputed in FP64 inside the kernel).  (Values
+    whose squares overflow FP32 cannot start a mixed solve with either residual kernel: the
+    inner solve's dot products are FP32.)"""
+    monkeypatch.setenv("SYLV_TUNE_FORCE", "256,1,1,1")
+    p = small_problem("sphere", 16, 64, 6, 9, seed=35, nrhs=nrhs)   # n = 1024: whole tiles
+    ldu = p.n + pad
+    op = operator_for(p, ld=ldu)
+    Xo, b = oracle_solution(p)
+    Bd = device_batch(b, ldu)
+    X, info = op.solve(Bd, tol=1e-11, precision=1)
+    assert info["code"] == 0, info
+    assert info["residual_staged"] == (3 if pad == 0 else 2), info
+    assert relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+    X0 = Xo + 1e-3
+    X, info = op.solve(Bd, X0=device_batch(X0, ldu), tol=1e-11, precision=1)
+    assert info["code"] == 0 and relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+    X0[:, :, ::37] = 1e-30                  # below the split's range: FP64 at those pixels
+    X, info = op.solve(Bd, X0=device_batch(X0, ldu), tol=1e-11, precision=1)
+    assert info["code"] == 0 and relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+    op.close()
+
+
+def op_degree_of(p):
+    """Off-diagonal entries per row of the problem's prior shape."""
+    deg = int(np.max(np.diff(p.graph.rowptr))) - 1
+    return 3 * deg if p.prior == "igmrf" else deg
 
 
 MC_CASES = [

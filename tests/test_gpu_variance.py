@@ -77,3 +77,49 @@ def test_lattice_average_matches_closed_form():
     avg = var.cpu().numpy()[:, :p.n].mean(axis=1)
     assert np.abs(avg - cf).max() <= 0.02 * cf.max()
     op.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_colouring_probes_match_exact_diagonal_within_the_coupling_bound(precision):
+    """sylv_variance_probing (probes generated on the device from a distance colouring) against
+    the exact diagonal of a dense inverse: at every (source, pixel) the error lies within the
+    sum of the magnitudes of the G^{-1} entries between same-colour pixels (the estimator's
+    value is the diagonal plus those entries), it equals the oracle's estimator on the same
+    probes, and the largest error falls as the colouring distance grows."""
+    p = _problem("sphere", 12, 24, 4, 6, seed=21)
+    op = operator_for(p)
+    G = _G(p)
+    Ginv = np.linalg.inv(G.toarray())
+    exact = np.diag(Ginv).reshape(p.k, p.n)
+    slack = 1e-9 if precision == 0 else 1e-5            # solve tolerance
+    errs = []
+    for pc in (1, 2, 3, 4):
+        col = synth.grid_colouring(p.graph, pc)
+        var, info = op.variance_probing(col, pc * pc, tol=1e-11, precision=precision)
+        assert info["code"] == 0, info
+        est = var.cpu().numpy()[:, :p.n]
+        bound = np.empty_like(exact)
+        for j in range(p.k):
+            blk = np.abs(Ginv[j * p.n:(j + 1) * p.n, j * p.n:(j + 1) * p.n])
+            for i in range(p.n):
+                same = col == col[i]
+                bound[j, i] = blk[i, same].sum() - blk[i, i]
+        assert np.all(np.abs(est - exact) <= bound + slack * exact), pc
+        ref = variance.probe_diag(G, synth.colouring_probes(p.graph, p.k, pc))
+        assert np.abs(est - ref).max() <= slack * np.abs(ref).max(), pc
+        errs.append(np.abs(est - exact).max() / exact.max())
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    op.close()
+
+
+def test_colouring_out_of_range_is_refused():
+    import torch
+    from paper_2204_08057_gb300 import binding as Bn
+    p = _problem("sphere", 8, 12, 3, 5, seed=2)
+    op = operator_for(p)
+    col = synth.grid_colouring(p.graph, 2)
+    col[5] = 4                                            # outside [0, 4)
+    with pytest.raises(Bn.SylvError) as e:
+        op.variance_probing(col, 4, tol=1e-10)
+    assert e.value.code == Bn.SYLV_E_INVALID
+    op.close()

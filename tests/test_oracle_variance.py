@@ -56,3 +56,58 @@ def test_lattice_closed_form_and_unbiased_probes():
     # a plain power of the Laplacian in place of the prior's would not match
     cf2 = variance.lattice_homogeneous_diag(H, W, p.tau, p.kappa, A, p.D[:, 0], power=2)
     assert np.abs(cf2 - cf).max() > 1e-3 * cf.max()
+
+
+# ---- probing with a distance colouring of the grid (Tang and Saad's probing for the diagonal
+# of a matrix inverse): one 0/1 probe per (colour, source) ------------------------------------
+def test_grid_colouring_separates_same_colour_pixels():
+    """Brute force on small grids: any two distinct pixels of one colour are at least p steps
+    apart (unweighted shortest paths of the pixel graph), and every colour is used."""
+    import scipy.sparse.csgraph as csg
+    for g, p in ((synth.latlong_sphere(7, 12), 3), (synth.periodic_lattice(8, 8), 4),
+                 (synth.latlong_sphere(6, 8), 2), (synth.periodic_lattice(6, 9), 3)):
+        adj = model.laplacian_from_csr(g.rowptr, g.col, g.val, g.n).tocsr()
+        adj.data[:] = 1.0
+        dist = csg.shortest_path(adj, unweighted=True)
+        col = synth.grid_colouring(g, p)
+        assert sorted(set(col.tolist())) == list(range(p * p))
+        same = (col[:, None] == col[None, :]) & ~np.eye(g.n, dtype=bool)
+        assert dist[same].min() >= p, (g.kind, p)
+
+
+def test_colouring_probe_estimate_is_the_same_colour_sum():
+    """With colouring probes the estimator returns, at (j, i), the sum of the entries of G^{-1}
+    between (j, i) and every (j, i') of the same colour: the exact diagonal plus the
+    same-colour couplings.  Checked against a dense inverse; with one pixel per colour (every
+    probe a unit vector) it is the exact diagonal."""
+    p = _small("sphere", 6, 8, 3)
+    G = _G(p)
+    Ginv = np.linalg.inv(G.toarray())
+    for pc in (1, 2):
+        col = synth.grid_colouring(p.graph, pc)
+        est = variance.probe_diag(G, synth.colouring_probes(p.graph, p.k, pc))
+        ref = np.empty((p.k, p.n))
+        for j in range(p.k):
+            blk = Ginv[j * p.n:(j + 1) * p.n, j * p.n:(j + 1) * p.n]
+            ref[j] = np.array([blk[i, col == col[i]].sum() for i in range(p.n)])
+        assert np.abs(est - ref).max() <= 1e-12 * np.abs(ref).max(), pc
+    q = _small("sphere", 3, 4, 2)
+    Gq = _G(q)
+    est = variance.probe_diag(Gq, synth.colouring_probes(q.graph, q.k, 4))   # 12 colours
+    assert np.abs(est - variance.exact_diag(Gq, q.k, q.n)).max() <= 1e-12 * est.max()
+
+
+def test_probing_error_shrinks_with_distance():
+    """The error is the same-colour coupling, which decays with graph distance: the largest
+    error falls as the colouring distance grows, and from p = 2 every estimate is positive."""
+    p = _small("sphere", 8, 24, 3, seed=9)
+    G = _G(p)
+    ex = variance.exact_diag(G, p.k, p.n)
+    errs = []
+    for pc in (1, 2, 3, 4):
+        est = variance.probe_diag(G, synth.colouring_probes(p.graph, p.k, pc))
+        errs.append(np.abs(est - ex).max() / ex.max())
+        if pc >= 2:
+            assert np.all(est > 0), pc
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] <= 1e-2 * errs[0], errs
