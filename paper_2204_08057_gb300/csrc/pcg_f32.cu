@@ -191,9 +191,9 @@ cudaError_t apply_x_tma_impl(const OpData& op, const float* X, float* Y, int R, 
   static int grid = 0;
   const auto kern = V == 2 ? tma::k_apply_mc<K, M, E>
                            : (V == 1 ? tma::k_apply_tma_ops<K, M, E> : tma::k_apply_tma<K, M, E>);
+  constexpr size_t ring = (size_t)tma::NST_X * tma::ApplyXLayout<K, M, E>::STAGE_BYTES;
   const size_t smem = V == 2 ? tma::mc_applyx_smem<K, M, E>()
-                             : (V == 1 ? (size_t)tma::ApplyXOpsLayout<K, M, E>::SMEM
-                                       : (size_t)tma::NST_X * tma::ApplyXLayout<K, M, E>::STAGE_BYTES);
+                             : (V == 1 ? (size_t)tma::ApplyXOpsLayout<K, M, E>::SMEM : ring);
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -350,6 +350,26 @@ __device__ __forceinline__ void warp_accumulate(CtaShared<T, NV>& sh, int r,
   }
 }
 
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// The same as warp_accumulate for FP32 values: the 32 lanes are summed in FP32 (a fixed tree)
+// and lane 0 adds the warp's sum to the FP64 accumulator, so the FP64 unit (1/64 of the FP32
+// rate on this GPU) sees one conversion and one addition per warp instead of a tree per lane.
+template <typename T, int NV>
+__device__ __forceinline__ void warp_accumulate_f32(CtaShared<T, NV>& sh, int r,
+                                                    const float (&v)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const float s = warp_sum_f32(v[t]);
+    if (lane == 0) sh.wacc[r][warp][t] += double(s);
+  }
+}
+
 // Column state after an inner operator kernel with total p . q: alpha, or the end of the inner
 // solve (exact solution reached, or breakdown).  `count` keeps the active/unfinished counters.
 __device__ __forceinline__ void after_apply(ColState& cs, double pq, Control* ctl, bool count) {
@@ -564,8 +584,13 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
           pq += pj * qj;
         }
       }
-      const double v[1] = {double(pq)};
-      warp_accumulate<T, 1>(sh, r, v);
+      if constexpr (sizeof(T) == 4) {
+        const float v[1] = {float(pq)};
+        warp_accumulate_f32<T, 1>(sh, r, v);
+      } else {
+        const double v[1] = {double(pq)};
+        warp_accumulate<T, 1>(sh, r, v);
+      }
     }
   }
   double tot[RMAX][1];
@@ -649,8 +674,13 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
           rr += ri[j] * ri[j];
         }
       }
-      const double v[2] = {double(rz), double(rr)};
-      warp_accumulate<T, 2>(sh, r, v);
+      if constexpr (sizeof(T) == 4) {
+        const float v[2] = {float(rz), float(rr)};
+        warp_accumulate_f32<T, 2>(sh, r, v);
+      } else {
+        const double v[2] = {double(rz), double(rr)};
+        warp_accumulate<T, 2>(sh, r, v);
+      }
     }
   }
   double tot[RMAX][2];

@@ -32,8 +32,8 @@ namespace tma {
 
 constexpr int MC_NOP = 2;   // operator slots
 constexpr int MC_NVS = 3;   // vector stages of the inner kernels (18-24 KB each)
-constexpr int MC_NVS_X = 8; // vector stages of the stand-alone apply (k rows, 4-8 KB each: a
-                            // deeper ring keeps as many bytes in flight)
+constexpr int MC_NVS_X = 5; // vector stages of the stand-alone apply (2k rows each: two
+                            // columns per unit, so a warp keeps both columns' gathers in flight)
 
 template <int NVS = MC_NVS>
 struct McPipe {
@@ -67,10 +67,10 @@ __device__ __forceinline__ void mc_init(McPipe<NVS>& mp) {
 // result is broadcast to the warp.  false: give up (timeout, or the consumers gave up).
 template <int NVS>
 __device__ __forceinline__ bool mc_wait_release(McPipe<NVS>& mp, uint64_t* bar,
-                                                uint32_t parity) {
+                                                uint32_t parity, long long budget) {
   const int lane = threadIdx.x & 31;
   bool ok = true;
-  if (lane == 0) ok = mbar_wait_bounded(bar, parity);
+  if (lane == 0) ok = mbar_wait_bounded(bar, parity, budget);
   ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
   if (!ok || mp.bad) {
     if (lane == 0) mp.bad = 1;
@@ -88,14 +88,16 @@ __device__ __forceinline__ void mc_produce(McPipe<NVS>& mp, unsigned char* opbuf
                                            int op_bytes,
                                            unsigned char* vecbuf, int vec_bytes,
                                            NextTile&& next_tile, OpIssue&& op_issue,
-                                           VecIssue&& vec_issue) {
+                                           VecIssue&& vec_issue,
+                                           long long budget = WAIT_BUDGET_CYCLES) {
   const int lane = threadIdx.x & 31;
   const int na = mp.nact;
   int u = 0;
   for (int lt = 0;; ++lt) {
     const int tile = next_tile(lt);
     const int os = lt % MC_NOP;
-    if (lt >= MC_NOP && !mc_wait_release(mp, &mp.oempty[os], ((lt / MC_NOP) - 1) & 1)) return;
+    if (lt >= MC_NOP && !mc_wait_release(mp, &mp.oempty[os], ((lt / MC_NOP) - 1) & 1, budget))
+      return;
     if (lane == 0) mp.otile[os] = tile;
     __syncwarp();
     if (tile < 0) {
@@ -110,7 +112,8 @@ __device__ __forceinline__ void mc_produce(McPipe<NVS>& mp, unsigned char* opbuf
     if (lane == 0) mp.o_issued = lt + 1;
     for (int a = 0; a < na; ++a, ++u) {
       const int vs = u % NVS;
-      if (u >= NVS && !mc_wait_release(mp, &mp.vempty[vs], ((u / NVS) - 1) & 1)) return;
+      if (u >= NVS && !mc_wait_release(mp, &mp.vempty[vs], ((u / NVS) - 1) & 1, budget))
+        return;
       fence_proxy_async();
       vec_issue(tile, mp.cols[a], vecbuf + (size_t)vs * vec_bytes, &mp.vfull[vs]);
       if (lane == 0) mp.v_issued = u + 1;
@@ -125,13 +128,14 @@ template <int NVS, typename OnTile, typename OnUnit>
 __device__ __forceinline__ void mc_consume(McPipe<NVS>& mp, const unsigned char* opbuf,
                                            int op_bytes,
                                            const unsigned char* vecbuf, int vec_bytes,
-                                           OnTile&& on_tile, OnUnit&& on_unit) {
+                                           OnTile&& on_tile, OnUnit&& on_unit,
+                                           long long budget = WAIT_BUDGET_CYCLES) {
   const int lane = threadIdx.x & 31;
   const int na = mp.nact;
   int u = 0;
   for (int lt = 0;; ++lt) {
     const int os = lt % MC_NOP;
-    if (!mbar_wait_bounded(&mp.ofull[os], (lt / MC_NOP) & 1) || mp.bad) {
+    if (!mbar_wait_bounded(&mp.ofull[os], (lt / MC_NOP) & 1, budget) || mp.bad) {
       mp.bad = 1;
       return;
     }
@@ -142,7 +146,7 @@ __device__ __forceinline__ void mc_consume(McPipe<NVS>& mp, const unsigned char*
     if (lane == 0) mbar_arrive(&mp.oempty[os]);
     for (int a = 0; a < na; ++a, ++u) {
       const int vs = u % NVS;
-      if (!mbar_wait_bounded(&mp.vfull[vs], (u / NVS) & 1) || mp.bad) {
+      if (!mbar_wait_bounded(&mp.vfull[vs], (u / NVS) & 1, budget) || mp.bad) {
         mp.bad = 1;
         return;
       }
@@ -237,44 +241,64 @@ __device__ __forceinline__ void load_pixel_op(const CtaShared<float, NV>& sh, co
   }
 }
 
-// w = G z at the pixel for one column: zi the pixel's values (from the stage), sz the stage's
-// z rows (stride TILE_PX), zg the column's vector in global memory (stride ld).
+// w = G z at the pixel for UC columns at once (all their neighbour loads issued before any
+// arithmetic): zi the pixel's values (from the stages), sz the stages' z rows (stride
+// TILE_PX), zg the columns' vectors in global memory (stride ld).
+template <int K, int E, int UC, int NV>
+__device__ __forceinline__ void pixel_apply_mcn(const CtaShared<float, NV>& sh,
+                                                const PixelOp<K, E>& po,
+                                                const float* const (&sz)[UC],
+                                                const float* const (&zg)[UC], int64_t ld,
+                                                const float (&zi)[UC][K], float (&w)[UC][K]) {
+  float nb[UC][E][K];
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const bool in = (po.in_tile >> e) & 1u;
+      const float* src = in ? sz[u] + po.c[e] : zg[u] + po.c[e];
+      const int64_t stride = in ? (int64_t)TILE_PX : ld;
+#pragma unroll
+      for (int j = 0; j < K; ++j) nb[u][e][j] = src[j * stride];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+    float lap[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) lap[j] = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int j = 0; j < K; ++j) lap[j] += po.v[e] * nb[u][e][j];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[u][j] = sh.tau[j] * lap[j];
+#pragma unroll
+    for (int x = 0; x < K; ++x) {
+#pragma unroll
+      for (int y = 0; y <= x; ++y) {
+        const float pxy = po.P[x * (x + 1) / 2 + y];
+        w[u][x] += pxy * zi[u][y];
+        if (y != x) w[u][y] += pxy * zi[u][x];
+      }
+    }
+  }
+}
+
+// The same for one column.
 template <int K, int E, int NV>
 __device__ __forceinline__ void pixel_apply_mc(const CtaShared<float, NV>& sh,
                                                const PixelOp<K, E>& po, const float* sz,
                                                const float* zg, int64_t ld,
                                                const float (&zi)[K], float (&w)[K]) {
-  const float* src[E];
-  int64_t stride[E];
+  const float* const szs[1] = {sz};
+  const float* const zgs[1] = {zg};
+  float zi1[1][K], w1[1][K];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const bool in = (po.in_tile >> e) & 1u;
-    src[e] = in ? sz + po.c[e] : zg + po.c[e];
-    stride[e] = in ? (int64_t)TILE_PX : ld;
-  }
-  float nb[E][K];
+  for (int j = 0; j < K; ++j) zi1[0][j] = zi[j];
+  pixel_apply_mcn<K, E, 1, NV>(sh, po, szs, zgs, ld, zi1, w1);
 #pragma unroll
-  for (int e = 0; e < E; ++e)
-#pragma unroll
-    for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
-  float lap[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) lap[j] = 0.f;
-#pragma unroll
-  for (int e = 0; e < E; ++e)
-#pragma unroll
-    for (int j = 0; j < K; ++j) lap[j] += po.v[e] * nb[e][j];
-#pragma unroll
-  for (int j = 0; j < K; ++j) w[j] = sh.tau[j] * lap[j];
-#pragma unroll
-  for (int x = 0; x < K; ++x) {
-#pragma unroll
-    for (int y = 0; y <= x; ++y) {
-      const float pxy = po.P[x * (x + 1) / 2 + y];
-      w[x] += pxy * zi[y];
-      if (y != x) w[y] += pxy * zi[x];
-    }
-  }
+  for (int j = 0; j < K; ++j) w[j] = w1[0][j];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -337,32 +361,34 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
   unsigned char* vecbuf = dsm + (size_t)MC_NOP * OR::BYTES;
   const int warp = threadIdx.x >> 5;
   if (warp == NCONS) {
-    mc_produce(
-        mp, opbuf, OR::BYTES, vecbuf, VR::BYTES,
-        [&](int lt) {
-          const int tile = cr.slot + lt * nsl;
-          return tile < sd.ntiles ? tile : -1;
-        },
-        [&](int tile, unsigned char* slot, uint64_t* bar) {
-          const int64_t base = (int64_t)tile * TILE_PX;
-          issue_rows(reinterpret_cast<float*>(slot), OR::ROWS, bar, [&](int q) -> const void* {
-            if (q < OR::VAL) return op.D32 + (size_t)(q - OR::D) * ld + base;
-            if (q < OR::DIAG) return op.ell_val32 + (size_t)(q - OR::VAL) * ld + base;
-            if (q == OR::DIAG) return op.diag32 + base;
-            return op.ell_col + (size_t)(q - OR::COL) * ld + base;
-          });
-        },
-        [&](int tile, int r, unsigned char* stage, uint64_t* bar) {
-          const int64_t base = (int64_t)tile * TILE_PX;
-          const size_t voff = (size_t)r * K * ld;
-          const bool first = sh.aux[r] != 0;   // p and q are not read on a first iteration
-          issue_rows(reinterpret_cast<float*>(stage), first ? K : VR::ROWS, bar,
-                     [&](int q) -> const void* {
-                       if (q < K) return zg + voff + (size_t)q * ld + base;
-                       if (q < 2 * K) return pg + voff + (size_t)(q - K) * ld + base;
-                       return qg + voff + (size_t)(q - 2 * K) * ld + base;
-                     });
-        });
+    if (!(ctl->inject_stall & STALL_APPLY))
+      mc_produce(
+          mp, opbuf, OR::BYTES, vecbuf, VR::BYTES,
+          [&](int lt) {
+            const int tile = cr.slot + lt * nsl;
+            return tile < sd.ntiles ? tile : -1;
+          },
+          [&](int tile, unsigned char* slot, uint64_t* bar) {
+            const int64_t base = (int64_t)tile * TILE_PX;
+            issue_rows(reinterpret_cast<float*>(slot), OR::ROWS, bar, [&](int q) -> const void* {
+              if (q < OR::VAL) return op.D32 + (size_t)(q - OR::D) * ld + base;
+              if (q < OR::DIAG) return op.ell_val32 + (size_t)(q - OR::VAL) * ld + base;
+              if (q == OR::DIAG) return op.diag32 + base;
+              return op.ell_col + (size_t)(q - OR::COL) * ld + base;
+            });
+          },
+          [&](int tile, int r, unsigned char* stage, uint64_t* bar) {
+            const int64_t base = (int64_t)tile * TILE_PX;
+            const size_t voff = (size_t)r * K * ld;
+            const bool first = sh.aux[r] != 0;   // p and q are not read on a first iteration
+            issue_rows(reinterpret_cast<float*>(stage), first ? K : VR::ROWS, bar,
+                       [&](int q) -> const void* {
+                         if (q < K) return zg + voff + (size_t)q * ld + base;
+                         if (q < 2 * K) return pg + voff + (size_t)(q - K) * ld + base;
+                         return qg + voff + (size_t)(q - 2 * K) * ld + base;
+                       });
+          },
+          pipe_budget(ctl));
   } else {
     const int t = threadIdx.x;
     PixelOp<K, E> po;
@@ -403,9 +429,10 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
               pq += pn[j] * qn[j];
             }
           }
-          const double v1[1] = {double(pq)};
-          warp_accumulate<float, 1>(sh, r, v1);
-        });
+          const float v1[1] = {pq};
+          warp_accumulate_f32<float, 1>(sh, r, v1);
+        },
+        pipe_budget(ctl));
   }
   if (mc_failed(mp, &ctl->error)) return;
   double tot[RMAX][1];
@@ -480,31 +507,33 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   unsigned char* vecbuf = dsm + (size_t)MC_NOP * L::OP_BYTES;
   const int warp = threadIdx.x >> 5;
   if (warp == NCONS) {
-    mc_produce(
-        mp, opbuf, L::OP_BYTES, vecbuf, L::VEC_BYTES,
-        [&](int lt) {
-          const int tile = cr.slot + lt * nsl;
-          return tile < sd.ntiles ? tile : -1;
-        },
-        [&](int tile, unsigned char* slot, uint64_t* bar) {
-          const int64_t base = (int64_t)tile * TILE_PX;
-          issue_rows(reinterpret_cast<float*>(slot), prec ? L::OP_ROWS : 0, bar,
-                     [&](int q) -> const void* {
-                       if (q < K) return op.fs32 + (size_t)q * ld + base;
-                       return op.fl16 + (size_t)(q - K) * ld + base;
-                     });
-        },
-        [&](int tile, int r, unsigned char* stage, uint64_t* bar) {
-          const int64_t base = (int64_t)tile * TILE_PX;
-          const size_t voff = (size_t)r * K * ld;
-          issue_rows(reinterpret_cast<float*>(stage), L::VEC_ROWS, bar,
-                     [&](int q) -> const void* {
-                       if (q < K) return dgl + voff + (size_t)q * ld + base;
-                       if (q < 2 * K) return pg + voff + (size_t)(q - K) * ld + base;
-                       if (q < 3 * K) return rg + voff + (size_t)(q - 2 * K) * ld + base;
-                       return qg + voff + (size_t)(q - 3 * K) * ld + base;
-                     });
-        });
+    if (!(ctl->inject_stall & STALL_UPDATE))
+      mc_produce(
+          mp, opbuf, L::OP_BYTES, vecbuf, L::VEC_BYTES,
+          [&](int lt) {
+            const int tile = cr.slot + lt * nsl;
+            return tile < sd.ntiles ? tile : -1;
+          },
+          [&](int tile, unsigned char* slot, uint64_t* bar) {
+            const int64_t base = (int64_t)tile * TILE_PX;
+            issue_rows(reinterpret_cast<float*>(slot), prec ? L::OP_ROWS : 0, bar,
+                       [&](int q) -> const void* {
+                         if (q < K) return op.fs32 + (size_t)q * ld + base;
+                         return op.fl16 + (size_t)(q - K) * ld + base;
+                       });
+          },
+          [&](int tile, int r, unsigned char* stage, uint64_t* bar) {
+            const int64_t base = (int64_t)tile * TILE_PX;
+            const size_t voff = (size_t)r * K * ld;
+            issue_rows(reinterpret_cast<float*>(stage), L::VEC_ROWS, bar,
+                       [&](int q) -> const void* {
+                         if (q < K) return dgl + voff + (size_t)q * ld + base;
+                         if (q < 2 * K) return pg + voff + (size_t)(q - K) * ld + base;
+                         if (q < 3 * K) return rg + voff + (size_t)(q - 2 * K) * ld + base;
+                         return qg + voff + (size_t)(q - 3 * K) * ld + base;
+                       });
+          },
+          pipe_budget(ctl));
   } else {
     const int t = threadIdx.x;
     BlockChol<K, float> f;
@@ -555,9 +584,10 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
               rr += ri[j] * ri[j];
             }
           }
-          const double v2[2] = {double(rz), double(rr)};
-          warp_accumulate<float, 2>(sh, r, v2);
-        });
+          const float v2[2] = {rz, rr};
+          warp_accumulate_f32<float, 2>(sh, r, v2);
+        },
+        pipe_budget(ctl));
   }
   if (mc_failed(mp, &ctl->error)) return;
   double tot[RMAX][2];
@@ -578,7 +608,7 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
 // multiple of TILE_PX and every caller row starts 16-byte aligned.
 template <int K>
 struct McXVec {
-  static constexpr int BYTES = K * TILE_PX * 4;
+  static constexpr int BYTES = 2 * K * TILE_PX * 4;   // x rows of a column pair
 };
 
 template <int K, int M, int E>
@@ -595,9 +625,10 @@ k_apply_mc(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R,
   __shared__ CtaShared<float, 1> sh;
   __shared__ __align__(8) McPipe<MC_NVS_X> mp;
   stage_operator<float, 1>(op, K, sh);
+  const int npair = (R + 1) / 2;   // a unit is a pair of columns (the last may be single)
   if (threadIdx.x == 0) {
-    for (int r = 0; r < R; ++r) mp.cols[r] = r;
-    mp.nact = R;
+    for (int a = 0; a < npair; ++a) mp.cols[a] = a;
+    mp.nact = npair;
     mc_init(mp);
   }
   __syncthreads();
@@ -626,10 +657,11 @@ k_apply_mc(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R,
             return op.ell_col + (size_t)(q - OR::COL) * ld + base;
           });
         },
-        [&](int tile, int r, unsigned char* stage, uint64_t* bar) {
+        [&](int tile, int a, unsigned char* stage, uint64_t* bar) {
           const int64_t base = (int64_t)tile * TILE_PX;
-          const size_t xoff = (size_t)r * K * ldu;
-          issue_rows(reinterpret_cast<float*>(stage), K, bar, [&](int q) -> const void* {
+          const int nc = 2 * a + 1 < R ? 2 : 1;
+          const size_t xoff = (size_t)(2 * a) * K * ldu;   // the pair's K or 2K rows follow
+          issue_rows(reinterpret_cast<float*>(stage), nc * K, bar, [&](int q) -> const void* {
             return X + xoff + (size_t)q * ldu + base;
           });
         });
@@ -643,16 +675,25 @@ k_apply_mc(OpData op, const float* __restrict__ X, float* __restrict__ Y, int R,
           base = (int64_t)tile * TILE_PX;
           load_pixel_op<K, M, E>(sh, reinterpret_cast<const float*>(slot), t, base, po);
         },
-        [&](int tile, int r, const unsigned char* stage_b, auto&& release) {
+        [&](int tile, int a, const unsigned char* stage_b, auto&& release) {
           const float* stage = reinterpret_cast<const float*>(stage_b);
-          const size_t xoff = (size_t)r * K * ldu;
-          float xi[K], w[K];
+          const bool two = 2 * a + 1 < R;   // a single last column is computed twice
+          const size_t x0 = (size_t)(2 * a) * K * ldu, x1 = two ? x0 + (size_t)K * ldu : x0;
+          const float* const sz[2] = {stage, two ? stage + (size_t)K * TILE_PX : stage};
+          const float* const zg[2] = {X + x0, X + x1};
+          float xi[2][K], w[2][K];
 #pragma unroll
-          for (int j = 0; j < K; ++j) xi[j] = stage[j * TILE_PX + t];
-          pixel_apply_mc<K, E>(sh, po, stage, X + xoff, ldu, xi, w);
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int j = 0; j < K; ++j) xi[u][j] = sz[u][j * TILE_PX + t];
+          pixel_apply_mcn<K, E, 2>(sh, po, sz, zg, ldu, xi, w);
           release();
 #pragma unroll
-          for (int j = 0; j < K; ++j) Y[xoff + (size_t)j * ldu + base + t] = w[j];
+          for (int j = 0; j < K; ++j) Y[x0 + (size_t)j * ldu + base + t] = w[0][j];
+          if (two) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) Y[x1 + (size_t)j * ldu + base + t] = w[1][j];
+          }
         });
   }
   const bool bad = mc_failed(mp, ctr);

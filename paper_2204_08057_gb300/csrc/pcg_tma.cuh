@@ -75,13 +75,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Waits for the phase of the given parity, for at most `budget` SM clock cycles.  The waits of
+// a pipeline (a stage to fill or to be released) take the kernel's budget (Control::
+// wait_budget, shortened only to test the timeout path); the waits that drain copies already
+// in flight before a CTA leaves keep the full default, so no copy outlives its CTA.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long budget = WAIT_BUDGET_CYCLES) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > WAIT_BUDGET_CYCLES) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
+}
+
+// The pipeline wait budget of a kernel launched with this control word.
+__device__ __forceinline__ long long pipe_budget(const Control* ctl) {
+  const long long b = ctl->wait_budget;
+  return b > 0 ? b : WAIT_BUDGET_CYCLES;
 }
 
 // Units of a CTA: its tiles (slot, slot + nslots, ...) times its active columns; unit u is
@@ -131,13 +142,14 @@ __device__ __forceinline__ void pipe_init(PipeShared& ps) {
 // Producer loop over units u0 .. u1 - 1: waits for stage release (from the second round of the
 // ring on), then issues unit u with issue(u, stage).
 template <typename Issue>
-__device__ __forceinline__ void producer_loop_range(PipeShared& ps, int u0, int u1, Issue&& issue) {
+__device__ __forceinline__ void producer_loop_range(PipeShared& ps, int u0, int u1, Issue&& issue,
+                                                    long long budget = WAIT_BUDGET_CYCLES) {
   const int lane = threadIdx.x & 31;
   for (int u = u0; u < u1; ++u) {
     const int st = u % NSTAGE;
     if (u >= NSTAGE) {
       bool ok = true;
-      if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NSTAGE) - 1) & 1);
+      if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NSTAGE) - 1) & 1, budget);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       if (!ok || ps.bad) {
         if (lane == 0) ps.bad = 1;
@@ -404,7 +416,8 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
     // consumers apply the previous update's state change (which keeps p, q and first as they are)
     head = U.n < NSTAGE ? U.n : NSTAGE;
     if (warp == NCONS) {
-      producer_loop_range(ps, 0, head, issue);
+      if (!(ctl->inject_stall & STALL_APPLY))
+        producer_loop_range(ps, 0, head, issue, pipe_budget(ctl));
     } else if (mode == 2) {
       sum_slots<2>(sd.partial2, sd.nslots[1], R, sh.act, sh.red, tot2);
       if (threadIdx.x < R && sh.act[threadIdx.x]) {
@@ -441,13 +454,14 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   }
 
   if (warp == NCONS) {
-    producer_loop_range(ps, head, U.n, issue);
+    if (!(ctl->inject_stall & STALL_APPLY))
+      producer_loop_range(ps, head, U.n, issue, pipe_budget(ctl));
   } else {
     const int t = threadIdx.x;
-    double acc = 0.0;
+    float acc = 0.f;   // this thread's p . q over its units of one column (FP32)
     for (int u = 0; u < U.n; ++u) {
       const int st = u % NSTAGE;
-      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1, pipe_budget(ctl)) || ps.bad) {
         ps.bad = 1;
         break;
       }
@@ -504,11 +518,11 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       __syncwarp();
       if (lane == 0) mbar_arrive(&ps.empty[st]);
       consumed = u + 1;
-      acc += double(pq);
+      acc += pq;
       if (U.nact > 1 || u + 1 == U.n) {
-        const double v1[1] = {acc};
-        warp_accumulate<float, 1>(sh, r, v1);
-        acc = 0.0;
+        const float v1[1] = {acc};
+        warp_accumulate_f32<float, 1>(sh, r, v1);
+        acc = 0.f;
       }
     }
   }
@@ -612,7 +626,8 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
     // consumers form alpha from the operator kernel's partial sums
     head = U.n < NSTAGE ? U.n : NSTAGE;
     if (warp == NCONS) {
-      producer_loop_range(ps, 0, head, issue);
+      if (!(ctl->inject_stall & STALL_UPDATE))
+        producer_loop_range(ps, 0, head, issue, pipe_budget(ctl));
     } else if (mode == 2) {
       sum_slots<1>(sd.partial, sd.nslots[0], R, sh.act, sh.red, tot1);
       if (threadIdx.x < R && sh.act[threadIdx.x]) {
@@ -649,13 +664,14 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
   }
 
   if (warp == NCONS) {
-    producer_loop_range(ps, head, U.n, issue);
+    if (!(ctl->inject_stall & STALL_UPDATE))
+      producer_loop_range(ps, head, U.n, issue, pipe_budget(ctl));
   } else {
     const int t = threadIdx.x;
-    double acc_rz = 0.0, acc_rr = 0.0;
+    float acc_rz = 0.f, acc_rr = 0.f;   // over this thread's units of one column (FP32)
     for (int u = 0; u < U.n; ++u) {
       const int st = u % NSTAGE;
-      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1, pipe_budget(ctl)) || ps.bad) {
         ps.bad = 1;
         break;
       }
@@ -701,12 +717,12 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
           rr += ri[j] * ri[j];
         }
       }
-      acc_rz += double(rz);
-      acc_rr += double(rr);
+      acc_rz += rz;
+      acc_rr += rr;
       if (U.nact > 1 || u + 1 == U.n) {
-        const double v2[2] = {acc_rz, acc_rr};
-        warp_accumulate<float, 2>(sh, r, v2);
-        acc_rz = acc_rr = 0.0;
+        const float v2[2] = {acc_rz, acc_rr};
+        warp_accumulate_f32<float, 2>(sh, r, v2);
+        acc_rz = acc_rr = 0.f;
       }
     }
   }
@@ -791,7 +807,7 @@ k_residual_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
   int consumed = 0;
 
   if (warp == NCONS) {
-    producer_loop_range(ps, 0, U.n, [&](int u, int st) {
+    producer_loop_range(ps, 0, (ctl->inject_stall & STALL_RESIDUAL) ? 0 : U.n, [&](int u, int st) {
       const int tile = cr.slot + (u / U.nact) * sd.nslots[3];
       const int r = ps.cols[u % U.nact];
       const bool noop = x0_zero && sh.aux[r] == PH_START;   // X = 0: no operator term
@@ -840,13 +856,13 @@ k_residual_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
         }
         if (src) bulk_load(dst, src, nb, &ps.full[st]);
       }
-    });
+    }, pipe_budget(ctl));
   } else {
     const int t = threadIdx.x;
     double a_rr64 = 0.0, a_bb = 0.0, a_rz = 0.0, a_rr = 0.0;
     for (int u = 0; u < U.n; ++u) {
       const int st = u % NSTAGE;
-      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1, pipe_budget(ctl)) || ps.bad) {
         ps.bad = 1;
         break;
       }

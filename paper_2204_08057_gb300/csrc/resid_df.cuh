@@ -201,7 +201,7 @@ k_residual_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
         }
       }
       if (!ok && valid) pixel_residual_f64<K, E, 4>(op, sh, X, B, ldu, i, with_op, rh, rl);
-      double rr64 = 0.0, bb = 0.0, rz = 0.0, rr = 0.0;
+      float rr64 = 0.f, bb = 0.f, rz = 0.f, rr = 0.f;   // (FP32 partials, FP64 across warps)
       if (valid) {
         float ri[K], zi[K];
         float rr_px = 0.f, bb_px = 0.f;
@@ -211,18 +211,8 @@ k_residual_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
           rr_px = fmaf(rh[j], rh[j], fmaf(2.f * rh[j], rl[j], rr_px));
           bb_px = fmaf(bh[j], bh[j], bb_px);
         }
-        rr64 = double(rr_px);
-        if (sh.aux[r] == PH_START) bb = double(bb_px);   // ||B||^2: first residual only
-        if (!isfinite(rr_px) || !isfinite(bb_px)) {      // FP32 overflow: the sums in FP64
-          rr64 = bb = 0.0;
-#pragma unroll
-          for (int j = 0; j < K; ++j) {
-            const double rj = double(rh[j]) + double(rl[j]), bj = double(bh[j]) + double(bl[j]);
-            rr64 += rj * rj;
-            bb += bj * bj;
-          }
-          if (sh.aux[r] != PH_START) bb = 0.0;
-        }
+        rr64 = rr_px;
+        if (sh.aux[r] == PH_START) bb = bb_px;   // ||B||^2: first residual only
         {
           float* rv = (float*)sd.vr + off;
           float* dv = (float*)sd.vd + off;
@@ -242,12 +232,12 @@ k_residual_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
             rzt += ri[j] * zi[j];
             rrt += ri[j] * ri[j];
           }
-          rz = double(rzt);
-          rr = double(rrt);
+          rz = rzt;
+          rr = rrt;
         }
       }
-      const double v[4] = {rr64, bb, rz, rr};
-      warp_accumulate<double, 4>(sh, r, v);
+      const float v[4] = {rr64, bb, rz, rr};
+      warp_accumulate_f32<double, 4>(sh, r, v);
     }
   }
   double tot[RMAX][4];
@@ -322,7 +312,7 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   int consumed = 0;
 
   if (warp == NCONS) {
-    producer_loop_range(ps, 0, U.n, [&](int u, int st) {
+    producer_loop_range(ps, 0, (ctl->inject_stall & STALL_RESIDUAL) ? 0 : U.n, [&](int u, int st) {
       const int tile = cr.slot + (u / U.nact) * sd.nslots[3];
       const int r = ps.cols[u % U.nact];
       const bool noop = x0_zero && sh.aux[r] == PH_START;   // X = 0: no operator term
@@ -375,14 +365,17 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
         }
         if (src) bulk_load(dst, src, nbytes, &ps.full[st]);
       }
-    });
+    }, pipe_budget(ctl));
   } else {
     const int t = threadIdx.x;
-    double a_rr64 = 0.0, a_bb = 0.0, a_rz = 0.0, a_rr = 0.0;
+    // ||r||^2, ||B||^2, r . z, r . r over this thread's units of one column: sums of FP32
+    // products in FP32 (a stopping test needs a few digits; the sums of squares cannot cancel),
+    // FP64 across warps and CTAs
+    float a_rr64 = 0.f, a_bb = 0.f, a_rz = 0.f, a_rr = 0.f;
     int buffered = 0;   // units that used the split-x tile buffer so far
     for (int u = 0; u < U.n; ++u) {
       const int st = u % NSTAGE;
-      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1) || ps.bad) {
+      if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1, pipe_budget(ctl)) || ps.bad) {
         ps.bad = 1;
         break;
       }
@@ -420,7 +413,7 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
         // give up after the wait budget instead of blocking)
         __syncwarp();
         if (lane == 0) mbar_arrive(&cbar);
-        if (!mbar_wait_bounded(&cbar, buffered & 1) || ps.bad) {
+        if (!mbar_wait_bounded(&cbar, buffered & 1, pipe_budget(ctl)) || ps.bad) {
           ps.bad = 1;
           break;
         }
@@ -442,7 +435,8 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
             }
           } else {
 #pragma unroll
-            for (int j = 0; j < K; ++j) ok &= df::split(Xg[(size_t)j * ldu + c], nh[e][j], nl[e][j]);
+            for (int j = 0; j < K; ++j)
+              ok &= df::split(Xg[(size_t)j * ldu + c], nh[e][j], nl[e][j]);
           }
         }
 #pragma unroll
@@ -509,21 +503,11 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       __syncwarp();
       if (lane == 0) mbar_arrive(&ps.empty[st]);
       consumed = u + 1;
-      double rr64 = 0.0, bb = 0.0;
+      float rr64 = 0.f, bb = 0.f;
       float rzt = 0.f, rrt = 0.f;   // products in the inner type, like the inner kernels
       if (i < n) {
-        rr64 = double(rr_px);
-        if (sh.aux[r] == PH_START) bb = double(bb_px);   // ||B||^2: first residual only
-        if (!isfinite(rr_px) || !isfinite(bb_px)) {      // FP32 overflow: the sums in FP64
-          rr64 = bb = 0.0;
-#pragma unroll
-          for (int j = 0; j < K; ++j) {
-            const double rj = double(rh[j]) + double(rl[j]), bj = double(bh[j]) + double(bl[j]);
-            rr64 += rj * rj;
-            bb += bj * bj;
-          }
-          if (sh.aux[r] != PH_START) bb = 0.0;
-        }
+        rr64 = rr_px;
+        if (sh.aux[r] == PH_START) bb = bb_px;   // ||B||^2: first residual only
         float* rv = (float*)sd.vr + off;
         float* dv = (float*)sd.vd + off;
         float* zv = (float*)sd.vz + off;
@@ -538,12 +522,12 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       }
       a_rr64 += rr64;
       a_bb += bb;
-      a_rz += double(rzt);
-      a_rr += double(rrt);
+      a_rz += rzt;
+      a_rr += rrt;
       if (U.nact > 1 || u + 1 == U.n) {
-        const double v4[4] = {a_rr64, a_bb, a_rz, a_rr};
-        warp_accumulate<double, 4>(sh, r, v4);
-        a_rr64 = a_bb = a_rz = a_rr = 0.0;
+        const float v4[4] = {a_rr64, a_bb, a_rz, a_rr};
+        warp_accumulate_f32<double, 4>(sh, r, v4);
+        a_rr64 = a_bb = a_rz = a_rr = 0.f;
       }
     }
   }

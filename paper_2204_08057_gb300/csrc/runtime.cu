@@ -717,6 +717,12 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
   c.max_outer = o.max_outer;
   c.precond = o.precond;
   c.x0_zero = o.use_x0 ? 0 : 1;
+  // SYLV_WAIT_BUDGET_CYCLES shortens the staged kernels' pipeline waits (tests of the timeout
+  // path; the waits that drain copies in flight keep the default)
+  if (const char* wb = std::getenv("SYLV_WAIT_BUDGET_CYCLES")) c.wait_budget = std::atoll(wb);
+  // SYLV_INJECT_STALL=bits makes the named staged kernels' producers issue nothing (tests of
+  // the timeout path: a wait that nothing completes runs out; no copy is ever in flight)
+  if (const char* is = std::getenv("SYLV_INJECT_STALL")) c.inject_stall = std::atoi(is);
   const int iters = o.check_every > 0 ? o.check_every : 16;
   const bool prof = o.profile != 0;
   double ms_apply = 0, ms_update = 0, ms_res = 0;
@@ -821,7 +827,8 @@ int run_plan(Plan& P, const double* const* B, double* const* X, const sylv_opts&
       else if (rs_staged[gi] == 1)
         CK(launch_residual_staged(g.k, g.m, g.e, g.ncta[3], P.d_desc, g.d_ctas[3], P.d_ctl, s));
       else
-        CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], P.d_ctl, s));
+        CK(launch_residual<T>(g.k, g.m, g.e, g.ncta[2], g.block, P.d_desc, g.d_ctas[2], P.d_ctl,
+                              s));
     }
     if (prof) CK(cudaEventRecord(P.evr1, s));
     launches += 2 * ng;

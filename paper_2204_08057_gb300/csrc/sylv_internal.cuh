@@ -129,7 +129,14 @@ struct Control {
   int max_outer;
   int precond;
   int x0_zero;                // X starts at zero: the first residual is B itself
+  long long wait_budget;      // SM clock cycles a staged kernel's pipeline wait may take before
+                              // it records SYLV_E_TIMEOUT; 0: the default (about a second)
+  int inject_stall;           // tests of the timeout path: the producer warps of the staged
+                              // kernels named by the bits (1 residual, 2 operator, 4 update)
+                              // issue no copies, so their consumers' first wait runs out
+  int pad_ctl;
 };
+enum : int { STALL_RESIDUAL = 1, STALL_APPLY = 2, STALL_UPDATE = 4 };
 
 struct CtaRef {
   int sys;   // system of this CTA (-1: idle, the CTA returns at once)

@@ -517,6 +517,41 @@ def test_autograd_reuses_one_handle_across_parameters():
     prob.close()
 
 
+@pytest.mark.parametrize("force,nrhs,stall", [
+    ("256,1,1,1", 1, 1),     # staged double-float residual
+    ("256,1,1,1", 1, 2),     # operator kernel, consumer-side sums
+    ("256,1,1,1", 2, 4),     # update kernel
+    ("256,1,2,2", 3, 2),     # multi-column operator kernel
+    ("256,1,2,2", 3, 4),     # multi-column update kernel
+])
+def test_expired_wait_returns_timeout_and_the_handle_recovers(force, nrhs, stall, monkeypatch):
+    """Failure detection without a device fault: a staged kernel whose producer issues nothing
+    (SYLV_INJECT_STALL, a flag set on the host) leaves its consumers waiting on a stage that
+    nothing fills; their bounded waits (budget cut to ~10 ms by SYLV_WAIT_BUDGET_CYCLES) run
+    out, the CTAs record the timeout and leave, and the solve returns SYLV_E_TIMEOUT.  The same
+    handle then solves correctly (the next solve's set-up resets the counters and column states
+    the aborted kernels left)."""
+    from paper_2204_08057_gb300 import binding as Bn
+    monkeypatch.setenv("SYLV_TUNE_FORCE", force)
+    p = small_problem("sphere", 16, 64, 6, 9, seed=51, nrhs=nrhs)   # whole tiles: staged
+    op = operator_for(p)
+    Xo, b = oracle_solution(p)
+    Bd = device_batch(b, p.n)
+    X, info = op.solve(Bd, tol=1e-11, precision=1)        # plan, tuner and kernels in place
+    assert info["code"] == 0
+    monkeypatch.setenv("SYLV_WAIT_BUDGET_CYCLES", "20000000")
+    monkeypatch.setenv("SYLV_INJECT_STALL", str(stall))
+    with pytest.raises(Bn.SylvError) as e:
+        op.solve(Bd, tol=1e-11, precision=1, check_every=2)
+    assert e.value.code == Bn.SYLV_E_TIMEOUT
+    assert "wait" in str(e.value)
+    monkeypatch.delenv("SYLV_INJECT_STALL")
+    monkeypatch.delenv("SYLV_WAIT_BUDGET_CYCLES")
+    X, info = op.solve(Bd, tol=1e-11, precision=1)
+    assert info["code"] == 0 and relerr(X.cpu().numpy()[:, :, :p.n], Xo) <= 1e-6
+    op.close()
+
+
 def test_single_pixel_and_isolated_pixels():
     """n = 1 (no neighbours, ELL width 0): G is the k x k block itself."""
     import torch
