@@ -75,6 +75,56 @@ __device__ __forceinline__ void sub_from(float bh, float bl, const Acc& g, float
   fast_two_sum(s, c, rh, rl);
 }
 
+// ---- the same on pairs of values, with the packed FP32 instructions of sm_100+
+// (add/mul/fma.rn.f32x2): lane by lane the same error-free transformations, half the
+// instructions.  a - b is formed as fma(b, -1, a): the product is exact, one rounding.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = sub2(s, a);
+  e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  e = sub2(b, sub2(s, a));
+}
+
+struct Acc2 {
+  float2 s, c;
+};
+
+__device__ __forceinline__ Acc2 zero2() {
+  return Acc2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+}
+
+// acc += (ah + al)(bh + bl) lane by lane (lo lo dropped)
+__device__ __forceinline__ void fma2(Acc2& acc, float2 ah, float2 al, float2 bh, float2 bl) {
+  const float2 p = __fmul2_rn(ah, bh);
+  float2 e = __ffma2_rn(ah, bh, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+  float2 s, t;
+  two_sum2(acc.s, p, s, t);
+  acc.s = s;
+  acc.c = __fadd2_rn(acc.c, __fadd2_rn(t, e));
+}
+
+__device__ __forceinline__ void norm2(const Acc2& a, float2& h, float2& l) {
+  fast_two_sum2(a.s, a.c, h, l);
+}
+
+__device__ __forceinline__ void sub_from2(float2 bh, float2 bl, const Acc2& g, float2& rh,
+                                          float2& rl) {
+  float2 s, t;
+  two_sum2(bh, make_float2(-g.s.x, -g.s.y), s, t);
+  const float2 c = sub2(__fadd2_rn(t, bl), g.c);
+  fast_two_sum2(s, c, rh, rl);
+}
+
 // Splits an FP64 value into h + l (see the header); returns false outside the valid range
 // (h, l are then meaningless).
 __device__ __forceinline__ bool split(double a, float& h, float& l) {

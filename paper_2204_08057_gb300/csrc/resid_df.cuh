@@ -28,6 +28,99 @@ struct DfTile {
   float l[K][TILE_PX];
 };
 
+// lap_j += v_e * x_{col_e, j} for a batch of EC neighbours (split values), all sources j; for an
+// even number of sources on pairs of sources with the packed instructions.
+template <int K, int EC>
+__device__ __forceinline__ void df_stencil(df::Acc (&lap)[K], const float (&vh)[EC],
+                                           const float (&vl)[EC], const float (&nh)[EC][K],
+                                           const float (&nl)[EC][K]) {
+  if constexpr (K % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < K / 2; ++q) {
+      df::Acc2 a{make_float2(lap[2 * q].s, lap[2 * q + 1].s),
+                 make_float2(lap[2 * q].c, lap[2 * q + 1].c)};
+#pragma unroll
+      for (int e = 0; e < EC; ++e)
+        df::fma2(a, make_float2(vh[e], vh[e]), make_float2(vl[e], vl[e]),
+                 make_float2(nh[e][2 * q], nh[e][2 * q + 1]),
+                 make_float2(nl[e][2 * q], nl[e][2 * q + 1]));
+      lap[2 * q] = df::Acc{a.s.x, a.c.x};
+      lap[2 * q + 1] = df::Acc{a.s.y, a.c.y};
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < EC; ++e)
+#pragma unroll
+      for (int j = 0; j < K; ++j) df::fma(lap[j], vh[e], vl[e], nh[e][j], nl[e][j]);
+  }
+}
+
+// r = b - (P x + tau o lap) at the pixel, normalised pairs; getp(q) gives the (hi, lo) of the
+// packed lower-triangle entry q of the pixel block.  false: a non-finite result.
+template <int K, typename GetP>
+__device__ __forceinline__ bool df_finish(const df::Acc (&lap)[K], const float (&xh)[K],
+                                          const float (&xl)[K], GetP&& getp,
+                                          const float* tau_h, const float* tau_l,
+                                          const float (&bh)[K], const float (&bl)[K],
+                                          float (&rh)[K], float (&rl)[K]) {
+  bool ok = true;
+  if constexpr (K % 2 == 0) {
+    // output pairs (2q, 2q + 1): sum over b of P_{2q+u, b} x_b, then tau o lap, then b - g
+#pragma unroll
+    for (int q = 0; q < K / 2; ++q) {
+      df::Acc2 g = df::zero2();
+#pragma unroll
+      for (int b = 0; b < K; ++b) {
+        const int a0 = 2 * q, a1 = 2 * q + 1;
+        const int q0 = a0 >= b ? a0 * (a0 + 1) / 2 + b : b * (b + 1) / 2 + a0;
+        const int q1 = a1 >= b ? a1 * (a1 + 1) / 2 + b : b * (b + 1) / 2 + a1;
+        float p0h, p0l, p1h, p1l;
+        getp(q0, p0h, p0l);
+        getp(q1, p1h, p1l);
+        df::fma2(g, make_float2(p0h, p1h), make_float2(p0l, p1l), make_float2(xh[b], xh[b]),
+                 make_float2(xl[b], xl[b]));
+      }
+      float2 lh, ll;
+      df::norm2(df::Acc2{make_float2(lap[2 * q].s, lap[2 * q + 1].s),
+                         make_float2(lap[2 * q].c, lap[2 * q + 1].c)},
+                lh, ll);
+      df::fma2(g, make_float2(tau_h[2 * q], tau_h[2 * q + 1]),
+               make_float2(tau_l[2 * q], tau_l[2 * q + 1]), lh, ll);
+      float2 r2h, r2l;
+      df::sub_from2(make_float2(bh[2 * q], bh[2 * q + 1]), make_float2(bl[2 * q], bl[2 * q + 1]),
+                    g, r2h, r2l);
+      rh[2 * q] = r2h.x;
+      rh[2 * q + 1] = r2h.y;
+      rl[2 * q] = r2l.x;
+      rl[2 * q + 1] = r2l.y;
+    }
+  } else {
+    df::Acc g[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) g[j] = df::zero();
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        float ph, pl;
+        getp(a * (a + 1) / 2 + b, ph, pl);
+        df::fma(g[a], ph, pl, xh[b], xl[b]);
+        if (b != a) df::fma(g[b], ph, pl, xh[a], xl[a]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      float lh, ll;
+      df::norm(lap[j], lh, ll);
+      df::fma(g[j], tau_h[j], tau_l[j], lh, ll);
+      df::sub_from(bh[j], bl[j], g[j], rh[j], rl[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j) ok &= isfinite(rh[j]) && isfinite(rl[j]);
+  return ok;
+}
+
 // r = b - G x at pixel i of one column in double-float; xh, xl: the pixel's own split x;
 // tile: the split x of the tile [base, base + tw) (in-tile neighbours), X: the column's FP64
 // vector (out-of-tile neighbours), bh, bl: the split b.  false: recompute in FP64.
@@ -69,33 +162,14 @@ __device__ __forceinline__ bool pixel_residual_df(const OpData& op, const float*
         for (int j = 0; j < K; ++j) ok &= df::split(X[(size_t)j * ldu + c], nh[t][j], nl[t][j]);
       }
     }
-#pragma unroll
-    for (int t = 0; t < EC; ++t)
-#pragma unroll
-      for (int j = 0; j < K; ++j) df::fma(lap[j], vh[t], vl[t], nh[t][j], nl[t][j]);
+    df_stencil<K, EC>(lap, vh, vl, nh, nl);
   }
-  df::Acc g[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) g[j] = df::zero();
-#pragma unroll
-  for (int a = 0; a < K; ++a) {
-#pragma unroll
-    for (int b = 0; b <= a; ++b) {
-      const int q = a * (a + 1) / 2 + b;
-      const float ph = __ldg(op.blk_hl + (size_t)q * ld + i);
-      const float pl = __ldg(op.blk_hl + (size_t)(NB + q) * ld + i);
-      df::fma(g[a], ph, pl, xh[b], xl[b]);
-      if (b != a) df::fma(g[b], ph, pl, xh[a], xl[a]);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    float lh, ll;
-    df::norm(lap[j], lh, ll);
-    df::fma(g[j], tau_h[j], tau_l[j], lh, ll);
-    df::sub_from(bh[j], bl[j], g[j], rh[j], rl[j]);
-    ok &= isfinite(rh[j]) && isfinite(rl[j]);
-  }
+  ok &= df_finish<K>(lap, xh, xl,
+                     [&](int q, float& ph, float& pl) {
+                       ph = __ldg(op.blk_hl + (size_t)q * ld + i);
+                       pl = __ldg(op.blk_hl + (size_t)(NB + q) * ld + i);
+                     },
+                     tau_h, tau_l, bh, bl, rh, rl);
   return ok;
 }
 
@@ -422,10 +496,12 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
         df::Acc lap[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) lap[j] = df::zero();
-        float nh[E][K], nl[E][K];
+        float nh[E][K], nl[E][K], vh[E], vl[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int64_t c = scol[e * TILE_PX + t];
+          vh[e] = svh[e * TILE_PX + t];
+          vl[e] = svl[e * TILE_PX + t];
           const uint32_t loc = (uint32_t)(c - base);
           if (loc < (uint32_t)TILE_PX) {
 #pragma unroll
@@ -439,33 +515,13 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
               ok &= df::split(Xg[(size_t)j * ldu + c], nh[e][j], nl[e][j]);
           }
         }
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const float vh = svh[e * TILE_PX + t], vl = svl[e * TILE_PX + t];
-#pragma unroll
-          for (int j = 0; j < K; ++j) df::fma(lap[j], vh, vl, nh[e][j], nl[e][j]);
-        }
-        df::Acc g[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) g[j] = df::zero();
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-#pragma unroll
-          for (int b = 0; b <= a; ++b) {
-            const int q = a * (a + 1) / 2 + b;
-            const float ph = sph[q * TILE_PX + t], pl = spl[q * TILE_PX + t];
-            df::fma(g[a], ph, pl, xh[b], xl[b]);
-            if (b != a) df::fma(g[b], ph, pl, xh[a], xl[a]);
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-          float lh, ll;
-          df::norm(lap[j], lh, ll);
-          df::fma(g[j], tau_h[j], tau_l[j], lh, ll);
-          df::sub_from(bh[j], bl[j], g[j], rh[j], rl[j]);
-          ok &= isfinite(rh[j]) && isfinite(rl[j]);
-        }
+        df_stencil<K, E>(lap, vh, vl, nh, nl);
+        ok &= df_finish<K>(lap, xh, xl,
+                           [&](int q, float& ph, float& pl) {
+                             ph = sph[q * TILE_PX + t];
+                             pl = spl[q * TILE_PX + t];
+                           },
+                           tau_h, tau_l, bh, bl, rh, rl);
       } else {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
