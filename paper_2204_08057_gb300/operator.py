@@ -115,9 +115,9 @@ class Operator:
         Bb = self._batch(Bv, self.k)
         if opts is None:
             opts = B.make_opts(**kw)
-        X = Bb.new_zeros(Bb.shape) if X0 is None else self._batch(X0, self.k).clone()
-        if X0 is not None:
-            opts.use_x0 = 1
+        # without a start the library zeroes X itself (the whole nrhs x k x ld block)
+        X = Bb.new_empty(Bb.shape) if X0 is None else self._batch(X0, self.k).clone()
+        opts.use_x0 = 1 if X0 is not None else 0
         allow = tuple(allow) + ((B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ())
         code, info = B.sylv_solve(self.handle, Bb, X, Bb.shape[0], opts, k=self.k, ld=self.ld,
                                   n=self.n, stream=stream, allow=allow)
@@ -154,9 +154,9 @@ class Operator:
         Bb = self._batch(Bv, self.k)
         if opts is None:
             opts = B.make_opts(**kw)
-        X = Bb.new_zeros(Bb.shape) if X0 is None else self._batch(X0, self.k).clone()
-        if X0 is not None:
-            opts.use_x0 = 1
+        # without a start the library zeroes X itself (the whole nrhs x k x ld block)
+        X = Bb.new_empty(Bb.shape) if X0 is None else self._batch(X0, self.k).clone()
+        opts.use_x0 = 1 if X0 is not None else 0
         allow = tuple(allow) + ((B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ())
         code, info = B.sylv_solve_sylvester(self.handle, Bb, X, Bb.shape[0], opts, k=self.k,
                                             ld=self.ld, n=self.n, stream=stream, allow=allow)
@@ -222,7 +222,8 @@ class Operator:
             lam = self._batch(lam0, self.k).clone()
             opts.use_x0 = 1
         else:
-            lam = Xb.new_zeros(Xb.shape)
+            lam = Xb.new_empty(Xb.shape)      # zeroed by the library (no start given)
+            opts.use_x0 = 0
         gt, gk, gb, info = B.sylv_backward(self.handle, Xb, Gb, Yb, Xb.shape[0], lam, opts,
                                            k=self.k, m=self.m, ld=self.ld, n=self.n,
                                            want=want, stream=stream)
@@ -234,7 +235,8 @@ def solve_batched(ops, Bs, *, opts=None, stream=None, allow_not_converged=False,
     if opts is None:
         opts = B.make_opts(**kw)
     Bb = [op._batch(b, op.k) for op, b in zip(ops, Bs)]
-    Xs = [b.new_zeros(b.shape) for b in Bb]
+    Xs = [b.new_empty(b.shape) for b in Bb]   # zeroed by the library (no start given)
+    opts.use_x0 = 0
     allow = (B.SYLV_E_NOT_CONVERGED,) if allow_not_converged else ()
     code, infos = B.sylv_solve_batched([op.handle for op in ops], Bb, Xs,
                                        [b.shape[0] for b in Bb], opts,
