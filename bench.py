@@ -122,32 +122,33 @@ class ClockSampler:
 # algorithmic bytes per pixel: every stream a kernel must read or write once per pixel
 # ---------------------------------------------------------------------------------------------
 def bytes_inner_apply(k, m, E, s=4):
-    # read z, p, q (3k) + D (m) + ELL values (E) + diagonal (1); write p, q (2k); ELL cols int32
-    return (5 * k + m + E + 1) * s + 4 * E
+    # read z, p, q, d (4k) + D (m) + ELL values (E) + diagonal (1); write p, q, d (3k); ELL
+    # cols int32 (the previous iteration's d += alpha p is done here, where p is read anyway)
+    return (7 * k + m + E + 1) * s + 4 * E
 
 
 def bytes_inner_update(k, m, s=4):
-    # read d, p, r, q (4k) + preconditioner scaling (k, FP32) + factor (k(k+1)/2, FP16);
-    # write d, r, z (3k)
-    return (8 * k) * s + 2 * (k * (k + 1) // 2)
+    # read r, q (2k) + preconditioner scaling (k, FP32) + factor (k(k+1)/2, FP16);
+    # write r, z (2k)
+    return (5 * k) * s + 2 * (k * (k + 1) // 2)
 
 
 def fp64_ops_inner(k, E):
     """FP64 floating-point operations per pixel of one FP64 PCG iteration (an FMA is two), as
     the FP64 kernels compute them: the operator kernel (pixel block k^2 FMAs, stencil E k, the
-    tau scaling k, p and q updates 2k, p . q k) and the update kernel (d and r updates 2k,
-    block solve k(k-1) FMAs and 4k multiplies, r . z and r . r 2k)."""
-    apply_fma = k * k + E * k + 4 * k
-    update_fma, update_mul = k * k + 3 * k, 4 * k
+    tau scaling k, d, p and q updates 3k, p . q k) and the update kernel (r update k, block
+    solve k(k-1) FMAs and 4k multiplies, r . z and r . r 2k)."""
+    apply_fma = k * k + E * k + 5 * k
+    update_fma, update_mul = k * k + 2 * k, 4 * k
     return 2 * apply_fma + 2 * update_fma + update_mul
 
 
 def bytes_inner_fp64(k, E):
-    """Bytes per pixel of one FP64 PCG iteration: operator kernel reads z, p, q, the FP64 pixel
-    block (k(k+1)/2), ELL values (FP64) and columns, writes p, q; update kernel reads d, p, r,
-    q and the FP64 factor (k + k(k+1)/2), writes d, r, z."""
+    """Bytes per pixel of one FP64 PCG iteration: operator kernel reads z, p, q, d, the FP64
+    pixel block (k(k+1)/2), ELL values (FP64) and columns, writes p, q, d; update kernel reads
+    r, q and the FP64 factor (k + k(k+1)/2), writes r, z."""
     nb = k * (k + 1) // 2
-    return (5 * k * 8 + nb * 8 + E * 8 + 4 * E) + (7 * k * 8 + (k + nb) * 8)
+    return (7 * k * 8 + nb * 8 + E * 8 + 4 * E) + (4 * k * 8 + (k + nb) * 8)
 
 
 def fp64_peak_tflops(dev):
@@ -722,6 +723,9 @@ def run_batched(args):
                       "rule": "largest first to the least-loaded rank, work = n k"},
         "iterations_max": max(i["iterations"] for i in infos),
         "relres_max": max(i["relres"] for i in infos),
+        "per_system": {"n": [p.n for p in probs], "k": [p.k for p in probs],
+                       "iterations": [i["iterations"] for i in infos],
+                       "outer": [i["outer"] for i in infos]},
         "kernel_ms_per_solve": {"inner_apply": infos[0]["ms_apply"],
                                 "inner_update": infos[0]["ms_update"],
                                 "residual64": infos[0]["ms_residual"]},

@@ -2,20 +2,24 @@
 //
 // Per inner iteration two kernels run over every active system:
 //
-//   inner_apply:  p = z + beta p,  q = G z + beta q   (= G p, since G p = G z + beta G p_old),
+//   inner_apply:  d += alpha_prev p_old (the previous iteration's step),  p = z + beta p_old,
+//                 q = G z + beta q   (= G p, since G p = G z + beta G p_old),
 //                 partial sums of p . q; the last CTA of a system sets alpha = gamma / (p . q).
-//   inner_update: d += alpha p,  r -= alpha q,  z = P^{-1} r (pixel-block Jacobi),
+//   inner_update: r -= alpha q,  z = P^{-1} r (pixel-block Jacobi),
 //                 partial sums of r . z and r . r; the last CTA sets beta, gamma and the
 //                 stopping state.
 //
 // This is Algorithm 2 with a preconditioner, reordered so that the operator is applied to the
-// freshly written z (no halo of the still-to-be-updated p is needed) and the direction update
-// p = z + beta p is folded into the operator kernel.  The operator application is the block
+// freshly written z (no halo of the still-to-be-updated p is needed), the direction update
+// p = z + beta p is folded into the operator kernel, and so is the solution step d += alpha p
+// of the iteration before (both need the old p, which is then read once per iteration instead
+// of twice).  When the inner solve ends on an update, that update's alpha p is added by
+// update_x (ColState::dpend).  The operator application is the block
 // mapping of eq. block-vector-mapping-matvec fused with the neighbour stencil of Algorithm 1:
 //   (G X)_{j,i} = tau_j (kappa_j^2 w_i x_{j,i} + L_ii x_{j,i} + sum_e L_{i,col_e} x_{j,col_e})
 //               + sum_c a_cj d_ci (a_c . x_i).
 //
-// The FP64 refinement loop adds two kernels: update_x (X += d) and residual (r = B - G X in
+// The FP64 refinement loop adds two kernels: update_x (X += d [+ alpha p]) and residual (r = B - G X in
 // FP64, r_in = r rounded to the inner type, d = 0, z = P^{-1} r_in), whose last CTA decides
 // convergence of each column on the true FP64 residual.
 //
@@ -90,6 +94,7 @@ struct CtaShared {
   alignas(16) T tau[8];
   alignas(16) T tk2[8];
   T sc[RMAX];        // per-column scalar (beta or alpha)
+  T sc2[RMAX];       // second per-column scalar (the operator kernels: the last alpha)
   int act[RMAX];     // column takes part in this kernel
   int aux[RMAX];     // per-column flag (first iteration)
   double wacc[RMAX][MAX_WARPS][NV];  // per-warp partial sums
@@ -404,6 +409,7 @@ __device__ __forceinline__ void after_update(ColState& cs, double rz, double rr,
     }
   } else if (rr <= cs.thr_in || rr == 0.0) {
     cs.phase = PH_INNER_DONE;
+    cs.dpend = 1;
     if (count) atomicSub(&ctl->n_active, 1u);
   } else if (!(rz > 0.0)) {
     cs.phase = PH_FAILED;
@@ -414,6 +420,7 @@ __device__ __forceinline__ void after_update(ColState& cs, double rz, double rr,
     }
   } else if (cs.it >= ctl->maxit) {
     cs.phase = PH_INNER_DONE;
+    cs.dpend = 1;
     cs.stop_after = 1;
     if (count) atomicSub(&ctl->n_active, 1u);
   } else {
@@ -455,6 +462,7 @@ __device__ __forceinline__ void after_residual(ColState& cs, const double (&t)[4
     const double fac = need > ctl->tol_in2 ? need : ctl->tol_in2;
     cs.phase = PH_INNER;
     cs.first = 1;
+    cs.dpend = 0;
     cs.gamma = rz;
     cs.rr_in0 = rr;
     cs.rr_in = rr;
@@ -521,7 +529,8 @@ __device__ __forceinline__ bool finish_partials(const SysDesc& sd, int slot, int
 }
 
 // ---------------------------------------------------------------------------------------------
-// inner_apply: p = z + beta p, q = G z + beta q, partial p . q
+// inner_apply: d += alpha p (the previous iteration's step, deferred to here so that p is read
+// once per iteration), p = z + beta p, q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
 // FP32 instances are held to 64 registers (4 CTAs of 256 per SM); FP64 ones, whose
 // preconditioner factor alone needs ~60 registers, to 128.
@@ -541,6 +550,7 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
       const ColState& cs = sd.st[r];
       act = cs.phase == PH_INNER;
       sh.sc[r] = T(cs.beta);
+      sh.sc2[r] = T(cs.alpha);
       sh.aux[r] = cs.first;
     }
     sh.act[r] = act;
@@ -560,6 +570,7 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
       const T* z = (const T*)sd.vz + off;
       T* p = (T*)sd.vp + off;
       T* q = (T*)sd.vq + off;
+      T* d = (T*)sd.vd + off;
       T zi[K], w[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) zi[j] = z[j * ld + i];
@@ -570,13 +581,15 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
       }
       T pq = T(0);
       if (valid) {
-        const T beta = sh.sc[r];
+        const T beta = sh.sc[r], alpha = sh.sc2[r];
         const bool first = sh.aux[r] != 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           T pj = zi[j], qj = w[j];
           if (!first) {
-            pj += beta * p[j * ld + i];
+            const T po = p[j * ld + i];
+            d[j * ld + i] += alpha * po;   // the previous iteration's d += alpha p
+            pj += beta * po;
             qj += beta * q[j * ld + i];
           }
           p[j * ld + i] = pj;
@@ -603,7 +616,8 @@ k_inner_apply(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
 }
 
 // ---------------------------------------------------------------------------------------------
-// inner_update: d += alpha p, r -= alpha q, z = P^{-1} r, partial r . z and r . r
+// inner_update: r -= alpha q, z = P^{-1} r, partial r . z and r . r (d += alpha p is left to
+// the next operator kernel, or to k_update_x when the inner solve ends here)
 // ---------------------------------------------------------------------------------------------
 template <int K, int M, int E, typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
@@ -646,10 +660,8 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
     for (int r = 0; r < R; ++r) {
       if (!sh.act[r]) continue;
       const size_t off = (size_t)r * K * ld;
-      T* d = (T*)sd.vd + off;
       T* rv = (T*)sd.vr + off;
       T* z = (T*)sd.vz + off;
-      const T* p = (const T*)sd.vp + off;
       const T* q = (const T*)sd.vq + off;
       const T alpha = sh.sc[r];
       T rz = T(0), rr = T(0);
@@ -657,7 +669,6 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
         T ri[K], zi[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          d[j * ld + i] += alpha * p[j * ld + i];
           ri[j] = rv[j * ld + i] - alpha * q[j * ld + i];
           rv[j * ld + i] = ri[j];
         }
@@ -693,7 +704,9 @@ k_inner_update(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ cta
 }
 
 // ---------------------------------------------------------------------------------------------
-// update_x: X += d for columns whose inner solve finished
+// update_x: X += d for columns whose inner solve finished (with the last iteration's alpha p,
+// in the inner type as the operator kernel would have added it, when the solve ended on an
+// update)
 // ---------------------------------------------------------------------------------------------
 template <int K, typename T>
 __global__ void __launch_bounds__(256)
@@ -703,14 +716,22 @@ k_update_x(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas) {
   const SysDesc& sd = descs[cr.sys];
   const int64_t ld = sd.op.ld, ldu = sd.op.ldu, n = sd.op.n;
   for (int r = 0; r < sd.R; ++r) {
-    if (sd.st[r].phase != PH_INNER_DONE) continue;
+    const ColState& cs = sd.st[r];
+    if (cs.phase != PH_INNER_DONE) continue;
+    const bool pend = cs.dpend != 0;
+    const T alpha = T(cs.alpha);
     const T* d = (const T*)sd.vd + (size_t)r * K * ld;
+    const T* p = (const T*)sd.vp + (size_t)r * K * ld;
     double* X = sd.X + (size_t)r * K * ldu;
     for (int tile = cr.slot; tile < sd.ntiles; tile += sd.nslots[2]) {
       const int64_t i = (int64_t)tile * blockDim.x + threadIdx.x;
       if (i >= n) continue;
 #pragma unroll
-      for (int j = 0; j < K; ++j) X[j * ldu + i] += double(d[j * ld + i]);
+      for (int j = 0; j < K; ++j) {
+        T dj = d[j * ld + i];
+        if (pend) dj += alpha * p[j * ld + i];
+        X[j * ldu + i] += double(dj);
+      }
     }
   }
 }

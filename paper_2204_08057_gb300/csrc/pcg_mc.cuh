@@ -31,7 +31,7 @@ namespace sylv {
 namespace tma {
 
 constexpr int MC_NOP = 2;   // operator slots
-constexpr int MC_NVS = 3;   // vector stages of the inner kernels (18-24 KB each)
+constexpr int MC_NVS = 3;   // vector stages of the inner kernels (12-32 KB each)
 constexpr int MC_NVS_X = 5; // vector stages of the stand-alone apply (2k rows each: two
                             // columns per unit, so a warp keeps both columns' gathers in flight)
 
@@ -302,12 +302,12 @@ __device__ __forceinline__ void pixel_apply_mc(const CtaShared<float, NV>& sh,
 }
 
 // ---------------------------------------------------------------------------------------------
-// inner_apply, several columns: p = z + beta p, q = G z + beta q, partial p . q (last CTA sets
-// alpha)
+// inner_apply, several columns: d += alpha p (the previous iteration's step), p = z + beta p,
+// q = G z + beta q, partial p . q (last CTA sets alpha)
 // ---------------------------------------------------------------------------------------------
 template <int K>
 struct McApplyVec {
-  static constexpr int Z = 0, P = K, Q = 2 * K, ROWS = 3 * K;
+  static constexpr int Z = 0, P = K, Q = 2 * K, Dv = 3 * K, ROWS = 4 * K;
   static constexpr int BYTES = ROWS * TILE_PX * 4;
 };
 
@@ -337,6 +337,7 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
       const ColState& cs = sd.st[r];
       act = cs.phase == PH_INNER;
       sh.sc[r] = float(cs.beta);
+      sh.sc2[r] = float(cs.alpha);
       sh.aux[r] = cs.first;
     }
     sh.act[r] = act;
@@ -357,6 +358,7 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
   float* zg = (float*)sd.vz;
   float* pg = (float*)sd.vp;
   float* qg = (float*)sd.vq;
+  float* dgl = (float*)sd.vd;
   unsigned char* opbuf = dsm;
   unsigned char* vecbuf = dsm + (size_t)MC_NOP * OR::BYTES;
   const int warp = threadIdx.x >> 5;
@@ -380,12 +382,13 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
           [&](int tile, int r, unsigned char* stage, uint64_t* bar) {
             const int64_t base = (int64_t)tile * TILE_PX;
             const size_t voff = (size_t)r * K * ld;
-            const bool first = sh.aux[r] != 0;   // p and q are not read on a first iteration
+            const bool first = sh.aux[r] != 0;   // p, q and d are not read on a first iteration
             issue_rows(reinterpret_cast<float*>(stage), first ? K : VR::ROWS, bar,
                        [&](int q) -> const void* {
-                         if (q < K) return zg + voff + (size_t)q * ld + base;
-                         if (q < 2 * K) return pg + voff + (size_t)(q - K) * ld + base;
-                         return qg + voff + (size_t)(q - 2 * K) * ld + base;
+                         if (q < VR::P) return zg + voff + (size_t)(q - VR::Z) * ld + base;
+                         if (q < VR::Q) return pg + voff + (size_t)(q - VR::P) * ld + base;
+                         if (q < VR::Dv) return qg + voff + (size_t)(q - VR::Q) * ld + base;
+                         return dgl + voff + (size_t)(q - VR::Dv) * ld + base;
                        });
           },
           pipe_budget(ctl));
@@ -403,19 +406,22 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
           const float* stage = reinterpret_cast<const float*>(stage_b);
           const int64_t i = base + t;
           const size_t voff = (size_t)r * K * ld;
+          const bool first = sh.aux[r] != 0;
           float zi[K], w[K];
 #pragma unroll
           for (int j = 0; j < K; ++j) zi[j] = stage[(VR::Z + j) * TILE_PX + t];
           pixel_apply_mc<K, E>(sh, po, stage + (size_t)VR::Z * TILE_PX, zg + voff, ld, zi, w);
-          const bool first = sh.aux[r] != 0;
-          const float beta = sh.sc[r];
-          float pn[K], qn[K];
+          const float beta = sh.sc[r], alpha = sh.sc2[r];
+          float pn[K], qn[K], dv[K];
 #pragma unroll
           for (int j = 0; j < K; ++j) {
             pn[j] = zi[j];
             qn[j] = w[j];
+            dv[j] = 0.f;
             if (!first) {
-              pn[j] += beta * stage[(VR::P + j) * TILE_PX + t];
+              const float po = stage[(VR::P + j) * TILE_PX + t];
+              dv[j] = stage[(VR::Dv + j) * TILE_PX + t] + alpha * po;
+              pn[j] += beta * po;
               qn[j] += beta * stage[(VR::Q + j) * TILE_PX + t];
             }
           }
@@ -424,6 +430,7 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
           if (i < n) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
+              if (!first) dgl[voff + (size_t)j * ld + i] = dv[j];
               pg[voff + (size_t)j * ld + i] = pn[j];
               qg[voff + (size_t)j * ld + i] = qn[j];
               pq += pn[j] * qn[j];
@@ -445,14 +452,14 @@ k_inner_apply_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ c
 }
 
 // ---------------------------------------------------------------------------------------------
-// inner_update, several columns: d += alpha p, r -= alpha q, z = P^{-1} r, partial r . z and
-// r . r (last CTA sets beta, gamma and the stopping state)
+// inner_update, several columns: r -= alpha q, z = P^{-1} r, partial r . z and r . r (last CTA
+// sets beta, gamma and the stopping state; d += alpha p is the next operator kernel's)
 // ---------------------------------------------------------------------------------------------
 template <int K>
 struct McUpdateRows {
   static constexpr int NB = K * (K + 1) / 2, NB2 = (NB + 1) / 2;
   static constexpr int S = 0, L16 = K, OP_ROWS = K + NB2;            // operator slot
-  static constexpr int Dv = 0, P = K, R = 2 * K, Q = 3 * K, VEC_ROWS = 4 * K;   // vector stage
+  static constexpr int R = 0, Q = K, VEC_ROWS = 2 * K;                 // vector stage
   static constexpr int OP_BYTES = OP_ROWS * TILE_PX * 4, VEC_BYTES = VEC_ROWS * TILE_PX * 4;
 };
 
@@ -498,10 +505,8 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   const int64_t ld = op.ld, n = op.n;
   const int nsl = sd.nslots[1];
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
-  float* dgl = (float*)sd.vd;
   float* rg = (float*)sd.vr;
   float* zg = (float*)sd.vz;
-  const float* pg = (const float*)sd.vp;
   const float* qg = (const float*)sd.vq;
   unsigned char* opbuf = dsm;
   unsigned char* vecbuf = dsm + (size_t)MC_NOP * L::OP_BYTES;
@@ -527,10 +532,8 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
             const size_t voff = (size_t)r * K * ld;
             issue_rows(reinterpret_cast<float*>(stage), L::VEC_ROWS, bar,
                        [&](int q) -> const void* {
-                         if (q < K) return dgl + voff + (size_t)q * ld + base;
-                         if (q < 2 * K) return pg + voff + (size_t)(q - K) * ld + base;
-                         if (q < 3 * K) return rg + voff + (size_t)(q - 2 * K) * ld + base;
-                         return qg + voff + (size_t)(q - 3 * K) * ld + base;
+                         if (q < L::Q) return rg + voff + (size_t)(q - L::R) * ld + base;
+                         return qg + voff + (size_t)(q - L::Q) * ld + base;
                        });
           },
           pipe_budget(ctl));
@@ -560,12 +563,10 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
           const int64_t i = base + t;
           const size_t voff = (size_t)r * K * ld;
           const float alpha = sh.sc[r];
-          float ri[K], zi[K], dn[K];
+          float ri[K], zi[K];
 #pragma unroll
-          for (int j = 0; j < K; ++j) {
-            dn[j] = stage[(L::Dv + j) * TILE_PX + t] + alpha * stage[(L::P + j) * TILE_PX + t];
+          for (int j = 0; j < K; ++j)
             ri[j] = stage[(L::R + j) * TILE_PX + t] - alpha * stage[(L::Q + j) * TILE_PX + t];
-          }
           release();
           if (prec) {
             block_solve<K, float>(f, ri, zi);
@@ -577,7 +578,6 @@ k_inner_update_mc(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
           if (i < n) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-              dgl[voff + (size_t)j * ld + i] = dn[j];
               rg[voff + (size_t)j * ld + i] = ri[j];
               zg[voff + (size_t)j * ld + i] = zi[j];
               rz += ri[j] * zi[j];

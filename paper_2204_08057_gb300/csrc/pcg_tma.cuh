@@ -2,15 +2,17 @@
 //
 // Same arithmetic as k_inner_apply / k_inner_update, restructured for the memory system.
 // A unit is one (tile, column) pair; every contiguous stream a unit needs (its rows of z, p, q
-// or d, p, r, q, the noise maps D, the ELL rows of L and its diagonal, or the stored
-// preconditioner factor; TILE_PX values each) is brought into shared memory by cp.async.bulk
+// or r, q, the noise maps D, the ELL rows of L and its diagonal, or the stored preconditioner
+// factor; TILE_PX values each) is brought into shared memory by cp.async.bulk
 // copies.  One producer warp issues the copies of unit u into stage u % NSTAGE once the
 // consumers have released that stage (an "empty" mbarrier with one arrival per consumer
 // warp), and the copies complete on the stage's "full" mbarrier.  Eight consumer warps (one
 // pixel per thread) wait only on "full", compute, and release the stage: there is no
 // CTA-wide barrier per unit, so warps drift independently and the copies stay in flight.
 // The loads need no registers while in flight; the only per-thread global loads left are the
-// stencil gathers that fall outside the tile (neighbours one image row away).
+// stencil gathers that fall outside the tile (neighbours one image row away) and, in the
+// operator kernel, the pixel's row of d (coalesced; d += alpha p of the previous iteration is
+// done there, where p is read anyway, instead of in the update kernel).
 //
 // With one active column, units run tile after tile and dot products accumulate in registers
 // until the end; with several, the columns of a tile run back to back (so the tile's operator
@@ -140,16 +142,16 @@ __device__ __forceinline__ void pipe_init(PipeShared& ps) {
 }
 
 // Producer loop over units u0 .. u1 - 1: waits for stage release (from the second round of the
-// ring on), then issues unit u with issue(u, stage).
-template <typename Issue>
+// ring on), then issues unit u with issue(u, stage).  NST: stages of the ring.
+template <int NST = NSTAGE, typename Issue>
 __device__ __forceinline__ void producer_loop_range(PipeShared& ps, int u0, int u1, Issue&& issue,
                                                     long long budget = WAIT_BUDGET_CYCLES) {
   const int lane = threadIdx.x & 31;
   for (int u = u0; u < u1; ++u) {
-    const int st = u % NSTAGE;
-    if (u >= NSTAGE) {
+    const int st = u % NST;
+    if (u >= NST) {
       bool ok = true;
-      if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NSTAGE) - 1) & 1, budget);
+      if (lane == 0) ok = mbar_wait_bounded(&ps.empty[st], ((u / NST) - 1) & 1, budget);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       if (!ok || ps.bad) {
         if (lane == 0) ps.bad = 1;
@@ -163,13 +165,14 @@ __device__ __forceinline__ void producer_loop_range(PipeShared& ps, int u0, int 
 
 // After both roles are done: on a recorded timeout, flag it, wait (bounded) for the copies
 // still in flight and report true (the caller leaves without partial sums).
+template <int NST = NSTAGE>
 __device__ __forceinline__ bool pipe_failed(PipeShared& ps, int consumed, Control* ctl) {
   __syncthreads();
   if (!ps.bad) return false;
   if (threadIdx.x == 0) {
     atomicOr(&ctl->error, 1u);
     for (int u = consumed; u < ps.issued; ++u)
-      mbar_wait_bounded(&ps.full[u % NSTAGE], (u / NSTAGE) & 1);
+      mbar_wait_bounded(&ps.full[u % NST], (u / NST) & 1);
   }
   __syncthreads();
   return true;
@@ -251,9 +254,9 @@ struct ApplyLayout {
 template <int K, int M>
 struct UpdateLayout {
   static constexpr int NB = K * (K + 1) / 2, NB2 = (NB + 1) / 2;
-  static constexpr int Dv = 0, P = K, R = 2 * K, Q = 3 * K, S = 4 * K, L16 = 5 * K;
-  static constexpr int ROWS = 5 * K + NB2;
-  static constexpr int NOPREC_ROWS = 4 * K;
+  static constexpr int R = 0, Q = K, S = 2 * K, L16 = 3 * K;
+  static constexpr int ROWS = 3 * K + NB2;
+  static constexpr int NOPREC_ROWS = 2 * K;
   static constexpr int STAGE_BYTES = ROWS * TILE_PX * 4;
 };
 
@@ -331,7 +334,8 @@ __device__ __forceinline__ void pixel_operator_ws(const CtaShared<float, NV>& sh
 }
 
 // ---------------------------------------------------------------------------------------------
-// inner_apply (staged): p = z + beta p, q = G z + beta q, partial p . q
+// inner_apply (staged): d += alpha p (the previous iteration's step), p = z + beta p,
+// q = G z + beta q, partial p . q
 // ---------------------------------------------------------------------------------------------
 // mode 0: the last CTA sets alpha (last-CTA protocol); mode 1: column states as stored in st;
 // mode 2: first the state change of the previous update kernel, from its partials.
@@ -359,6 +363,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       if (newp) cst[r] = cs;
       act = cs.phase == PH_INNER;
       sh.sc[r] = float(cs.beta);
+      sh.sc2[r] = float(cs.alpha);   // (the update kernels' state change keeps alpha)
       sh.aux[r] = cs.first;
     }
     sh.act[r] = act;
@@ -382,6 +387,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   const float* zg = (const float*)sd.vz;
   float* pg = (float*)sd.vp;
   float* qg = (float*)sd.vq;
+  float* dgl = (float*)sd.vd;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int consumed = 0;
   auto issue = [&](int u, int st) {
@@ -472,6 +478,7 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
       const int32_t* scol = reinterpret_cast<const int32_t*>(stage + (size_t)L::COL * TILE_PX);
       const size_t voff = (size_t)r * K * ld;
+      const bool first = sh.aux[r] != 0;
       float zi[K], lap[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) zi[j] = stage[(L::Z + j) * TILE_PX + t];
@@ -499,15 +506,19 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
         for (int j = 0; j < K; ++j) nb[e][j] = src[e][j * stride[e]];
       float w[K];
       pixel_operator_ws<K, M, E>(sh, stage + (size_t)L::D * TILE_PX + t, zi, lap, v, nb, w);
-      const bool first = sh.aux[r] != 0;
-      const float beta = sh.sc[r];
+      const float beta = sh.sc[r], alpha = sh.sc2[r];
       float pq = 0.f;
       if (i < n) {
+        float dv[K];   // the pixel's d, all loads in flight before the first use
+#pragma unroll
+        for (int j = 0; j < K; ++j) dv[j] = first ? 0.f : dgl[voff + (size_t)j * ld + i];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           float pj = zi[j], qj = w[j];
           if (!first) {
-            pj += beta * stage[(L::P + j) * TILE_PX + t];
+            const float po = stage[(L::P + j) * TILE_PX + t];
+            dgl[voff + (size_t)j * ld + i] = dv[j] + alpha * po;
+            pj += beta * po;
             qj += beta * stage[(L::Q + j) * TILE_PX + t];
           }
           pg[voff + (size_t)j * ld + i] = pj;
@@ -541,7 +552,8 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------------
-// inner_update (staged): d += alpha p, r -= alpha q, z = P^{-1} r, partial r . z and r . r
+// inner_update (staged): r -= alpha q, z = P^{-1} r, partial r . z and r . r (d += alpha p is
+// the next operator kernel's)
 // ---------------------------------------------------------------------------------------------
 // mode 0: the last CTA sets beta, gamma and the stopping state (last-CTA protocol); mode 1:
 // column states as stored in st2 (alpha included); mode 2: first alpha (the operator kernel's
@@ -589,10 +601,8 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
   const int64_t ld = op.ld, n = op.n;
   const bool prec = ctl->precond == SYLV_PRECOND_BLOCK_JACOBI;
   Units U = count_units(sd, cr.slot, sd.nslots[1], ps.nact);
-  float* dgl = (float*)sd.vd;
   float* rg = (float*)sd.vr;
   float* zg = (float*)sd.vz;
-  const float* pg = (const float*)sd.vp;
   const float* qg = (const float*)sd.vq;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int consumed = 0;
@@ -611,12 +621,10 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
     const size_t voff = (size_t)r * K * ld;
     for (int q = lane; q < nrows; q += 32) {
       const void* src;
-      if (q < K) src = dgl + voff + (size_t)q * ld + base;
-      else if (q < 2 * K) src = pg + voff + (size_t)(q - K) * ld + base;
-      else if (q < 3 * K) src = rg + voff + (size_t)(q - 2 * K) * ld + base;
-      else if (q < 4 * K) src = qg + voff + (size_t)(q - 3 * K) * ld + base;
-      else if (q < 5 * K) src = op.fs32 + (size_t)(q - 4 * K) * ld + base;
-      else src = op.fl16 + (size_t)(q - 5 * K) * ld + base;
+      if (q < L::Q) src = rg + voff + (size_t)(q - L::R) * ld + base;
+      else if (q < L::S) src = qg + voff + (size_t)(q - L::Q) * ld + base;
+      else if (q < L::L16) src = op.fs32 + (size_t)(q - L::S) * ld + base;
+      else src = op.fl16 + (size_t)(q - L::L16) * ld + base;
       bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
     }
   };
@@ -681,12 +689,10 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
       const float* stage = reinterpret_cast<const float*>(dsm + (size_t)st * L::STAGE_BYTES);
       const float alpha = sh.sc[r];
       const size_t voff = (size_t)r * K * ld;
-      float ri[K], zi[K], dn[K];
+      float ri[K], zi[K];
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        dn[j] = stage[(L::Dv + j) * TILE_PX + t] + alpha * stage[(L::P + j) * TILE_PX + t];
+      for (int j = 0; j < K; ++j)
         ri[j] = stage[(L::R + j) * TILE_PX + t] - alpha * stage[(L::Q + j) * TILE_PX + t];
-      }
       if (prec) {
         BlockChol<K, float> f;
         const __half2* sl = reinterpret_cast<const __half2*>(stage + (size_t)L::L16 * TILE_PX);
@@ -710,7 +716,6 @@ k_inner_update_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__
       if (i < n) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          dgl[voff + (size_t)j * ld + i] = dn[j];
           rg[voff + (size_t)j * ld + i] = ri[j];
           zg[voff + (size_t)j * ld + i] = zi[j];
           rz += ri[j] * zi[j];

@@ -421,6 +421,7 @@ __global__ void k_init_states(int ncols, const int* __restrict__ col_sys,
   cs.status = SYLV_OK;
   cs.first = 1;
   cs.stop_after = 0;
+  cs.dpend = 0;
   if (col_rhs[t] == 0) *d[col_sys[t]].counter = 0u;
 }
 

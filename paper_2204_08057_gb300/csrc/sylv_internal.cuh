@@ -53,7 +53,9 @@ struct ColState {
   int status;      // SYLV_* status once final
   int first;       // next inner apply is the first of this inner solve
   int stop_after;  // inner solve stopped on the iteration cap
-  int pad0, pad1;
+  int dpend;       // d still lacks alpha p of the last iteration (the operator kernel of the
+                   // next iteration adds it; k_update_x when the inner solve ended there)
+  int pad1;
 };
 
 // Operator data of one handle, in the device layouts the kernels read.
