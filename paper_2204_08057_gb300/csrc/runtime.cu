@@ -127,6 +127,12 @@ struct Plan {
   int* d_col_rhs = nullptr;
   std::vector<int> col_sys, col_rhs;
   cudaStream_t cap_stream = nullptr;
+  // several shape groups: one stream per group while a chunk graph is captured, so the
+  // groups' iteration chains become parallel branches of the graph (their kernels never wait
+  // on one another; the GPU fills one group's kernel tails with another's CTAs)
+  std::vector<cudaStream_t> gstreams;
+  std::vector<cudaEvent_t> gjoin;
+  cudaEvent_t gfork = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
   int graph_profile = 0;
@@ -200,6 +206,9 @@ Plan::~Plan() {
   if (ev1) cudaEventDestroy(ev1);
   if (evr0) cudaEventDestroy(evr0);
   if (evr1) cudaEventDestroy(evr1);
+  for (auto e : gjoin) cudaEventDestroy(e);
+  if (gfork) cudaEventDestroy(gfork);
+  for (auto gs : gstreams) cudaStreamDestroy(gs);
   if (cap_stream) cudaStreamDestroy(cap_stream);
 }
 
@@ -591,6 +600,15 @@ int build_plan(Plan& P, int nsys, const sylv_handle* hs, const int* R, int inner
     d.counter = P.work[s].counter;
   }
   CK(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+  if (P.groups.size() > 1) {
+    P.gstreams.assign(P.groups.size(), nullptr);
+    P.gjoin.assign(P.groups.size(), nullptr);
+    for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+      CK(cudaStreamCreateWithFlags(&P.gstreams[gi], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&P.gjoin[gi], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&P.gfork, cudaEventDisableTiming));
+  }
   CK(cudaEventCreate(&P.ev0));
   CK(cudaEventCreate(&P.ev1));
   CK(cudaEventCreate(&P.evr0));
@@ -634,6 +652,35 @@ int launch_inner_iteration(Plan& P, cudaStream_t s, cudaEvent_t e_mid, cudaEvent
   return SYLV_OK;
 }
 
+// Iteration `it` of a chunk for one group only (the branch of that group in a chunk graph).
+template <typename T>
+int launch_group_iteration(Plan& P, const Group& g, cudaStream_t s, int it, int iters) {
+  CK(launch_inner_apply<T>(g.k, g.m, g.e, kernel_variant(g, 0, it), g.ncta[0], g.block,
+                           P.d_desc, g.d_ctas[0], P.d_ctl, s));
+  CK(launch_inner_update<T>(g.k, g.m, g.e, kernel_variant(g, 1, it), g.ncta[1], g.block,
+                            P.d_desc, g.d_ctas[1], P.d_ctl, s));
+  if (it == iters - 1 && g.csum)
+    CK(launch_inner_close(g.ncta[1], P.d_desc, g.d_ctas[1], P.d_ctl, s));
+  return SYLV_OK;
+}
+
+// The chunk as one branch per group: fork from the capturing stream, each group's `iters`
+// iterations on its own stream, join back.
+template <typename T>
+int capture_group_branches(Plan& P, int iters) {
+  CK(cudaEventRecord(P.gfork, P.cap_stream));
+  for (size_t gi = 0; gi < P.groups.size(); ++gi) {
+    CK(cudaStreamWaitEvent(P.gstreams[gi], P.gfork, 0));
+    for (int it = 0; it < iters; ++it) {
+      const int rc = launch_group_iteration<T>(P, P.groups[gi], P.gstreams[gi], it, iters);
+      if (rc != SYLV_OK) return rc;
+    }
+    CK(cudaEventRecord(P.gjoin[gi], P.gstreams[gi]));
+    CK(cudaStreamWaitEvent(P.cap_stream, P.gjoin[gi], 0));
+  }
+  return SYLV_OK;
+}
+
 template <typename T>
 int ensure_graph(Plan& P, int iters, int profile) {
   if (P.graph && P.graph_iters == iters && P.graph_profile == profile) return SYLV_OK;
@@ -655,11 +702,16 @@ int ensure_graph(Plan& P, int iters, int profile) {
                                              cudaEventRecordExternal);
     if (e != cudaSuccess) rc = cuda_fail(e, "event record in capture");
   }
-  for (int it = 0; it < iters && rc == SYLV_OK; ++it)
-    rc = launch_inner_iteration<T>(P, P.cap_stream,
-                                   profile ? P.chunk_events[2 * it + 1] : nullptr,
-                                   profile ? P.chunk_events[2 * it + 2] : nullptr, true, it,
-                                   iters);
+  if (!profile && !P.gstreams.empty() && rc == SYLV_OK) {
+    rc = capture_group_branches<T>(P, iters);
+  } else {
+    // (one stream when profiling: the per-launch events time the kernels one after another)
+    for (int it = 0; it < iters && rc == SYLV_OK; ++it)
+      rc = launch_inner_iteration<T>(P, P.cap_stream,
+                                     profile ? P.chunk_events[2 * it + 1] : nullptr,
+                                     profile ? P.chunk_events[2 * it + 2] : nullptr, true, it,
+                                     iters);
+  }
   cudaError_t e = cudaStreamEndCapture(P.cap_stream, &graph);
   if (rc != SYLV_OK) {
     if (graph) cudaGraphDestroy(graph);
