@@ -66,6 +66,10 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -415,6 +419,8 @@ k_inner_apply_tma(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
       else src = op.ell_col + (size_t)(q - L::COL) * ld + base;
       if (src) bulk_load(stage + (size_t)q * TILE_PX, src, rowb, &ps.full[st]);
     }
+    // the unit's d rows, which the consumers load directly: into L2 ahead of them
+    if (!first && lane < K) bulk_prefetch_l2(dgl + voff + (size_t)lane * ld + base, rowb);
   };
   int head = 0;
   if (newp) {
