@@ -517,6 +517,48 @@ def test_autograd_reuses_one_handle_across_parameters():
     prob.close()
 
 
+@pytest.mark.parametrize("force,nrhs,precision,precond", [
+    ("128,1,0,0", 1, 0, 1),     # FP64 PCG (direct kernels), block-Jacobi
+    ("128,1,0,0", 2, 0, 0),     # FP64 CG
+    ("128,1,0,0", 2, 1, 0),     # direct FP32 kernels
+    ("256,1,1,1", 1, 1, 0),     # staged pair, consumer-side sums
+    ("256,1,1,1", 2, 1, 0),
+    ("256,1,2,2", 3, 1, 0),     # multi-column pair
+])
+def test_capped_iterates_match_oracle_pcg_steps(force, nrhs, precision, precond, monkeypatch):
+    """Capping the iterations at j (1, 2, 7) stops the solve on the j-th CG iterate from X = 0:
+    it must equal the oracle's CG (Algorithm 2) or block-Jacobi PCG after exactly j steps.
+    This pins every step of the iteration, in particular the solution step that the operator
+    kernel of the next iteration performs and its completion by the X update when the solve
+    ends on an update (after one step, the only contribution).  The FP32 kernels are compared
+    without the preconditioner: their preconditioner applies an FP16 copy of the block factor,
+    a different (approximate) block-Jacobi operator than the oracle's exact one, so only the
+    converged solutions agree there (the solve-parity tests)."""
+    from oracle import solve as osolve
+    from paper_2204_08057_gb300 import binding as Bn
+    monkeypatch.setenv("SYLV_TUNE_FORCE", force)
+    p = small_problem("sphere", 16, 64, 6, 9, seed=61, nrhs=nrhs)   # whole tiles: staged
+    op = operator_for(p)
+    _, b = oracle_solution(p)
+    L, A = oracle_L(p), model.powerlaw_mixing(p.nu, p.beta)
+    Bd = device_batch(b, p.n)
+    for j in (1, 2, 7):
+        X, info = op.solve(Bd, tol=1e-14, maxit=j, precision=precision, precond=precond,
+                           allow_not_converged=True)
+        assert info["code"] == Bn.SYLV_E_NOT_CONVERGED and info["iterations"] == j, (j, info)
+        Xg = X.cpu().numpy()[:, :, :p.n]
+        for r in range(nrhs):
+            if precond:
+                xo, it, _, _ = osolve.pcg_block_jacobi(L, p.D, p.tau, p.kappa, A, b[r], maxit=j)
+            else:
+                xo, it, _ = osolve.cg(lambda x: model.apply(L, p.D, p.tau, p.kappa, A, x),
+                                      b[r], maxit=j)
+            assert it == j
+            err = relerr(Xg[r], xo)
+            assert err <= (1e-11 if precision == 0 else 1e-4), (j, r, err)
+    op.close()
+
+
 @pytest.mark.parametrize("force,nrhs,stall", [
     ("256,1,1,1", 1, 1),     # staged double-float residual
     ("256,1,1,1", 1, 2),     # operator kernel, consumer-side sums
