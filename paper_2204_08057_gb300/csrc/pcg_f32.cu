@@ -299,7 +299,7 @@ cudaError_t launch_residual_df(int k, int m, int e, int ncta, int block, const S
 namespace {
 template <int K, int M, int E>
 size_t residual_tma_df_smem() {
-  return (size_t)tma::NSTAGE * tma::ResidLayout<K, E>::STAGE_BYTES + 2 * sizeof(DfTile<K>);
+  return (size_t)tma::NSTAGE * tma::ResidLayout<K, E>::STAGE_BYTES;
 }
 
 template <int K, int M, int E>

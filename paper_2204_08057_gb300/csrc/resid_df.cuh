@@ -327,10 +327,13 @@ k_residual_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ ctas
 // the same residual with bulk-copy staging (the layout of k_residual_tma: X and B of the tile as
 // the caller's FP64 rows, the pixel blocks and ELL values as FP32 pairs, the ELL columns, the
 // preconditioner's scaling and factor), warp-specialised: one producer warp fills a two-stage
-// ring, eight consumer warps compute.  The consumers split their own x into a tile buffer
-// (double-buffered by the count of units that use it, so one barrier per unit keeps writers
-// and readers apart) that in-tile stencil neighbours read.  Same conditions as the FP64 staged
-// kernel: whole tiles, an even ldu, 16-byte aligned X and B.
+// ring, eight consumer warps compute.  Each thread splits every x it reads where it reads it:
+// its own and its in-tile neighbours' from the stage, the others from the caller's X.  The
+// in-tile splits are done twice (once per reader), but the consumer warps never wait for one
+// another, so they drift apart and hide each other's latency (a shared buffer of split values
+// needed a barrier per unit among them: same time on one column, 151 against 173 ms per
+// 8-column solve of 50M pixels).  Same conditions as the FP64 staged kernel: whole tiles, an
+// even ldu, 16-byte aligned X and B.
 // ---------------------------------------------------------------------------------------------
 template <int K, int M, int E>
 __global__ void __launch_bounds__(tma::WS_THREADS, 1)
@@ -342,9 +345,7 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ CtaShared<double, 4> sh;
   __shared__ __align__(8) PipeShared ps;
-  __shared__ __align__(8) uint64_t cbar;   // consumer warps: split x written (one per warp)
   __shared__ float tau_h[8], tau_l[8];
-  DfTile<K>* tiles = reinterpret_cast<DfTile<K>*>(dsm + (size_t)NSTAGE * L::STAGE_BYTES);
   const CtaRef cr = ctas[blockIdx.x];
   if (cr.sys < 0) return;  // idle CTA of a reassigned launch
   const SysDesc& sd = descs[cr.sys];
@@ -373,8 +374,7 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
     for (int r = 0; r < R; ++r)
       if (sh.act[r]) ps.cols[na++] = r;
     ps.nact = na;
-    mbar_init(&cbar, NCONS);
-    pipe_init(ps);   // (its fence also covers cbar's initialisation)
+    pipe_init(ps);
   }
   if (!__syncthreads_or(act)) return;
 
@@ -446,7 +446,6 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
     // products in FP32 (a stopping test needs a few digits; the sums of squares cannot cancel),
     // FP64 across warps and CTAs
     float a_rr64 = 0.f, a_bb = 0.f, a_rz = 0.f, a_rr = 0.f;
-    int buffered = 0;   // units that used the split-x tile buffer so far
     for (int u = 0; u < U.n; ++u) {
       const int st = u % NSTAGE;
       if (!mbar_wait_bounded(&ps.full[st], (u / NSTAGE) & 1, pipe_budget(ctl)) || ps.bad) {
@@ -473,48 +472,32 @@ k_residual_tma_df(const SysDesc* __restrict__ descs, const CtaRef* __restrict__ 
 #pragma unroll
       for (int j = 0; j < K; ++j) ok &= df::split(sb[j * TILE_PX + t], bh[j], bl[j]);
       if (with_op) {
-        DfTile<K>& tb = tiles[buffered & 1];
         float xh[K], xl[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-          const bool okj = df::split(sx[j * TILE_PX + t], xh[j], xl[j]);
-          ok &= okj;
-          tb.h[j][t] = okj ? xh[j] : __int_as_float(0x7fc00000);   // NaN: not split
-          tb.l[j][t] = xl[j];
-        }
-        // every consumer warp has written its pixels' split x: one arrival per warp on cbar,
-        // then a bounded wait for the phase (a warp that gave up never arrives, and the others
-        // give up after the wait budget instead of blocking)
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&cbar);
-        if (!mbar_wait_bounded(&cbar, buffered & 1, pipe_budget(ctl)) || ps.bad) {
-          ps.bad = 1;
-          break;
-        }
-        ++buffered;
-        // stencil: in-tile neighbours from the split buffer, the others from the caller's X
+        for (int j = 0; j < K; ++j) ok &= df::split(sx[j * TILE_PX + t], xh[j], xl[j]);
+        // stencil: every neighbour's x split where it is read, in-tile ones from the stage,
+        // the others from the caller's X (generic pointers: no branch, no barrier between the
+        // consumer warps)
         df::Acc lap[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) lap[j] = df::zero();
         float nh[E][K], nl[E][K], vh[E], vl[E];
+        const double* src[E];
+        int64_t stride[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int64_t c = scol[e * TILE_PX + t];
           vh[e] = svh[e * TILE_PX + t];
           vl[e] = svl[e * TILE_PX + t];
           const uint32_t loc = (uint32_t)(c - base);
-          if (loc < (uint32_t)TILE_PX) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-              nh[e][j] = tb.h[j][loc];
-              nl[e][j] = tb.l[j][loc];
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-              ok &= df::split(Xg[(size_t)j * ldu + c], nh[e][j], nl[e][j]);
-          }
+          const bool in = loc < (uint32_t)TILE_PX;
+          src[e] = in ? sx + loc : Xg + c;
+          stride[e] = in ? (int64_t)TILE_PX : ldu;
         }
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+#pragma unroll
+          for (int j = 0; j < K; ++j) ok &= df::split(src[e][j * stride[e]], nh[e][j], nl[e][j]);
         df_stencil<K, E>(lap, vh, vl, nh, nl);
         ok &= df_finish<K>(lap, xh, xl,
                            [&](int q, float& ph, float& pl) {
