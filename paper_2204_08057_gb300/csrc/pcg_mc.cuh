@@ -31,8 +31,8 @@ namespace sylv {
 namespace tma {
 
 constexpr int MC_NOP = 2;   // operator slots
-constexpr int MC_NVS = 3;   // vector stages of the inner kernels (12-32 KB each)
-constexpr int MC_NVS_X = 5; // vector stages of the stand-alone apply (2k rows each: two
+constexpr int MC_NVS = 2;   // vector stages of the inner kernels (12-32 KB each)
+constexpr int MC_NVS_X = 4; // vector stages of the stand-alone apply (2k rows each: two
                             // columns per unit, so a warp keeps both columns' gathers in flight)
 
 template <int NVS = MC_NVS>
